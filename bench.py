@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Design iterations per second of SIMP topology optimisation on one GB300.
+
+Workload: the 3D cantilever of Ferrari & Sigmund (2020), Sec. 4, on a
+96x48x48 H8 grid (221,184 elements, 698,691 DOFs): volfrac 0.12, penal 3,
+rmin sqrt(3), volume-preserving projection (ft = 3) with beta 2 -> 16 doubling
+every 25 iterations, state solve by PCG to a relative residual of 1e-8.
+
+A step is one full design iteration (filter, projection and eta, state solve,
+sensitivities, chain rule, OC update) through the C ABI (to_step). The timed
+steps are design iterations W+1 .. W+K of one run from the paper's initial
+design. Under torchrun every rank runs an independent replica on its GPU
+(the single-grid path does not shard); value = all ranks' iterations / the
+slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TO iters/s, 3D 2.2e5 elems: learned+mixed vs plain FP64; % HBM roofline"
+UNIT = "design iterations/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA peak from unit counts: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "gmg"])
+    ap.add_argument("--grid", default="96x48x48")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(grid):
+    nelx, nely, nelz = (int(v) for v in grid.split("x"))
+    return dict(nelx=nelx, nely=nely, nelz=nelz, volfrac=0.12, penal=3.0, rmin=math.sqrt(3.0),
+                ft=3, eta=0.5, beta=2.0, move=0.2, cg_rtol=1e-8)
+
+
+def workload_name(w):
+    return (f"3D cantilever {w['nelx']}x{w['nely']}x{w['nelz']} H8 "
+            f"({w['nelx'] * w['nely'] * w['nelz']} elements), volfrac 0.12, penal 3, rmin sqrt(3), "
+            f"ft 3, beta 2->16 x2 every 25 it, PCG rtol 1e-8")
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our GPU arm --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_05436_gb300 import TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI
+    from paper_2005_05436_gb300 import build as B, default_params, inputs as I, load
+    from paper_2005_05436_gb300.topopt import Design, Grid
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    lib = load()
+
+    w = workload(args.grid)
+    precision = TO_MIXED if args.precision == "mixed" else TO_FP64
+    precond = TO_PC_GMG if args.precond == "gmg" else TO_PC_JACOBI
+    F, fixed = I.cantilever_3d(w["nelx"], w["nely"], w["nelz"])
+    p = default_params(3, w["nelx"], w["nely"], w["nelz"], volfrac=w["volfrac"], penal=w["penal"],
+                       rmin=w["rmin"], ft=w["ft"], eta=w["eta"], beta=w["beta"], move=w["move"],
+                       cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
+                       penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+    stream = torch.cuda.current_stream()
+    g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
+    x0 = torch.from_numpy(I.initial_design(g.nel, w["volfrac"])).cuda()
+    d = Design(g, x0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(d.step())
+    torch.cuda.synchronize()
+    snap = [t.clone() for t in (d.x, d.xPhys, d.xOld, d.U)]
+    snap_sc = (d.st.eta, d.st.penal, d.st.beta, d.st.loop)
+
+    # ---- device-timed steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.to_kernel_launches()
+    timed = []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict the working set from L2 between steps
+            ev[k][0].record(stream)
+            timed.append(d.step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = lib.to_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (matrix-free K u), same process
+    us = g.time_apply_K(d.xPhys, precision, reps=30)
+    nel, ndof = g.nel, g.ndof
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    if precision == TO_FP64:
+        flops = 2.0 * 24 * 24 * nel
+        achieved = flops / (us * 1e-6) / 1e12
+        roof = {"kernel": "k_apply_K3<double> (node-centric FP64 K u)", "bound": "alu",
+                "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "us_per_launch": round(us, 2),
+                "peak_source": "FP64 FMA units: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        nbytes = 4.0 * (2 * ndof + nel)
+        achieved = nbytes / (us * 1e-6) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "mixed K u", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "us_per_launch": round(us, 2), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        for t, s in zip((d.x, d.xPhys, d.xOld, d.U), snap):
+            t.copy_(s)
+        d.st.eta, d.st.penal, d.st.beta, d.st.loop = snap_sc
+        x_host = torch.empty(nel, dtype=torch.float64, pin_memory=True)
+        x_host.copy_(snap[0].cpu())
+        out_host = torch.empty(nel, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        cs = []
+        for k in range(args.steps):
+            d.x.copy_(x_host, non_blocking=True)
+            info = d.step()
+            out_host.copy_(d.x, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            x_host.copy_(out_host)
+            cs.append(info["c"])
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(world * args.steps / e2e_s, 4), "unit": UNIT,
+               "h2d_bytes_per_step": nel * 8, "d2h_bytes_per_step": nel * 8 + 8 * 18}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        n_cg = [t["n_cg"] for t in timed] if precision == TO_FP64 and args.precond == "jacobi" else None
+        cpu = cpu_baseline(args.grid, n_cg_hint=n_cg)
+
+    last = timed[-1]
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == TO_FP64 else "f32+tf32 inner, f64 residual/refinement",
+        "data": "synthetic (paper's cantilever load and supports; no dataset)",
+        "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                   "precision": args.precision, "precond": args.precond,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "per_step": [{"loop": t["loop"], "ms": round(m, 2), "n_cg": t["n_cg"], "n_refine": t["n_refine"],
+                      "c": t["c"], "rel_res": t["rel_res"], "t_solve_ms": round(t["t_solve_ms"], 2)}
+                     for t, m in zip(timed, step_ms)],
+        "final": {"c": last["c"], "V": last["V"], "eta": last["eta"]},
+        "paper_context": "top3D125 + MGCG, 96x48x48 rmin 2sqrt(3): 14.20 s/it (0.0704 it/s), "
+                         "serial Matlab FP64 on an i7-5500U (Table 4); different rmin, context only",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------- the oracle (CPU) --
+
+def oracle_step_sample(grid, s=None, cg_cap=25, n_cg_hint=None):
+    """One design iteration of the FP64 oracle on the full grid with its PCG
+    capped at cg_cap iterations; the solve time is scaled to n_cg iterations
+    (the count the same Jacobi-PCG needs, if known, else a geometric
+    extrapolation of the capped residual decay to rtol 1e-8).
+    Returns (seconds per design iteration, detail dict, state)."""
+    import numpy as np
+
+    from oracle import topopt_oracle as O
+    from paper_2005_05436_gb300 import inputs as I
+
+    w = workload(grid)
+    p = O.Params(nelx=w["nelx"], nely=w["nely"], nelz=w["nelz"], volfrac=w["volfrac"], penal=w["penal"],
+                 rmin=w["rmin"], ft=3, beta=w["beta"], eta=w["eta"], move=w["move"], solver="pcg",
+                 cg_rtol=w["cg_rtol"])
+    F, fixed = I.cantilever_3d(w["nelx"], w["nely"], w["nelz"])
+    g = O.Grid(p.nelx, p.nely, p.nelz)
+    Ke = O.element_stiffness(3, p.nu)
+    if s is None:
+        s = O.initial_state(p)
+    t = {}
+    c0 = time.perf_counter()
+    xt = O.filter_forward(g, s.x, p.rmin, p.ftBC)
+    s.eta, _ = O.eta_newton(xt, s.eta, s.beta, p.volfrac, p.newton_tol)
+    dp = O.dprj(xt, s.eta, s.beta)
+    xphys = O.prj(xt, s.eta, s.beta)
+    t["filter_project"] = time.perf_counter() - c0
+    c0 = time.perf_counter()
+    E = O.simp_modulus(xphys, s.penal)
+    K = O.full_from_lower(O.assemble_lower(g, Ke, E))
+    t["assembly"] = time.perf_counter() - c0
+    c0 = time.perf_counter()
+    U, it, rel = O.solve_pcg(g, Ke, E, F, fixed, rtol=w["cg_rtol"], maxit=cg_cap, U0=s.U)
+    t_cg = time.perf_counter() - c0
+    # solve_pcg re-assembles internally: remove that share from the per-iteration cost
+    t_cg_iter = max(t_cg - t["assembly"], 1e-9) / max(it, 1)
+    if n_cg_hint:
+        n_cg = float(n_cg_hint)
+        how = "Jacobi-PCG iteration count of the same solve on the GPU FP64 path"
+    else:
+        rate = rel ** (1.0 / max(it, 1)) if rel > 0 else 0.5
+        n_cg = min(50000.0, math.log(w["cg_rtol"]) / math.log(min(rate, 0.999999)))
+        how = f"geometric extrapolation of the capped residual decay ({it} it -> {rel:.2e})"
+    t["solve"] = t["assembly"] + n_cg * t_cg_iter
+    c0 = time.perf_counter()
+    dc, c, _ = O.sensitivity(g, Ke, xphys, U, F, s.penal)
+    dV = np.full(g.nel, 1.0 / (g.nel * p.volfrac))
+    dcf = O.filter_backward(g, dc, p.rmin, p.ftBC, dp)
+    dV0 = O.filter_backward(g, dV, p.rmin, p.ftBC, dp)
+    t["sensitivity"] = time.perf_counter() - c0
+    c0 = time.perf_counter()
+    s.x, _, _ = O.oc_update(s.x, dcf, dV0, np.ones(g.nel, bool), p.move, p.volfrac, p.oc_tol)
+    t["oc"] = time.perf_counter() - c0
+    s.U = U
+    s.loop += 1
+    total = t["filter_project"] + t["solve"] + t["sensitivity"] + t["oc"]
+    detail = {k: round(v, 3) for k, v in t.items()}
+    detail.update({"cg_iters_run": it, "cg_iters_scaled_to": round(n_cg, 1), "cg_scale": how,
+                   "s_per_cg_iter": round(t_cg_iter, 4)})
+    return total, detail, s
+
+
+def cpu_baseline(grid, n_cg_hint=None):
+    hint = None
+    if n_cg_hint:
+        hint = sum(n_cg_hint) / len(n_cg_hint)
+    total, detail, _ = oracle_step_sample(grid, n_cg_hint=hint)
+    return {"value": round(1.0 / total, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("one FP64 oracle design iteration on the full grid (numpy/scipy, single thread): "
+                       "filter+projection, assembly, sensitivities, OC timed in full; Jacobi-PCG run "
+                       "for 25 iterations and its time scaled to the iteration count of the same solve"),
+            "detail": detail}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    s = None
+    for _ in range(args.warmup):
+        _, _, s = oracle_step_sample(args.grid, s=s, cg_cap=10)
+    totals, details = [], []
+    for _ in range(args.steps):
+        tot, det, s = oracle_step_sample(args.grid, s=s, cg_cap=25)
+        totals.append(tot)
+        details.append(det)
+    value = args.steps / sum(totals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * sum(totals) / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(workload(args.grid)),
+                   "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: one oracle design iteration on the full grid, Jacobi-PCG "
+                                   "capped at 25 iterations and scaled by geometric extrapolation to rtol 1e-8",
+                         "detail": details[-1]},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * topopt.h - C ABI of the GB300 (sm_103a) SIMP topology-optimisation hot path.
+ *
+ * The library computes one design iteration of minimum-compliance topology
+ * optimisation on structured 2D Q4 / 3D H8 grids as defined by Ferrari &
+ * Sigmund (2020), "A new generation 99 line Matlab code for compliance
+ * topology optimization and its extension to 3D": density filter (Eq. 2),
+ * Heaviside projection with volume-preserving threshold (Eq. 1, Sec. 3.2),
+ * state solve K(xPhys) U = F (Eqs. 4-5) by preconditioned CG with a
+ * matrix-free stiffness operator, compliance sensitivities (Eq. 6) and their
+ * chain rule (Eq. 7), and the OC update with the lambda# bracket (Eqs. 13-14,
+ * 17).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a to_status; TO_OK is 0. On failure,
+ *    to_last_error() returns a thread-local message. Nothing throws or aborts
+ *    across the ABI.
+ *  - Array arguments are caller-owned DEVICE pointers (e.g. torch CUDA tensors)
+ *    unless the comment says "host". The library never frees caller memory.
+ *  - Work is enqueued on the stream given to to_init_grid (NULL = the legacy
+ *    default stream). Entry points that return host scalars (pointers marked
+ *    "host out") synchronise that stream before returning; the others are
+ *    asynchronous.
+ *  - Layouts follow the paper's column-major numbering (Sec. 3, PRE.2),
+ *    0-based: node n = iy + (nely+1)(iz + (nelz+1) ix), element
+ *    e = iy + nely (iz + nelz ix), DOF = dim*n + c with c = 0 (X, along ix),
+ *    1 (Y, up = -iy), 2 (Z, along iz). 2D grids use nelz = 0.
+ *  - FP64 arrays are float64 (double), masks uint8 / int8.
+ *  - Caller arrays must not overlap unless a comment allows in-place use.
+ */
+#ifndef TOPOPT_H
+#define TOPOPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum to_status {
+    TO_OK = 0,
+    TO_EINVAL = 1,    /* bad argument (sizes, NULL pointer, parameter range) */
+    TO_ENOMEM = 2,    /* device allocation failed */
+    TO_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    TO_ENOTCONV = 4,  /* an iteration hit its cap before its tolerance */
+    TO_ENAN = 5,      /* a NaN or Inf appeared in a residual or a reduction */
+    TO_ETIMEOUT = 6   /* a device-side wait passed its clock deadline */
+} to_status;
+
+enum { TO_FP64 = 0, TO_MIXED = 1 };                        /* to_params.precision */
+enum { TO_PC_JACOBI = 0, TO_PC_GMG = 1 };                  /* to_params.precond */
+enum { TO_CNT_ADD = 0, TO_CNT_MUL = 1 };                   /* to_continuation.kind */
+
+/* Continuation parCont = {istart, maxPar, isteps, deltaPar} (Sec. 3): after the
+ * OC update of iteration `loop` (1-based), if loop >= istart, par < maxpar and
+ * loop % isteps == 0, then par += delta (TO_CNT_ADD, the paper) or
+ * par = min(maxpar, par * delta) (TO_CNT_MUL). */
+typedef struct to_continuation {
+    int32_t istart;
+    int32_t isteps;
+    double maxpar;
+    double delta;
+    int32_t kind;
+    int32_t _pad;
+} to_continuation;
+
+/* Problem and solver parameters (the arguments of top99neo / top3D125, Sec. 3,
+ * plus the solver controls of the GPU path). Fill with to_params_init. */
+typedef struct to_params {
+    int32_t dim;            /* 2 or 3 */
+    int32_t nelx, nely, nelz;  /* elements per axis; nelz = 0 for 2D */
+    double E0, Emin, nu;    /* Eq. (5) moduli and Poisson ratio (1, 1e-9, 0.3) */
+    double volfrac;         /* volume fraction f of Eq. (3) */
+    double penal;           /* SIMP exponent p of Eq. (5), initial value */
+    double rmin;            /* filter radius of Eq. (2) */
+    int32_t ft;             /* 1: filter; 2: + projection, fixed eta; 3: + volume-preserving eta */
+    int32_t ftBC;           /* 'N' mirror (zero-Neumann) or 'D' zero padding */
+    double eta, beta;       /* projection threshold (initial) and sharpness (initial) */
+    double move;            /* OC move limit mu */
+    to_continuation penal_cnt, beta_cnt;
+    double newton_tol;      /* |mean(prj) - volfrac| stop of the eta Newton (paper: 1e-6) */
+    int32_t newton_maxit;   /* Newton cap before the bisection fallback (50) */
+    int32_t oc_maxit;       /* lambda bisection cap (200) */
+    double oc_tol;          /* (l2-l1)/(l1+l2) stop of the bisection (paper: 1e-4) */
+    double cg_rtol;         /* ||F - K U|| / ||F|| stop of the state solve (1e-8) */
+    int32_t cg_maxit;       /* PCG iteration cap */
+    int32_t precision;      /* TO_FP64 or TO_MIXED */
+    int32_t precond;        /* TO_PC_JACOBI or TO_PC_GMG */
+    int32_t mg_levels;      /* GMG levels incl. the fine grid, 0 = automatic */
+    int64_t deadline_cycles;/* clock64 limit of every device-side wait (2e9) */
+} to_params;
+
+typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */
+
+/* Result of one state solve. */
+typedef struct to_solve_info {
+    int32_t iters;          /* PCG iterations (inner iterations in TO_MIXED) */
+    int32_t refinements;    /* outer FP64 refinement steps (TO_MIXED), else 0 */
+    double rel_res;         /* ||F - K U||_2 / ||F||_2 in FP64 at exit */
+    int32_t status;         /* to_status of the solve */
+    int32_t _pad;
+} to_solve_info;
+
+/* Design state advanced by to_step. Device pointers are caller-owned, FP64:
+ * x[nEl] design variables, xPhys[nEl] physical densities, xOld[nEl] previous
+ * xPhys (ch measure), U[nDof] displacements (warm start in, solution out).
+ * Host scalars eta, penal, beta and loop are read and updated. */
+typedef struct to_state {
+    double* x;
+    double* xPhys;
+    double* xOld;
+    double* U;
+    double eta, penal, beta;
+    int32_t loop;
+    int32_t _pad;
+} to_state;
+
+/* Per-iteration record (the listing's log line: It, C, V, ch, penal, beta,
+ * eta, lm) plus solver and timing counters. */
+typedef struct to_iter_info {
+    int32_t loop;
+    int32_t n_cg;           /* PCG iterations of the state solve */
+    int32_t n_refine;       /* FP64 refinement steps (TO_MIXED) */
+    int32_t n_newton;       /* eta Newton steps */
+    int32_t n_bisect;       /* lambda bisection steps */
+    int32_t status;
+    double c;               /* compliance F^T U (Eq. 3) */
+    double V;               /* mean(xPhys) */
+    double ch;              /* ||xPhys - xOld||_2 / sqrt(nEl) */
+    double penal, beta, eta, lm;
+    double rel_res;         /* final FP64 relative residual of the solve */
+    double t_filter_ms, t_solve_ms, t_sens_ms, t_oc_ms;  /* CUDA-event phase times */
+} to_iter_info;
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* to_last_error(void);
+
+/* sizeof(to_params), sizeof(to_state), sizeof(to_iter_info) for binding checks. */
+size_t to_sizeof_params(void);
+size_t to_sizeof_state(void);
+size_t to_sizeof_iter_info(void);
+
+/* Defaults of the paper (Appendix B/C, PRE.1): E0 = 1, Emin = 1e-9, nu = 0.3,
+ * volfrac 0.5, penal 3, rmin 1.5 (2D) / sqrt(3) (3D), ft = 3, 'N', eta 0.5,
+ * beta 2, move 0.2, continuation penal {1, 25, 3, +0.25}, beta {1, 25, 2, +2};
+ * Newton tol 1e-6, bisection tol 1e-4, PCG rtol 1e-8, FP64, Jacobi. p (host out). */
+to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, int32_t nelz);
+
+/* Create a grid handle (Sec. 3 PRE.1-PRE.6): validates p, copies the load F[nDof],
+ * the fixed-DOF mask fixed[nDof] (1 = restrained, Appendix B/C PRE.3) and the
+ * optional passive mask passive[nEl] (0 active, 1 solid P1, -1 void P0; NULL =
+ * all active) into handle-owned device memory, builds Ke (Gauss quadrature of
+ * the Q4 / H8 element, Appendix B/C), the filter window (Eq. 2) and the
+ * normalisation Hs, and allocates the workspaces. `stream` is a cudaStream_t
+ * (NULL = default stream). *out (host out) receives the handle. */
+to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed,
+                       const int8_t* passive, void* stream, to_grid** out);
+
+/* Free the handle and its device memory (NULL is a no-op). */
+void to_destroy(to_grid* g);
+
+/* Current continuation scalars (p of Eq. 5, beta of Eq. 1, eta) used by the
+ * stand-alone entry points below. to_step keeps them in step. */
+to_status to_set_scalars(to_grid* g, double penal, double beta, double eta);
+
+/* Lower triangle K^(s) of the assembled K(xPhys) (Sec. 3.1, Eqs. 10-11) in CSR
+ * with sorted column indices, duplicates summed, fixed DOFs kept.
+ * nnz (host in/out): capacity of col/val in, number of entries out.
+ * row_ptr[nDof+1], col[nnz] int32, val[nnz] FP64 device arrays. With val == NULL
+ * only *nnz is computed. TO_EINVAL if the capacity is too small. */
+to_status to_assemble_lower(to_grid* g, const double* xPhys, int64_t* nnz,
+                            int32_t* row_ptr, int32_t* col, double* val);
+
+/* Matrix-free y = K(xPhys) u (Eqs. 4-5): y = sum_e E_e Ke u_e with
+ * E_e = Emin + xPhys_e^p (E0 - Emin). masked != 0: u at fixed DOFs is treated
+ * as 0 and y at fixed DOFs is 0 (the operator K(free, free) padded with zeros).
+ * u[nDof], y[nDof]; y must not alias u. */
+to_status to_apply_K(to_grid* g, const double* xPhys, const double* u, double* y, int32_t masked);
+
+/* State solve K(xPhys)(free, free) U = F (Eq. 4) by PCG (Jacobi or geometric
+ * multigrid; TO_MIXED: FP32 inner solves with FP64 iterative refinement) to
+ * ||F - K U|| <= cg_rtol ||F|| in FP64. F[nDof] (NULL = the handle's load),
+ * U[nDof]: warm start in, solution out (0 at fixed DOFs). info (host out, may
+ * be NULL). TO_ENOTCONV if cg_maxit is reached (U holds the last iterate). */
+to_status to_solve(to_grid* g, const double* xPhys, const double* F, double* U,
+                   to_solve_info* info);
+
+/* Density filter (Eq. 2, reading: xTilde = (A x) / Hs with A the cone-weight
+ * correlation under 'N' mirror or 'D' zero padding, Hs = A 1).
+ * dprj == NULL: forward out = (A in) / Hs.
+ * dprj != NULL: chain rule out = A^T (dprj * in / Hs) = H^T (dprj * in) (Eq. 7
+ * in the exact order). in[nEl], out[nEl], dprj[nEl]; out must not alias in. */
+to_status to_filter(to_grid* g, const double* in, double* out, const double* dprj);
+
+/* Heaviside projection (Eq. 1) with its derivative (Eq. 8) at the handle's beta:
+ * xPhys = prj(xTilde, eta), dprj = d prj / d xTilde. volume_preserving != 0:
+ * first solve mean(prj(xTilde, eta)) = volfrac for eta by Newton from
+ * *eta_inout (Sec. 3.2, Eq. 15), falling back to bisection on [0, 1].
+ * eta_inout (host in/out). xTilde, xPhys, dprj [nEl]. */
+to_status to_project(to_grid* g, const double* xTilde, double* xPhys, double* dprj,
+                     double* eta_inout, int32_t volume_preserving);
+
+/* Sensitivities (Eq. 6): dc_e = -p (E0 - Emin) xPhys_e^(p-1) u_e^T Ke u_e on
+ * active elements, 0 on passive ones; c_out (host out, may be NULL) = F^T U
+ * with the handle's F. xPhys[nEl], U[nDof], dc[nEl]. */
+to_status to_sensitivity(to_grid* g, const double* xPhys, const double* U, double* dc,
+                         double* c_out);
+
+/* OC update (Eqs. 13-14) of the active design variables in place:
+ * x <- clamp(x sqrt(max(0, -dc/dV0)) / lm, max(0, x - move), min(1, x + move)),
+ * with lm = sqrt(lambda) found by bisection on [0, lambda#] (Eq. 17) until
+ * (l2 - l1)/(l1 + l2) <= oc_tol, testing mean(x) > volfrac. The upper bracket
+ * is doubled while it is still feasible-violating. x[nEl] in/out, dc, dV0 [nEl];
+ * lm_out (host out, may be NULL). */
+to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV0,
+                       double* lm_out);
+
+/* One full design iteration (Sec. 3, RL.1-RL.4): filter, projection with
+ * volume-preserving eta (ft = 3), ch, state solve (warm-started from s->U),
+ * sensitivities, chain rule, OC update and continuation. s (host in/out,
+ * device arrays inside), info (host out, may be NULL). */
+to_status to_step(to_grid* g, to_state* s, to_iter_info* info);
+
+/* Instrumentation (no counterpart in the paper): number of kernels this library
+ * has launched in this process; a CUDA-graph launch counts its kernel nodes. */
+int64_t to_kernel_launches(void);
+
+/* Instrumentation (no counterpart in the paper): average device time in
+ * microseconds (us, host out) of one launch of the matrix-free K u kernel of
+ * `precision` (TO_FP64 or TO_MIXED) at E(xPhys), measured with CUDA events
+ * around `reps` back-to-back launches on the handle's stream, in the launch
+ * configuration the solver uses. */
+to_status to_time_apply_K(to_grid* g, const double* xPhys, int32_t precision, int32_t reps, double* us);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOPOPT_H */

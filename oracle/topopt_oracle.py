@@ -607,7 +607,8 @@ class Params:
     nu: float = 0.3
     penal_cnt: tuple = (1, 3.0, 25, 0.25)
     beta_cnt: tuple = (1, 2.0, 25, 2.0)
-    cnt_kind: str = "add"
+    penal_kind: str = "add"
+    beta_kind: str = "add"
     newton_tol: float = 1e-6
     oc_tol: float = 1e-4
     solver: str = "direct"
@@ -683,8 +684,8 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
     dV0 = filter_backward(g, dV, p.rmin, p.ftBC, dp)
     # RL.4 OC and continuation
     s.x, lm, n_bis = oc_update(s.x, dc, dV0, act, p.move, p.volfrac, p.oc_tol)
-    s.penal = continuation(s.penal, p.penal_cnt, s.loop, p.cnt_kind)
-    s.beta = continuation(s.beta, p.beta_cnt, s.loop, p.cnt_kind)
+    s.penal = continuation(s.penal, p.penal_cnt, s.loop, p.penal_kind)
+    s.beta = continuation(s.beta, p.beta_cnt, s.loop, p.beta_kind)
     info = dict(loop=s.loop, c=c, V=float(np.mean(xphys)), ch=ch, penal=s.penal,
                 beta=s.beta, eta=s.eta, lm=lm, n_newton=n_newton, n_bisect=n_bis,
                 n_cg=n_cg)

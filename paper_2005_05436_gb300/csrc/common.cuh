@@ -1,0 +1,235 @@
+// Shared device infrastructure of the topopt CUDA path (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "topopt.h"
+
+namespace topo {
+
+// ---------------------------------------------------------------- errors --
+
+struct Error : std::runtime_error {
+    to_status code;
+    Error(to_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define TOPO_CUDA(expr)                                                              \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess)                                                       \
+            throw ::topo::Error(_e == cudaErrorMemoryAllocation ? TO_ENOMEM : TO_ECUDA, \
+                                std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// Kernel-launch accounting: every launch site adds its kernel count; kernels
+// enqueued during a graph capture are counted when the graph is launched.
+void count_launches(long long n);
+long long launches_total();
+void set_capturing(bool on);
+
+#define TOPO_CHECK_LAUNCH()             \
+    do {                                \
+        TOPO_CUDA(cudaGetLastError());  \
+        ::topo::count_launches(1);      \
+    } while (0)
+
+#define TOPO_REQUIRE(cond, msg)                                                      \
+    do {                                                                             \
+        if (!(cond)) throw ::topo::Error(TO_EINVAL, msg);                            \
+    } while (0)
+
+// ------------------------------------------------------------ grid sizes --
+
+// Structured-grid dimensions in the paper's numbering (Sec. 3, PRE.2). A 2D grid
+// is stored as nelz = 1, nnz = 1 so that the 3D index formulas reduce to 2D.
+struct Dims {
+    int dim;
+    int nelx, nely, nelz;
+    int nnx, nny, nnz;
+    long long nel, nnodes, ndof;
+};
+
+inline Dims make_dims(int dim, int nelx, int nely, int nelz) {
+    Dims d;
+    d.dim = dim;
+    d.nelx = nelx;
+    d.nely = nely;
+    d.nelz = dim == 3 ? nelz : 1;
+    d.nnx = nelx + 1;
+    d.nny = nely + 1;
+    d.nnz = dim == 3 ? nelz + 1 : 1;
+    d.nel = (long long)d.nelx * d.nely * d.nelz;
+    d.nnodes = (long long)d.nnx * d.nny * d.nnz;
+    d.ndof = d.nnodes * dim;
+    return d;
+}
+
+// Element stiffness matrix as a kernel parameter (constant bank, warp-uniform
+// reads); all indices into it are compile-time constants in the kernels.
+template <typename T, int D>
+struct KeP {
+    T k[D * D];
+};
+
+// Filter window (Eq. 2): nw taps with offsets (ox, oy, oz) and cone weights.
+struct FilterTaps {
+    int nw;
+    const int* off;   // [nw * 3] (ox, oy, oz)
+    const double* w;  // [nw]
+    const float* wf;  // [nw]
+};
+
+__host__ __device__ inline int mirror_index(int j, int n) {
+    // Repeated border-duplicating reflection ('N' padding).
+    int p = 2 * n;
+    int r = j % p;
+    if (r < 0) r += p;
+    return r < n ? r : p - 1 - r;
+}
+
+// ------------------------------------------------------------ reductions --
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of NV values per thread; result valid in thread 0.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV*NT/32 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[k * (NT / 32) + wid] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < NT / 32 ? sm[k * (NT / 32) + lane] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Two-level deterministic reduction inside one launch: every block stores its
+// NV partials, the last block to arrive sums them in block order and returns
+// true with the totals in tot (thread 0 valid). partials: [NV * gridDim.x].
+template <int NT, int NV>
+__device__ bool last_block_totals(double (&v)[NV], double* partials, unsigned* counter,
+                                  double (&tot)[NV]) {
+    __shared__ double sm[NV * NT / 32];
+    __shared__ bool am_last;
+    block_sum<NT, NV>(v, sm);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        s[k] = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) s[k] += __ldcg(&partials[k * gridDim.x + i]);
+    }
+    block_sum<NT, NV>(s, sm);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// --------------------------------------------------------- grid barrier --
+
+// Sense-free generation barrier for cooperative launches. Every wait is bounded
+// by a clock64 deadline; on timeout (or when another block already failed) the
+// error word is set and all blocks return false so the kernel can exit.
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int error;  // 0 ok, TO_ETIMEOUT
+    int pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, long long deadline) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &b->gen;
+        volatile int* verr = &b->error;
+        unsigned my_gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&b->count, 1u);
+        ok = 1;
+        if (arrived == gridDim.x - 1) {
+            b->count = 0u;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*vgen == my_gen) {
+                if (*verr != 0 || clock64() - t0 > deadline) {
+                    atomicExch(&b->error, (int)TO_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Reduction across a cooperative grid: every block ends with the same totals,
+// summed in block order. Uses ping-pong partial buffers (parity) so that the
+// next reduction cannot overwrite partials that a slow block still reads.
+template <int NT, int NV>
+__device__ bool grid_totals(double (&v)[NV], double* partials /* [2][NV][gridDim] */, int parity,
+                            GridBarrier* bar, long long deadline, double (&tot)[NV]) {
+    __shared__ double sm[NV * NT / 32];
+    __shared__ double res[NV];
+    double* P = partials + (size_t)parity * NV * gridDim.x;
+    block_sum<NT, NV>(v, sm);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) P[k * gridDim.x + blockIdx.x] = v[k];
+    }
+    if (!grid_sync(bar, deadline)) return false;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        s[k] = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) s[k] += __ldcg(&P[k * gridDim.x + i]);
+    }
+    block_sum<NT, NV>(s, sm);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) res[k] = s[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = res[k];
+    __syncthreads();
+    return true;
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace topo

@@ -1,0 +1,84 @@
+// The opaque grid handle behind the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "kernels.h"
+
+namespace topo {
+
+// Device-resident scalars read back once per call.
+struct DevScalars {
+    ProjectOut po;
+    OcOut oo;
+    double change[2];  // sum (xPhys - xOld)^2, sum xPhys
+    double c;          // F^T U
+    double esum;       // sum E_e u_e^T Ke u_e
+    long long nnz;
+    PcgScalars pcg;
+    double res[4];     // refinement norms
+};
+
+struct Solver;  // solver.cu
+
+}  // namespace topo
+
+struct to_grid {
+    to_params p;
+    topo::Dims d;
+    int dev = 0, nsm = 0;
+    cudaStream_t ust = nullptr;  // caller's stream
+    cudaStream_t st = nullptr;   // work stream: the caller's, or a private one for NULL
+    bool own_stream = false;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t[5] = {};
+    std::vector<void*> allocs;
+
+    double penal = 3.0, beta = 2.0, eta = 0.5;
+
+    // Ke in the constant bank (kernel parameters) and in device memory
+    topo::KeP<double, 24> ke3{};
+    topo::KeP<double, 8> ke2{};
+    topo::KeP<float, 24> ke3f{};
+    topo::KeP<float, 8> ke2f{};
+    std::vector<double> Ke_host;
+    double* Ke_dev = nullptr;
+
+    // problem data
+    double* F = nullptr;
+    uint8_t* fixed = nullptr;
+    int8_t* passive = nullptr;
+    long long nact = 0, nsolid = 0, nvoid = 0;
+
+    // filter
+    topo::FilterTaps taps{};
+    double Hs_const = 1.0;
+    double* Hs = nullptr;  // 'D' only
+
+    // workspaces
+    double *E = nullptr, *xt = nullptr, *dprj = nullptr, *dc = nullptr, *dcf = nullptr;
+    double *dV = nullptr, *dV0 = nullptr, *ocp = nullptr;
+    float* Ef = nullptr;
+    double* v[7] = {};  // nDof vectors
+    double* partials = nullptr;
+    long long npartials = 0;
+    unsigned* counter = nullptr;
+    topo::GridBarrier* bar = nullptr;
+    topo::GridBarrier hbar{};
+    topo::DevScalars* ds = nullptr;
+    topo::DevScalars* hs = nullptr;  // pinned mirror
+    int proj_blocks = 0, oc_blocks = 0;
+    void* scan_tmp = nullptr;  // CSR assembly scan workspace (lazy)
+
+    topo::Solver* solver = nullptr;
+};
+
+namespace topo {
+void grid_sync_in(to_grid* g);
+void grid_sync_out(to_grid* g);
+void solver_init(to_grid* g);
+void solver_free(to_grid* g);
+// Solve K(E)(free, free) U = b with g->E already set; U: warm start in, solution out.
+to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info);
+// Enqueue `reps` launches of the mixed-precision K u kernel between events e0, e1.
+void time_apply_K_mixed(to_grid* g, const double* xPhys, int reps, cudaEvent_t e0, cudaEvent_t e1);
+}  // namespace topo

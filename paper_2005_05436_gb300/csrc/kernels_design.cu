@@ -1,0 +1,470 @@
+// Design-side kernels: SIMP modulus (Eq. 5), cone-weight density filter and its
+// chain rule (Eqs. 2, 7), Heaviside projection with the volume-preserving eta
+// (Eqs. 1, 8, 15), the OC update with the lambda# bracket (Eqs. 13-14, 17), and
+// the vector kernels of preconditioned CG.
+#include "kernels.h"
+
+namespace topo {
+
+// ------------------------------------------------------------- modulus --
+
+template <typename T>
+__global__ void k_modulus(long long n, const double* __restrict__ x, double penal, double E0,
+                          double Emin, T* __restrict__ E) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) E[i] = (T)(Emin + pow(x[i], penal) * (E0 - Emin));
+}
+
+template <typename T>
+void launch_modulus(long long n, const double* x, double penal, double E0, double Emin, T* E,
+                    cudaStream_t st) {
+    k_modulus<T><<<div_up(n, 256), 256, 0, st>>>(n, x, penal, E0, Emin, E);
+    TOPO_CHECK_LAUNCH();
+}
+template void launch_modulus<double>(long long, const double*, double, double, double, double*, cudaStream_t);
+template void launch_modulus<float>(long long, const double*, double, double, double, float*, cudaStream_t);
+
+// -------------------------------------------------------------- filter --
+
+__global__ void __launch_bounds__(256) k_filter(Dims d, FilterTaps taps, int bcN, const double* __restrict__ Hs,
+                                                double Hs_const, const double* __restrict__ in,
+                                                const double* __restrict__ dprj, double* __restrict__ out,
+                                                const int8_t* __restrict__ passive,
+                                                const double* __restrict__ keep) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.nel) return;
+    const int ey = (int)(e % d.nely);
+    const long long t = e / d.nely;
+    const int ez = (int)(t % d.nelz);
+    const int ex = (int)(t / d.nelz);
+    double s = 0.0;
+    for (int k = 0; k < taps.nw; ++k) {
+        int jx = ex + taps.off[3 * k], jy = ey + taps.off[3 * k + 1], jz = ez + taps.off[3 * k + 2];
+        if (bcN) {
+            jx = mirror_index(jx, d.nelx);
+            jy = mirror_index(jy, d.nely);
+            jz = mirror_index(jz, d.nelz);
+        } else if (jx < 0 || jx >= d.nelx || jy < 0 || jy >= d.nely || jz < 0 || jz >= d.nelz) {
+            continue;
+        }
+        const long long j = jy + (long long)d.nely * (jz + (long long)d.nelz * jx);
+        double v = in[j];
+        if (dprj) v = v * dprj[j] / (Hs ? Hs[j] : Hs_const);
+        s += taps.w[k] * v;
+    }
+    if (!dprj) s = s / (Hs ? Hs[e] : Hs_const);
+    if (passive && passive[e] != 0) s = keep[e];
+    out[e] = s;
+}
+
+void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+                   const double* in, const double* dprj, double* out, const int8_t* passive,
+                   const double* keep, cudaStream_t st) {
+    k_filter<<<div_up(d.nel, 256), 256, 0, st>>>(d, taps, bc == 'N', Hs, Hs_const, in, dprj, out,
+                                                 passive, keep);
+    TOPO_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------- projection --
+
+__device__ __forceinline__ double prj_d(double x, double tb_eta, double den, double beta, double eta) {
+    return (tb_eta + tanh(beta * (x - eta))) / den;
+}
+
+constexpr int PNT = 256;
+
+// Cooperative kernel: every block evaluates the same Newton sequence from the
+// same (deterministically reduced) sums.
+__global__ void __launch_bounds__(PNT) k_project(long long n, const double* __restrict__ xt,
+                                                 double* __restrict__ xphys, double* __restrict__ dprj,
+                                                 double beta, double eta0, double volfrac, int vp,
+                                                 double tol, int maxit, long long deadline,
+                                                 double* partials, GridBarrier* bar, ProjectOut* out) {
+    const long long stride = (long long)gridDim.x * PNT;
+    const long long i0 = (long long)blockIdx.x * PNT + threadIdx.x;
+    const double nd = (double)n;
+    double eta = eta0;
+    int it = 0, parity = 0, status = 0;
+
+    // mean(prj(xt, e)) - volfrac
+    auto gfun = [&](double e, double& f) -> bool {
+        const double tb = tanh(beta * e), den = tb + tanh(beta * (1.0 - e));
+        double v[1] = {0.0}, tot[1];
+        for (long long i = i0; i < n; i += stride) v[0] += prj_d(xt[i], tb, den, beta, e);
+        if (!grid_totals<PNT, 1>(v, partials, parity, bar, deadline, tot)) return false;
+        parity ^= 1;
+        f = tot[0] / nd - volfrac;
+        return true;
+    };
+    // mean(d prj / d eta) = mean(-beta sech^2(beta(x-eta)) sinh(beta x) sinh(beta(1-x)) / sinh(beta))
+    auto dgfun = [&](double e, double& g) -> bool {
+        const double sb = sinh(beta);
+        double v[1] = {0.0}, tot[1];
+        for (long long i = i0; i < n; i += stride) {
+            const double x = xt[i];
+            const double th = tanh(beta * (x - e));
+            v[0] += -beta * (1.0 - th * th) * sinh(beta * x) * sinh(beta * (1.0 - x)) / sb;
+        }
+        if (!grid_totals<PNT, 1>(v, partials, parity, bar, deadline, tot)) return false;
+        parity ^= 1;
+        g = tot[0] / nd;
+        return true;
+    };
+
+    if (vp) {
+        double f;
+        if (!gfun(eta, f)) return;
+        while (fabs(f) > tol && it < maxit) {
+            double g;
+            if (!dgfun(eta, g)) return;
+            eta = eta - f / g;
+            ++it;
+            if (!(eta >= 0.0 && eta <= 1.0)) break;
+            if (!gfun(eta, f)) return;
+        }
+        if (!(fabs(f) <= tol && eta >= 0.0 && eta <= 1.0)) {
+            double lo = 0.0, hi = 1.0;
+            for (int k = 0; k < 200; ++k) {
+                eta = 0.5 * (lo + hi);
+                if (!gfun(eta, f)) return;
+                if (fabs(f) <= tol || hi - lo <= 1e-16) break;
+                if (f > 0.0)
+                    lo = eta;
+                else
+                    hi = eta;
+                ++it;
+            }
+            if (!(fabs(f) <= tol)) status = (int)TO_ENOTCONV;
+        }
+    }
+    const double tb = tanh(beta * eta), den = tb + tanh(beta * (1.0 - eta));
+    for (long long i = i0; i < n; i += stride) {
+        const double x = xt[i];
+        const double th = tanh(beta * (x - eta));
+        xphys[i] = (tb + th) / den;
+        dprj[i] = beta * (1.0 - th * th) / den;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out->eta = eta;
+        out->newton = it;
+        out->status = status;
+    }
+}
+
+int project_max_blocks() {
+    int dev = 0, nsm = 0, per = 0;
+    TOPO_CUDA(cudaGetDevice(&dev));
+    TOPO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    TOPO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_project, PNT, 0));
+    return nsm * (per < 2 ? per : 2);
+}
+
+void launch_project(long long n, const double* xt, double* xphys, double* dprj, double beta,
+                    double eta0, double volfrac, int vp, double tol, int maxit, long long deadline,
+                    double* partials, GridBarrier* bar, ProjectOut* out, int nblocks, cudaStream_t st) {
+    TOPO_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+    void* args[] = {&n, &xt, &xphys, &dprj, &beta, &eta0, &volfrac, &vp, &tol, &maxit, &deadline,
+                    &partials, &bar, &out};
+    TOPO_CUDA(cudaLaunchCooperativeKernel((void*)k_project, dim3(nblocks), dim3(PNT), args, 0, st));
+    count_launches(1);
+}
+
+// ------------------------------------------------------------------ OC --
+
+constexpr int ONT = 256;
+constexpr int OC_DEPTH = 4;                      // bisection levels per pass
+constexpr int OC_NC = (1 << OC_DEPTH) - 1;       // candidates per pass
+
+__global__ void __launch_bounds__(ONT) k_oc(long long n, double* __restrict__ x, const double* __restrict__ dc,
+                                            const double* __restrict__ dV0, const int8_t* __restrict__ passive,
+                                            long long nact, double move, double volfrac, double tol,
+                                            int maxit, long long deadline, double* __restrict__ ocp,
+                                            double* partials, GridBarrier* bar, OcOut* out) {
+    const long long stride = (long long)gridDim.x * ONT;
+    const long long i0 = (long long)blockIdx.x * ONT + threadIdx.x;
+    const double nd = (double)n;
+    int parity = 0;
+
+    // ocP (Eq. 14 without lambda) and the constant passive volume
+    double s2[2] = {0.0, 0.0}, t2[2];
+    for (long long i = i0; i < n; i += stride) {
+        const bool act = !passive || passive[i] == 0;
+        if (act) {
+            const double o = x[i] * sqrt(fmax(0.0, -dc[i] / dV0[i]));
+            ocp[i] = o;
+            s2[0] += o;
+        } else {
+            s2[1] += x[i];
+        }
+    }
+    if (!grid_totals<ONT, 2>(s2, partials, parity, bar, deadline, t2)) return;
+    parity ^= 1;
+    const double pas_sum = t2[1];
+    double l1 = 0.0, l2 = (t2[0] / (double)nact) / volfrac;
+    double lmid = l2;
+    int steps = 0, status = 0;
+
+    auto newx = [&](long long i, double inv_lm) {
+        const double xi = x[i];
+        return fmax(fmax(fmin(fmin(ocp[i] * inv_lm, xi + move), 1.0), xi - move), 0.0);
+    };
+
+    if (l2 > 0.0) {
+        // reading R6: grow the bracket while the volume at l2 is still too large
+        for (int grow = 0; grow < 60; ++grow) {
+            double v[1] = {0.0}, tot[1];
+            const double inv = 1.0 / l2;
+            for (long long i = i0; i < n; i += stride)
+                if (!passive || passive[i] == 0) v[0] += newx(i, inv);
+            if (!grid_totals<ONT, 1>(v, partials, parity, bar, deadline, tot)) return;
+            parity ^= 1;
+            if (!((tot[0] + pas_sum) / nd > volfrac)) break;
+            l1 = l2;
+            l2 = 2.0 * l2;
+        }
+        lmid = l2;
+        // bisection, OC_DEPTH levels per pass: the complete tree of the next
+        // midpoints is evaluated in one sweep and then walked exactly as the
+        // sequential bisection would.
+        while ((l2 - l1) / (l1 + l2) > tol && steps < maxit) {
+            double a[OC_NC], b[OC_NC], c[OC_NC], inv[OC_NC];
+            a[0] = l1;
+            b[0] = l2;
+#pragma unroll
+            for (int k = 0; k < OC_NC; ++k) {
+                c[k] = 0.5 * (a[k] + b[k]);
+                inv[k] = 1.0 / c[k];
+                if (2 * k + 2 < OC_NC) {
+                    a[2 * k + 1] = a[k];
+                    b[2 * k + 1] = c[k];
+                    a[2 * k + 2] = c[k];
+                    b[2 * k + 2] = b[k];
+                }
+            }
+            double v[OC_NC], tot[OC_NC];
+#pragma unroll
+            for (int k = 0; k < OC_NC; ++k) v[k] = 0.0;
+            for (long long i = i0; i < n; i += stride) {
+                if (passive && passive[i] != 0) continue;
+#pragma unroll
+                for (int k = 0; k < OC_NC; ++k) v[k] += newx(i, inv[k]);
+            }
+            if (!grid_totals<ONT, OC_NC>(v, partials, parity, bar, deadline, tot)) return;
+            parity ^= 1;
+            int k = 0;
+            for (int lev = 0; lev < OC_DEPTH; ++lev) {
+                if (!((l2 - l1) / (l1 + l2) > tol && steps < maxit)) break;
+                lmid = c[k];
+                if ((tot[k] + pas_sum) / nd > volfrac) {
+                    l1 = lmid;
+                    k = 2 * k + 2;
+                } else {
+                    l2 = lmid;
+                    k = 2 * k + 1;
+                }
+                ++steps;
+            }
+        }
+        if ((l2 - l1) / (l1 + l2) > tol) status = (int)TO_ENOTCONV;
+        for (long long i = i0; i < n; i += stride) {
+            if (passive && passive[i] != 0) continue;
+            const double xi = x[i];
+            x[i] = fmax(fmax(fmin(fmin(ocp[i] / lmid, xi + move), 1.0), xi - move), 0.0);
+        }
+    } else {
+        lmid = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out->lm = lmid;
+        out->steps = steps;
+        out->status = status;
+    }
+}
+
+int oc_max_blocks() {
+    int dev = 0, nsm = 0, per = 0;
+    TOPO_CUDA(cudaGetDevice(&dev));
+    TOPO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    TOPO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oc, ONT, 0));
+    return nsm * (per < 2 ? per : 2);
+}
+
+void launch_oc(long long n, double* x, const double* dc, const double* dV0, const int8_t* passive,
+               long long nact, double move, double volfrac, double tol, int maxit, long long deadline,
+               double* ocp, double* partials, GridBarrier* bar, OcOut* out, int nblocks,
+               cudaStream_t st) {
+    TOPO_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+    void* args[] = {&n, &x, &dc, &dV0, &passive, &nact, &move, &volfrac, &tol, &maxit, &deadline,
+                    &ocp, &partials, &bar, &out};
+    TOPO_CUDA(cudaLaunchCooperativeKernel((void*)k_oc, dim3(nblocks), dim3(ONT), args, 0, st));
+    count_launches(1);
+}
+
+// ------------------------------------------------------- dots, fills --
+
+constexpr int RNT = 256;
+
+__global__ void __launch_bounds__(RNT) k_dot(long long n, const double* __restrict__ a,
+                                             const double* __restrict__ b, double* out,
+                                             double* partials, unsigned* counter) {
+    double v[1] = {0.0}, tot[1];
+    for (long long i = (long long)blockIdx.x * RNT + threadIdx.x; i < n; i += (long long)gridDim.x * RNT)
+        v[0] += a[i] * (b ? b[i] : a[i]);
+    if (last_block_totals<RNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) out[0] = tot[0];
+}
+
+static int red_blocks(long long n) {
+    int nb = div_up(n, RNT * 4);
+    return nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+}
+
+void launch_dot(long long n, const double* a, const double* b, double* out, double* partials,
+                unsigned* counter, cudaStream_t st) {
+    k_dot<<<red_blocks(n), RNT, 0, st>>>(n, a, b, out, partials, counter);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void __launch_bounds__(RNT) k_change(long long n, const double* __restrict__ a, double* b,
+                                                double* out, int copy, double* partials,
+                                                unsigned* counter) {
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long long i = (long long)blockIdx.x * RNT + threadIdx.x; i < n; i += (long long)gridDim.x * RNT) {
+        const double ai = a[i], di = ai - b[i];
+        v[0] += di * di;
+        v[1] += ai;
+        if (copy) b[i] = ai;
+    }
+    if (last_block_totals<RNT, 2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
+    }
+}
+
+void launch_change(long long n, const double* a, double* b, double* out, int copy, double* partials,
+                   unsigned* counter, cudaStream_t st) {
+    k_change<<<red_blocks(n), RNT, 0, st>>>(n, a, b, out, copy, partials, counter);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void k_fill(long long n, double* a, double v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+void launch_fill(long long n, double* a, double v, cudaStream_t st) {
+    k_fill<<<div_up(n, 256), 256, 0, st>>>(n, a, v);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void k_dv(long long n, const int8_t* passive, double v, double* dV) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dV[i] = (passive && passive[i] != 0) ? 0.0 : v;
+}
+void launch_dv(long long n, const int8_t* passive, double v, double* dV, cudaStream_t st) {
+    k_dv<<<div_up(n, 256), 256, 0, st>>>(n, passive, v, dV);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void k_mask_copy(long long n, const double* __restrict__ in, double* __restrict__ out,
+                            const uint8_t* __restrict__ fixed) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = fixed[i] ? 0.0 : in[i];
+}
+void launch_mask_copy(long long n, const double* in, double* out, const uint8_t* fixed, cudaStream_t st) {
+    k_mask_copy<<<div_up(n, 256), 256, 0, st>>>(n, in, out, fixed);
+    TOPO_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------- PCG --
+
+__global__ void __launch_bounds__(RNT) k_pcg_init(long long n, const double* __restrict__ b,
+                                                  const double* __restrict__ Ax, double* __restrict__ x,
+                                                  double* __restrict__ r, double* __restrict__ z,
+                                                  double* __restrict__ p, const double* __restrict__ dinv,
+                                                  const uint8_t* __restrict__ fixed, PcgScalars* s,
+                                                  double* partials, unsigned* counter) {
+    double v[3] = {0.0, 0.0, 0.0}, tot[3];
+    for (long long i = (long long)blockIdx.x * RNT + threadIdx.x; i < n; i += (long long)gridDim.x * RNT) {
+        const bool f = fixed[i] != 0;
+        const double bi = f ? 0.0 : b[i];
+        const double ri = f ? 0.0 : bi - Ax[i];
+        if (f) x[i] = 0.0;
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+        v[2] += bi * bi;
+    }
+    if (last_block_totals<RNT, 3>(v, partials, counter, tot) && threadIdx.x == 0) {
+        s->rz = tot[0];
+        s->rr = tot[1];
+        s->bb = tot[2];
+        s->iters = 0;
+        s->done = (tot[1] <= s->rtol2 * tot[2]) ? 1 : 0;
+        if (!isfinite(tot[1])) s->done = 3;
+    }
+}
+
+void launch_pcg_init(long long n, const double* b, const double* Ax, double* x, double* r, double* z,
+                     double* p, const double* dinv, const uint8_t* fixed, PcgScalars* s,
+                     double* partials, unsigned* counter, cudaStream_t st) {
+    k_pcg_init<<<red_blocks(n), RNT, 0, st>>>(n, b, Ax, x, r, z, p, dinv, fixed, s, partials, counter);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void __launch_bounds__(RNT) k_pcg_update(long long n, double* __restrict__ x,
+                                                    double* __restrict__ r, double* __restrict__ z,
+                                                    const double* __restrict__ p,
+                                                    const double* __restrict__ Ap,
+                                                    const double* __restrict__ dinv, PcgScalars* s,
+                                                    double* partials, unsigned* counter) {
+    if (s->done) return;
+    const double alpha = s->alpha;
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long long i = (long long)blockIdx.x * RNT + threadIdx.x; i < n; i += (long long)gridDim.x * RNT) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * Ap[i];
+        r[i] = ri;
+        const double zi = dinv[i] * ri;
+        z[i] = zi;
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+    }
+    if (last_block_totals<RNT, 2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        s->iters += 1;
+        s->rr = tot[1];
+        s->rz_new = tot[0];
+        s->beta = tot[0] / s->rz;
+        s->rz = tot[0];
+        if (!isfinite(tot[1]))
+            s->done = 3;
+        else if (tot[1] <= s->rtol2 * s->bb)
+            s->done = 1;
+        else if (s->iters >= s->maxit)
+            s->done = 2;
+    }
+}
+
+void launch_pcg_update(long long n, double* x, double* r, double* z, const double* p, const double* Ap,
+                       const double* dinv, PcgScalars* s, double* partials, unsigned* counter,
+                       cudaStream_t st) {
+    k_pcg_update<<<red_blocks(n), RNT, 0, st>>>(n, x, r, z, p, Ap, dinv, s, partials, counter);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void k_pcg_dir(long long n, const double* __restrict__ z, double* __restrict__ p,
+                          const PcgScalars* s) {
+    if (s->done) return;
+    const double beta = s->beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+void launch_pcg_dir(long long n, const double* z, double* p, const PcgScalars* s, cudaStream_t st) {
+    k_pcg_dir<<<div_up(n, 256), 256, 0, st>>>(n, z, p, s);
+    TOPO_CHECK_LAUNCH();
+}
+
+}  // namespace topo

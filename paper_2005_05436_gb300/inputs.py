@@ -106,6 +106,19 @@ def frame_reinforcement(nelx, nely):
     return F, fixed, passive
 
 
+def initial_design(nel, volfrac, passive=None):
+    """Initial design of the paper's PRE.6: x = (volfrac (nEl - |P0|) - |P1|) / |A|
+    on active elements, 1 on passive solid, 0 on passive void."""
+    if passive is None:
+        return np.full(nel, float(volfrac))
+    pas = np.asarray(passive)
+    nS, nV = int(np.sum(pas == 1)), int(np.sum(pas == -1))
+    x = np.full(nel, (volfrac * (nel - nV) - nS) / (nel - nS - nV))
+    x[pas == 1] = 1.0
+    x[pas == -1] = 0.0
+    return x
+
+
 def random_design(nel, seed, kind="uniform", lo=0.0, hi=1.0):
     """Seeded element field in [lo, hi].
 

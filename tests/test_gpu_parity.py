@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (normwise, ||gpu - oracle|| / ||oracle||): 1e-10 on K u, c and dc,
+1e-12 on filter and projection outputs (same operations, different summation
+order), bit-exact on CSR structure and OC move-limit/box decisions up to
+rounding, 1e-8 on xPhys over 20 design iterations.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import topopt_oracle as O
+from paper_2005_05436_gb300 import inputs as I
+from tests._util import make_grid, problem, rel, simp_field, to_cuda
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(60, 20, 0), (67, 23, 0), (1, 1, 0), (9, 1, 0), (24, 12, 12), (13, 7, 5), (1, 1, 1), (5, 1, 3)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2005_05436_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _xphys(g, seed):
+    return simp_field(g.nel, seed)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("masked", [0, 1])
+def test_apply_K_fp64(shape, masked):
+    g, F, fixed = make_grid(shape, penal=3.0)
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(og.dim)
+    xp = _xphys(g, 1)
+    u = I.random_vector(g.ndof, 2)
+    y = torch.empty(g.ndof, dtype=torch.float64, device="cuda")
+    g.apply_K(to_cuda(xp), to_cuda(u), y, masked=bool(masked))
+    ref = O.apply_K(og, Ke, O.simp_modulus(xp, 3.0), u, fixed if masked else None)
+    assert rel(y.cpu().numpy(), ref) <= 1e-12
+
+
+def test_apply_K_full_size_sampled_rows():
+    """96x48x48 cantilever: sampled rows against element-by-element oracle sums."""
+    shape = (96, 48, 48)
+    g, F, fixed = make_grid(shape, penal=3.0)
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(3)
+    xp = _xphys(g, 3)
+    u = I.random_vector(g.ndof, 4)
+    y = torch.empty(g.ndof, dtype=torch.float64, device="cuda")
+    g.apply_K(to_cuda(xp), to_cuda(u), y, masked=True)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([rng.integers(0, g.ndof, 200), [0, 1, 2, g.ndof - 1, g.ndof - 3]]))
+    ref = O.apply_K_rows(og, Ke, O.simp_modulus(xp, 3.0), u, rows, fixed)
+    got = y.cpu().numpy()[rows]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("shape,rmin,bc", [((60, 20, 0), 2.4, "N"), ((67, 23, 0), 3.3, "D"),
+                                           ((30, 10, 0), 9.0, "N"), ((9, 1, 0), 2.5, "N"),
+                                           ((6, 4, 0), 0.8, "N"), ((24, 12, 12), math.sqrt(3), "N"),
+                                           ((13, 7, 5), 2.2, "D"), ((3, 2, 2), 4.0, "N")])
+def test_filter_forward_backward(shape, rmin, bc):
+    g, F, fixed = make_grid(shape, rmin=rmin, ftBC=bc)
+    og = O.Grid(*shape)
+    x = I.random_design(g.nel, 6)
+    gr = I.random_vector(g.nel, 7)
+    dp = 0.5 + I.random_design(g.nel, 8)
+    out = torch.empty(g.nel, dtype=torch.float64, device="cuda")
+    g.filter(to_cuda(x), out)
+    assert rel(out.cpu().numpy(), O.filter_forward(og, x, rmin, bc)) <= 1e-13
+    g.filter(to_cuda(gr), out, to_cuda(dp))
+    assert rel(out.cpu().numpy(), O.filter_backward(og, gr, rmin, bc, dp)) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (13, 7, 5), (96, 48, 48)])
+@pytest.mark.parametrize("beta,eta0", [(2.0, 0.5), (8.0, 0.3), (16.0, 0.6)])
+def test_project_volume_preserving(shape, beta, eta0):
+    g, F, fixed = make_grid(shape, beta=beta, volfrac=0.4, newton_tol=1e-14)
+    g.set_scalars(3.0, beta, eta0)
+    og = O.Grid(*shape)
+    xt = np.clip(O.filter_forward(og, simp_field(g.nel, 9), 1.5, "N"), 0, 1) if g.nel < 5e4 else \
+        I.random_design(g.nel, 9)
+    xphys = torch.empty(g.nel, dtype=torch.float64, device="cuda")
+    dprj = torch.empty_like(xphys)
+    eta = g.project(to_cuda(xt), xphys, dprj, eta0, True)
+    eta_ref, _ = O.eta_newton(xt, eta0, beta, 0.4, tol=1e-14)
+    assert abs(eta - eta_ref) <= 1e-11
+    assert rel(xphys.cpu().numpy(), O.prj(xt, eta_ref, beta)) <= 1e-11
+    assert rel(dprj.cpu().numpy(), O.dprj(xt, eta_ref, beta)) <= 1e-10
+    assert abs(xphys.mean().item() - 0.4) <= 1e-13
+
+
+def test_project_fixed_eta_and_uniform_field():
+    g, F, fixed = make_grid((20, 10, 0), beta=8.0, volfrac=0.5, newton_tol=1e-14)
+    g.set_scalars(3.0, 8.0, 0.3)
+    xt = np.full(g.nel, 0.5)
+    xphys = torch.empty(g.nel, dtype=torch.float64, device="cuda")
+    dprj = torch.empty_like(xphys)
+    # uniform 0.5 with target 0.5: eta* = 0.5 exactly (Newton leaves [0,1], bisection finds it)
+    eta = g.project(to_cuda(xt), xphys, dprj, 0.3, True)
+    assert abs(eta - 0.5) <= 1e-12
+    x2 = I.random_design(g.nel, 3)
+    eta2 = g.project(to_cuda(x2), xphys, dprj, 0.3, False)
+    assert eta2 == 0.3
+    assert rel(xphys.cpu().numpy(), O.prj(x2, 0.3, 8.0)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (67, 23, 0), (13, 7, 5), (24, 12, 12)])
+def test_sensitivity_and_compliance_at_oracle_U(shape):
+    g, F, fixed = make_grid(shape, penal=3.0)
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(og.dim)
+    # a well-conditioned design: with isolated void elements (mechanisms) u_e^T Ke u_e
+    # is dominated by cancellation noise in any FP64 implementation
+    xp = 0.1 + 0.9 * I.random_design(g.nel, 10)
+    U = O.solve_direct(og, Ke, O.simp_modulus(xp, 3.0), F, fixed)
+    dc_ref, c_ref, _ = O.sensitivity(og, Ke, xp, U, F, 3.0)
+    dc = torch.empty(g.nel, dtype=torch.float64, device="cuda")
+    c = g.sensitivity(to_cuda(xp), to_cuda(U), dc)
+    assert rel(dc.cpu().numpy(), dc_ref) <= 1e-10
+    assert abs(c - c_ref) <= 1e-10 * abs(c_ref)
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (24, 12, 12), (200, 100, 0)])
+@pytest.mark.parametrize("tol", [1e-4, 1e-15])
+def test_oc_update(shape, tol):
+    g, F, fixed = make_grid(shape, volfrac=0.4, oc_tol=tol, move=0.2)
+    n = g.nel
+    rng = np.random.default_rng(11)
+    x = np.clip(0.4 + 0.3 * rng.standard_normal(n), 0.0, 1.0)
+    dc = -np.abs(rng.standard_normal(n)) * 10 ** rng.uniform(-6, 2, n)
+    dV0 = np.full(n, 1.0 / (n * 0.4)) * (1 + 0.1 * rng.random(n))
+    xr, lm_ref, steps = O.oc_update(x, dc, dV0, np.ones(n, bool), 0.2, 0.4, tol=tol)
+    xt = to_cuda(x)
+    lm = g.oc_update(xt, to_cuda(dc), to_cuda(dV0))
+    assert abs(lm - lm_ref) <= max(tol, 1e-14) * 4 * lm_ref
+    assert rel(xt.cpu().numpy(), xr) <= (1e-12 if tol < 1e-10 else 1e-3)
+    if tol < 1e-10:
+        assert abs(xt.mean().item() - 0.4) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (30, 7, 0), (12, 6, 6), (7, 5, 3)])
+def test_solve_against_direct(shape):
+    g, F, fixed = make_grid(shape, penal=3.0, cg_rtol=1e-12, cg_maxit=200000)
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(og.dim)
+    xp = np.clip(simp_field(g.nel, 12), 0.05, 1)
+    Ud = O.solve_direct(og, Ke, O.simp_modulus(xp, 3.0), F, fixed)
+    U = torch.zeros(g.ndof, dtype=torch.float64, device="cuda")
+    info = g.solve(to_cuda(xp), U)
+    assert info.rel_res <= 1e-12
+    assert rel(U.cpu().numpy(), Ud) <= 1e-8
+    c_gpu = float(np.dot(F, U.cpu().numpy()))
+    assert abs(c_gpu - F @ Ud) <= 1e-8 * abs(F @ Ud)
+
+
+@pytest.mark.parametrize("shape", [(6, 4, 0), (13, 7, 0), (3, 2, 2), (5, 4, 3)])
+def test_assemble_lower_csr(shape):
+    g, F, fixed = make_grid(shape, penal=3.0)
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(og.dim)
+    xp = _xphys(g, 13)
+    ref = O.assemble_lower(og, Ke, O.simp_modulus(xp, 3.0))
+    rp, col, val = g.assemble_lower(to_cuda(xp))
+    np.testing.assert_array_equal(rp.cpu().numpy(), ref.indptr)
+    np.testing.assert_array_equal(col.cpu().numpy(), ref.indices)
+    np.testing.assert_allclose(val.cpu().numpy(), ref.data, rtol=0, atol=1e-14 * np.abs(ref.data).max())
+
+
+def _run_parity(shape, n_iter, **kw):
+    from paper_2005_05436_gb300.topopt import Design
+    g, F, fixed = make_grid(shape, **kw)
+    p = g.params
+    op = O.Params.parity(nelx=shape[0], nely=shape[1], nelz=shape[2], volfrac=p.volfrac,
+                         penal=p.penal, rmin=p.rmin, beta=p.beta, eta=p.eta, move=p.move,
+                         ft=p.ft, ftBC=chr(p.ftBC),
+                         penal_cnt=(p.penal_cnt.istart, p.penal_cnt.maxpar, p.penal_cnt.isteps,
+                                    p.penal_cnt.delta),
+                         beta_cnt=(p.beta_cnt.istart, p.beta_cnt.maxpar, p.beta_cnt.isteps,
+                                   p.beta_cnt.delta),
+                         penal_kind="add" if p.penal_cnt.kind == 0 else "mul",
+                         beta_kind="add" if p.beta_cnt.kind == 0 else "mul")
+    s = O.initial_state(op)
+    Ke = O.element_stiffness(3 if shape[2] else 2)
+    d = Design(g, to_cuda(I.initial_design(g.nel, p.volfrac)))
+    worst = 0.0
+    for k in range(n_iter):
+        ref = O.design_step(op, s, F, fixed, None, Ke)
+        got = d.step()
+        assert got["loop"] == ref["loop"]
+        e_x = rel(d.xPhys.cpu().numpy(), s.xphys)
+        worst = max(worst, e_x)
+        assert e_x <= 1e-8, (k, e_x)
+        assert abs(got["c"] - ref["c"]) <= 1e-8 * abs(ref["c"]), (k, got["c"], ref["c"])
+        assert abs(got["eta"] - ref["eta"]) <= 1e-9
+        assert got["penal"] == ref["penal"] and got["beta"] == ref["beta"]
+    return worst
+
+
+def test_design_iterations_mbb_60x20_parity():
+    """Config 1 shape (60x20 MBB, rmin 2.4, ft = 3, beta 2) for 20 iterations."""
+    _run_parity((60, 20, 0), 20, volfrac=0.5, penal=3.0, rmin=2.4, beta=2.0, newton_tol=1e-14,
+                oc_tol=1e-15, cg_rtol=1e-13, cg_maxit=200000)
+
+
+def test_design_iterations_cantilever_parity():
+    _run_parity((12, 6, 6), 20, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0,
+                newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-13, cg_maxit=200000)
+
+
+def test_design_iterations_with_continuation_and_dirichlet_filter():
+    _run_parity((30, 10, 0), 12, volfrac=0.3, penal=1.0, rmin=1.8, beta=2.0, ftBC="D",
+                penal_cnt=(1, 3.0, 4, 0.25), beta_cnt=(1, 16.0, 5, 2.0, 1), newton_tol=1e-14,
+                oc_tol=1e-15, cg_rtol=1e-13, cg_maxit=200000)
+
+
+def test_passive_elements_step():
+    """Passive solid/void sets (frame reinforcement, scaled down)."""
+    from paper_2005_05436_gb300.topopt import Design
+    F, fixed, pas = I.frame_reinforcement(100, 100)
+    g, _, _ = make_grid((100, 100, 0), F=F, fixed=fixed, passive=pas, volfrac=0.2, rmin=4.0,
+                        cg_rtol=1e-10, cg_maxit=200000)
+    x0 = I.initial_design(g.nel, 0.2, pas)
+    d = Design(g, to_cuda(x0))
+    for _ in range(3):
+        info = d.step()
+    x = d.x.cpu().numpy()
+    assert np.all(x[pas == 1] == 1.0) and np.all(x[pas == -1] == 0.0)
+    assert abs(info["V"] - 0.2) < 1e-3
