@@ -222,6 +222,30 @@ to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV
  * device arrays inside), info (host out, may be NULL). */
 to_status to_step(to_grid* g, to_state* s, to_iter_info* info);
 
+/* OC update that allocates no device memory. The paper has no counterpart: this
+ * entry exists for callers that cannot call cudaMalloc, for example a process
+ * whose device memory is already reserved by another allocator (a framework's
+ * caching pool, so cudaMalloc would fail), or a latency-critical loop that must
+ * not take the implicit device synchronisation of cudaMalloc / cudaFree.
+ * It computes exactly what to_oc_update computes, without a grid handle:
+ * x[nel] (device, in/out) is updated from dc[nel], dV0[nel] and the optional
+ * passive[nel] mask (device; NULL = all active) with the given volfrac, move,
+ * oc_tol, oc_maxit and deadline_cycles, on `stream` (a cudaStream_t, NULL =
+ * default stream); lm_out (host out, may be NULL) receives lm = sqrt(lambda).
+ * Scratch: one file-scope device array of 8,651,520 bytes that every GPU which
+ * loads the library holds until the process exits; it bounds nel to
+ * 1,048,576 elements (larger nel returns TO_EINVAL). The array keeps the last
+ * call's contents; the call clears what must start at zero. All calls share
+ * the array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them. The first call on a device resolves the
+ * array's device address with that device current; make that first call
+ * before any stream capture. The call synchronises `stream` before returning.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. */
+to_status to_oc_update_noalloc(int64_t nel, double* x, const double* dc, const double* dV0,
+                               const int8_t* passive, double volfrac, double move, double oc_tol,
+                               int32_t oc_maxit, int64_t deadline_cycles, void* stream,
+                               double* lm_out);
+
 /* Instrumentation (no counterpart in the paper): number of kernels this library
  * has launched in this process; a CUDA-graph launch counts its kernel nodes. */
 int64_t to_kernel_launches(void);

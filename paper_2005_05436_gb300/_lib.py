@@ -85,6 +85,8 @@ _SIGS = {
     "to_sensitivity": (C.c_int, [P, P, P, P, C.POINTER(C.c_double)]),
     "to_oc_update": (C.c_int, [P, P, P, P, C.POINTER(C.c_double)]),
     "to_step": (C.c_int, [P, C.POINTER(State), C.POINTER(IterInfo)]),
+    "to_oc_update_noalloc": (C.c_int, [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
+                                       C.c_int32, C.c_int64, P, C.POINTER(C.c_double)]),
     "to_kernel_launches": (C.c_int64, []),
     "to_time_apply_K": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
 }
