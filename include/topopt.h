@@ -89,6 +89,10 @@ typedef struct to_params {
     int32_t precond;        /* TO_PC_JACOBI or TO_PC_GMG */
     int32_t mg_levels;      /* GMG levels incl. the fine grid, 0 = automatic */
     int64_t deadline_cycles;/* clock64 limit of every device-side wait (2e9) */
+    double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3) */
+    double mg_omega;        /* GMG l1-Jacobi smoother weight (1.0) */
+    int32_t mg_nu;          /* GMG pre- and post-smoothing sweeps per level (2) */
+    int32_t _pad1;
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("newton_tol", C.c_double), ("newton_maxit", C.c_int32), ("oc_maxit", C.c_int32),
                 ("oc_tol", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("mg_levels", C.c_int32),
-                ("deadline_cycles", C.c_int64)]
+                ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
+                ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("_pad1", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -140,6 +140,9 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->precision == TO_FP64 || p->precision == TO_MIXED, "precision");
     TOPO_REQUIRE(p->precond == TO_PC_JACOBI || p->precond == TO_PC_GMG, "precond");
     TOPO_REQUIRE(p->deadline_cycles > 0, "deadline_cycles must be > 0");
+    TOPO_REQUIRE(p->inner_rtol > 0.0 && p->inner_rtol < 1.0, "inner_rtol must be in (0, 1)");
+    TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
+                 "mg_omega in (0, 2), mg_nu in [1, 16]");
     const long long nnodes = (long long)(p->nelx + 1) * (p->nely + 1) * (p->dim == 3 ? p->nelz + 1 : 1);
     TOPO_REQUIRE(nnodes * p->dim < (1LL << 31) - 1, "grid too large for 32-bit DOF indices");
 }
@@ -183,6 +186,9 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->precond = TO_PC_JACOBI;
     p->mg_levels = 0;
     p->deadline_cycles = 2000000000LL;
+    p->inner_rtol = 1e-3;
+    p->mg_omega = 1.0;
+    p->mg_nu = 2;
     return TO_OK;
 }
 

@@ -31,6 +31,7 @@ struct Error : std::runtime_error {
 void count_launches(long long n);
 long long launches_total();
 void set_capturing(bool on);
+long long captured_launches_reset();  // kernels enqueued during captures since the last call
 
 #define TOPO_CHECK_LAUNCH()             \
     do {                                \

@@ -73,6 +73,20 @@ struct to_grid {
 };
 
 namespace topo {
+// Ke kernel parameters of the handle in the arithmetic type T.
+template <typename T>
+inline const KeP<T, 24>& grid_ke3(const to_grid* g);
+template <>
+inline const KeP<double, 24>& grid_ke3<double>(const to_grid* g) { return g->ke3; }
+template <>
+inline const KeP<float, 24>& grid_ke3<float>(const to_grid* g) { return g->ke3f; }
+template <typename T>
+inline const KeP<T, 8>& grid_ke2(const to_grid* g);
+template <>
+inline const KeP<double, 8>& grid_ke2<double>(const to_grid* g) { return g->ke2; }
+template <>
+inline const KeP<float, 8>& grid_ke2<float>(const to_grid* g) { return g->ke2f; }
+
 void grid_sync_in(to_grid* g);
 void grid_sync_out(to_grid* g);
 void solver_init(to_grid* g);

@@ -9,9 +9,18 @@ namespace topo {
 
 static std::atomic<long long> g_launches{0};
 static thread_local bool g_capturing = false;
+static thread_local long long g_captured = 0;
 
 void count_launches(long long n) {
-    if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+    if (g_capturing)
+        g_captured += n;
+    else
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+long long captured_launches_reset() {
+    const long long c = g_captured;
+    g_captured = 0;
+    return c;
 }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 void set_capturing(bool on) { g_capturing = on; }

@@ -8,45 +8,9 @@
 // exactly one thread (no atomics, deterministic), and all Ke indices are
 // compile-time constants so Ke is read from the constant bank.
 #include "kernels.h"
+#include "ku_device.cuh"
 
 namespace topo {
-
-// Local node index of the corner (ax, ay, az) of the unit element, ay = 1 for
-// the top row (physical Y up): (0,0,0) (1,0,0) (1,1,0) (0,1,0), then z = 1.
-__host__ __device__ constexpr int local_node(int ax, int ay, int az) {
-    return 4 * az + (ay ? (ax ? 2 : 3) : (ax ? 1 : 0));
-}
-__host__ __device__ constexpr int lnx(int M) { return ((M & 3) == 1 || (M & 3) == 2) ? 1 : 0; }
-__host__ __device__ constexpr int lny(int M) { return (M & 3) >= 2 ? 1 : 0; }
-__host__ __device__ constexpr int lnz(int M) { return M >> 2; }
-
-// ------------------------------------------------------------ 3D (H8) K u --
-
-template <typename T, int EXO, int EYO, int EZO>
-__device__ __forceinline__ void ku3_elem(const KeP<T, 24>& ke, const T* __restrict__ E,
-                                         const T* __restrict__ u, long long n, int ix, int iy, int iz,
-                                         const Dims& d, long long sz, long long sx, T& a0, T& a1,
-                                         T& a2) {
-    const int ex = ix - 1 + EXO, ey = iy - 1 + EYO, ez = iz - 1 + EZO;
-    if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) return;
-    const T Ee = E[ey + (long long)d.nely * (ez + (long long)d.nelz * ex)];
-    constexpr int L = local_node(1 - EXO, EYO, 1 - EZO);
-    T t0 = T(0), t1 = T(0), t2 = T(0);
-#pragma unroll
-    for (int M = 0; M < 8; ++M) {
-        const long long m = n + (EYO - lny(M)) + sz * (EZO - 1 + lnz(M)) + sx * (EXO - 1 + lnx(M));
-        const T u0 = u[3 * m], u1 = u[3 * m + 1], u2 = u[3 * m + 2];
-        t0 += ke.k[(3 * L + 0) * 24 + 3 * M + 0] * u0 + ke.k[(3 * L + 0) * 24 + 3 * M + 1] * u1 +
-              ke.k[(3 * L + 0) * 24 + 3 * M + 2] * u2;
-        t1 += ke.k[(3 * L + 1) * 24 + 3 * M + 0] * u0 + ke.k[(3 * L + 1) * 24 + 3 * M + 1] * u1 +
-              ke.k[(3 * L + 1) * 24 + 3 * M + 2] * u2;
-        t2 += ke.k[(3 * L + 2) * 24 + 3 * M + 0] * u0 + ke.k[(3 * L + 2) * 24 + 3 * M + 1] * u1 +
-              ke.k[(3 * L + 2) * 24 + 3 * M + 2] * u2;
-    }
-    a0 += Ee * t0;
-    a1 += Ee * t1;
-    a2 += Ee * t2;
-}
 
 template <typename T, bool PCG>
 __global__ void __launch_bounds__(256) k_apply_K3(Dims d, const KeP<T, 24> ke, const T* __restrict__ E,
@@ -57,20 +21,8 @@ __global__ void __launch_bounds__(256) k_apply_K3(Dims d, const KeP<T, 24> ke, c
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double dot = 0.0;
     if (n < d.nnodes) {
-        const long long sz = d.nny, sx = (long long)d.nny * d.nnz;
-        const int iy = (int)(n % d.nny);
-        const long long t = n / d.nny;
-        const int iz = (int)(t % d.nnz);
-        const int ix = (int)(t / d.nnz);
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        ku3_elem<T, 0, 0, 0>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 0, 1, 0>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 0, 0, 1>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 0, 1, 1>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 1, 0, 0>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 1, 1, 0>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 1, 0, 1>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
-        ku3_elem<T, 1, 1, 1>(ke, E, u, n, ix, iy, iz, d, sz, sx, a0, a1, a2);
+        T a0, a1, a2;
+        ku3_node<T, true>(ke, E, u, n, d, a0, a1, a2);
         if (mask_out) {
             if (fixed[3 * n + 0]) a0 = T(0);
             if (fixed[3 * n + 1]) a1 = T(0);
@@ -92,26 +44,6 @@ __global__ void __launch_bounds__(256) k_apply_K3(Dims d, const KeP<T, 24> ke, c
 
 // ------------------------------------------------------------ 2D (Q4) K u --
 
-template <typename T, int EXO, int EYO>
-__device__ __forceinline__ void ku2_elem(const KeP<T, 8>& ke, const T* __restrict__ E,
-                                         const T* __restrict__ u, long long n, int ix, int iy,
-                                         const Dims& d, long long sx, T& a0, T& a1) {
-    const int ex = ix - 1 + EXO, ey = iy - 1 + EYO;
-    if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely) return;
-    const T Ee = E[ey + (long long)d.nely * ex];
-    constexpr int L = local_node(1 - EXO, EYO, 0);
-    T t0 = T(0), t1 = T(0);
-#pragma unroll
-    for (int M = 0; M < 4; ++M) {
-        const long long m = n + (EYO - lny(M)) + sx * (EXO - 1 + lnx(M));
-        const T u0 = u[2 * m], u1 = u[2 * m + 1];
-        t0 += ke.k[(2 * L + 0) * 8 + 2 * M] * u0 + ke.k[(2 * L + 0) * 8 + 2 * M + 1] * u1;
-        t1 += ke.k[(2 * L + 1) * 8 + 2 * M] * u0 + ke.k[(2 * L + 1) * 8 + 2 * M + 1] * u1;
-    }
-    a0 += Ee * t0;
-    a1 += Ee * t1;
-}
-
 template <typename T, bool PCG>
 __global__ void __launch_bounds__(256) k_apply_K2(Dims d, const KeP<T, 8> ke, const T* __restrict__ E,
                                                   const T* __restrict__ u, T* __restrict__ y,
@@ -121,14 +53,8 @@ __global__ void __launch_bounds__(256) k_apply_K2(Dims d, const KeP<T, 8> ke, co
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double dot = 0.0;
     if (n < d.nnodes) {
-        const long long sx = d.nny;
-        const int iy = (int)(n % d.nny);
-        const int ix = (int)(n / d.nny);
-        T a0 = T(0), a1 = T(0);
-        ku2_elem<T, 0, 0>(ke, E, u, n, ix, iy, d, sx, a0, a1);
-        ku2_elem<T, 0, 1>(ke, E, u, n, ix, iy, d, sx, a0, a1);
-        ku2_elem<T, 1, 0>(ke, E, u, n, ix, iy, d, sx, a0, a1);
-        ku2_elem<T, 1, 1>(ke, E, u, n, ix, iy, d, sx, a0, a1);
+        T a0, a1;
+        ku2_node<T, true>(ke, E, u, n, d, a0, a1);
         if (mask_out) {
             if (fixed[2 * n + 0]) a0 = T(0);
             if (fixed[2 * n + 1]) a1 = T(0);

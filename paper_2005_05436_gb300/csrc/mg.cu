@@ -1,0 +1,734 @@
+// Geometric multigrid: fine-level fused operators, Galerkin coarsening, node
+// stencils, transfer operators, coarsest dense inverse and the V-cycle.
+#include <algorithm>
+#include <cmath>
+
+#include "grid.h"
+#include "ku_device.cuh"
+#include "mg.h"
+
+namespace topo {
+
+// Operators take displacements relative to the centre node (see ku_device.cuh).
+template <typename T>
+__host__ __device__ constexpr bool rel_form() { return true; }
+
+// ------------------------------------------------------ fine level (matrix-free)
+
+template <typename T, int MODE, bool PCG>
+__global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, const T* __restrict__ E,
+                                                  const T* __restrict__ u, const T* __restrict__ r,
+                                                  const T* __restrict__ dinv, T* __restrict__ out,
+                                                  const uint8_t* __restrict__ fixed, T omega,
+                                                  const int* skip, PcgScalars* pcg, double* partials,
+                                                  unsigned* counter) {
+    if (skip && *skip) return;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double dot = 0.0;
+    if (n < d.nnodes) {
+        T a[3];
+        ku3_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1], a[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long i = 3 * n + c;
+            T o = a[c];
+            if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a[c]);
+            if (MODE == 2) o = r[i] - a[c];
+            if (fixed[i]) o = T(0);
+            out[i] = o;
+            if (PCG) dot += (double)u[i] * (double)o;
+        }
+    }
+    if (PCG) {
+        double v[1] = {dot}, tot[1];
+        if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+            pcg->pAp = tot[0];
+            pcg->alpha = pcg->rz / tot[0];
+        }
+    }
+}
+
+template <typename T, int MODE, bool PCG>
+__global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, const T* __restrict__ E,
+                                                  const T* __restrict__ u, const T* __restrict__ r,
+                                                  const T* __restrict__ dinv, T* __restrict__ out,
+                                                  const uint8_t* __restrict__ fixed, T omega,
+                                                  const int* skip, PcgScalars* pcg, double* partials,
+                                                  unsigned* counter) {
+    if (skip && *skip) return;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double dot = 0.0;
+    if (n < d.nnodes) {
+        T a[2];
+        ku2_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const long long i = 2 * n + c;
+            T o = a[c];
+            if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a[c]);
+            if (MODE == 2) o = r[i] - a[c];
+            if (fixed[i]) o = T(0);
+            out[i] = o;
+            if (PCG) dot += (double)u[i] * (double)o;
+        }
+    }
+    if (PCG) {
+        double v[1] = {dot}, tot[1];
+        if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+            pcg->pAp = tot[0];
+            pcg->alpha = pcg->rz / tot[0];
+        }
+    }
+}
+
+template <typename T, int MODE, bool PCG>
+static void fine_op_dispatch(const to_grid* g, const T* E, const T* u, const T* r, const T* dinv, T* out,
+                             T omega, const int* skip, PcgScalars* pcg, cudaStream_t st) {
+    const Dims& d = g->d;
+    const int nb = div_up(d.nnodes, 256);
+    if (d.dim == 3)
+        k_fine_op3<T, MODE, PCG><<<nb, 256, 0, st>>>(d, grid_ke3<T>(g), E, u, r, dinv, out, g->fixed, omega,
+                                                     skip, pcg, g->partials, g->counter);
+    else
+        k_fine_op2<T, MODE, PCG><<<nb, 256, 0, st>>>(d, grid_ke2<T>(g), E, u, r, dinv, out, g->fixed, omega,
+                                                     skip, pcg, g->partials, g->counter);
+    TOPO_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_fine_op(const to_grid* g, int mode, const T* E, const T* u, const T* r, const T* dinv, T* out,
+                    T omega, const int* skip, PcgScalars* pcg, cudaStream_t st) {
+    if (mode == 0 && pcg)
+        fine_op_dispatch<T, 0, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
+    else if (mode == 0)
+        fine_op_dispatch<T, 0, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
+    else if (mode == 1)
+        fine_op_dispatch<T, 1, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
+    else
+        fine_op_dispatch<T, 2, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
+}
+template void launch_fine_op<double>(const to_grid*, int, const double*, const double*, const double*,
+                                     const double*, double*, double, const int*, PcgScalars*, cudaStream_t);
+template void launch_fine_op<float>(const to_grid*, int, const float*, const float*, const float*,
+                                    const float*, float*, float, const int*, PcgScalars*, cudaStream_t);
+
+// ------------------------------------------------------------ Galerkin
+
+// Weight of coarse corner B at the position of child j's corner b (trilinear /
+// bilinear interpolation; positions in half-element units 0, 1, 2).
+template <int DIM>
+__device__ __forceinline__ float pn_weight(int j, int b, int B) {
+    float w = 1.f;
+    const int p[3] = {lnx(j) + lnx(b), lny(j) + lny(b), lnz(j) + lnz(b)};
+    const int q[3] = {lnx(B), lny(B), lnz(B)};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) w *= q[a] ? 0.5f * p[a] : 0.5f * (2 - p[a]);
+    return w;
+}
+
+// One CTA per coarse element: Kc = sum_j P_j^T K_j P_j over the children j.
+// FROM_FINE: K_j = M_j (E_j Ke) M_j with M_j zeroing fine Dirichlet DOFs.
+template <typename T, int DIM, bool FROM_FINE>
+__global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __restrict__ Ef,
+                                                  const double* __restrict__ Ke, const T* __restrict__ Kf,
+                                                  const uint8_t* __restrict__ fixed_f, T* __restrict__ Kc) {
+    constexpr int NN = DIM == 3 ? 8 : 4, D = DIM * NN, DD = D * D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ks = (T*)smem_raw;  // [NN children][D*D]
+    T* Ts = Ks + NN * DD;  // [NN children][NN a][NN B][DIM][DIM]
+    const long long ec = blockIdx.x;
+    const int ey = (int)(ec % dc.nely);
+    const long long t0 = ec / dc.nely;
+    const int ez = (int)(t0 % dc.nelz);
+    const int ex = (int)(t0 / dc.nelz);
+    for (int idx = threadIdx.x; idx < NN * DD; idx += blockDim.x) {
+        const int j = idx / DD, rem = idx % DD, row = rem / D, col = rem % D;
+        const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j)), ezf = DIM == 3 ? 2 * ez + lnz(j) : 0;
+        const long long ef = eyf + (long long)df.nely * (ezf + (long long)df.nelz * exf);
+        T v;
+        if (FROM_FINE) {
+            const int a = row / DIM, c = row % DIM, b = col / DIM, k = col % DIM;
+            const long long na = (eyf + 1 - lny(a)) + (long long)df.nny * ((ezf + lnz(a)) + (long long)df.nnz * (exf + lnx(a)));
+            const long long nb = (eyf + 1 - lny(b)) + (long long)df.nny * ((ezf + lnz(b)) + (long long)df.nnz * (exf + lnx(b)));
+            const bool masked = fixed_f[DIM * na + c] || fixed_f[DIM * nb + k];
+            v = masked ? T(0) : (T)((double)Ef[ef] * Ke[rem]);
+        } else {
+            v = Kf[ef * DD + rem];
+        }
+        Ks[idx] = v;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NN * NN * NN * DIM * DIM; idx += blockDim.x) {
+        const int k = idx % DIM, c = (idx / DIM) % DIM, B = (idx / (DIM * DIM)) % NN,
+                  a = (idx / (DIM * DIM * NN)) % NN, j = idx / (DIM * DIM * NN * NN);
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < NN; ++b) s += Ks[j * DD + (a * DIM + c) * D + b * DIM + k] * (T)pn_weight<DIM>(j, b, B);
+        Ts[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < DD; idx += blockDim.x) {
+        const int row = idx / D, col = idx % D, A = row / DIM, c = row % DIM, B = col / DIM, k = col % DIM;
+        T s = T(0);
+        for (int j = 0; j < NN; ++j)
+#pragma unroll
+            for (int a = 0; a < NN; ++a)
+                s += (T)pn_weight<DIM>(j, a, A) * Ts[(((j * NN + a) * NN + B) * DIM + c) * DIM + k];
+        Kc[ec * DD + idx] = s;
+    }
+}
+
+// Level-0 element matrices E_e Ke (only for a dense solve of a tiny fine grid).
+template <typename T, int DIM>
+__global__ void k_elem_from_E(Dims d, const T* __restrict__ E, const double* __restrict__ Ke, T* __restrict__ Kel) {
+    constexpr int D = DIM == 3 ? 24 : 8, DD = D * D;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.nel * DD) return;
+    Kel[i] = (T)((double)E[i / DD] * Ke[i % DD]);
+}
+
+// ------------------------------------------------------------- stencils
+
+template <int DIM>
+__host__ __device__ constexpr int n_stencil() { return DIM == 3 ? 27 : 9; }
+
+// Node stencil S[n][s] = sum over the elements containing n and n + s of the
+// element-matrix block (n, n + s); R[n] = sum_s S[n][s]. SoA layout.
+template <typename T, int DIM>
+__global__ void k_stencil_build(Dims d, const T* __restrict__ Kel, T* __restrict__ S, T* __restrict__ R) {
+    constexpr int NS = n_stencil<DIM>(), D = DIM == 3 ? 24 : 8, DD = D * D, Q = DIM * DIM;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+    const int iy = (int)(n % d.nny);
+    const long long t = n / d.nny;
+    const int iz = (int)(t % d.nnz);
+    const int ix = (int)(t / d.nnz);
+    T rs[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) rs[q] = T(0);
+    for (int s = 0; s < NS; ++s) {
+        const int dx = DIM == 3 ? s / 9 - 1 : s / 3 - 1;
+        const int dz = DIM == 3 ? (s / 3) % 3 - 1 : 0;
+        const int dy = s % 3 - 1;
+        const int mx = ix + dx, my = iy + dy, mz = iz + dz;
+        T blk[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) blk[q] = T(0);
+        if (mx >= 0 && mx < d.nnx && my >= 0 && my < d.nny && mz >= 0 && mz < d.nnz) {
+            for (int o = 0; o < (DIM == 3 ? 8 : 4); ++o) {
+                const int exo = DIM == 3 ? (o >> 2) & 1 : (o >> 1) & 1, ezo = DIM == 3 ? (o >> 1) & 1 : 1,
+                          eyo = o & 1;
+                const int ex = ix - 1 + exo, ey = iy - 1 + eyo, ez = DIM == 3 ? iz - 1 + ezo : 0;
+                if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) continue;
+                const int bx = mx - ex, brow = my - ey, bz = mz - ez;
+                if (bx < 0 || bx > 1 || brow < 0 || brow > 1 || bz < 0 || bz > 1) continue;
+                const int Ln = local_node(1 - exo, eyo, DIM == 3 ? 1 - ezo : 0);
+                const int Lm = local_node(bx, 1 - brow, bz);
+                const T* Ke = Kel + (ey + (long long)d.nely * (ez + (long long)d.nelz * ex)) * DD;
+#pragma unroll
+                for (int c = 0; c < DIM; ++c)
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) blk[c * DIM + k] += Ke[(Ln * DIM + c) * D + Lm * DIM + k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            S[((long long)s * Q + q) * d.nnodes + n] = blk[q];
+            rs[q] += blk[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) R[(long long)q * d.nnodes + n] = rs[q];
+}
+
+// l1-Jacobi smoother weights: dinv = 1 / sum_j |A_ij| (row sums of absolute
+// values), so that lambda_max(D^-1 A) <= 1 (Gershgorin) for any modulus
+// contrast and the damped sweep contracts; coarse DOFs whose diagonal is zero
+// (all their fine DOFs are fixed) become fixed.
+template <typename T, int DIM>
+__global__ void k_stencil_diag(Dims d, const T* __restrict__ S, T* __restrict__ dinv, uint8_t* __restrict__ fixed) {
+    constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        const T diag = S[((long long)(NS / 2) * Q + c * DIM + c) * d.nnodes + n];
+        T l1 = T(0);
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) l1 += fabs(S[((long long)s * Q + c * DIM + k) * d.nnodes + n]);
+        const bool f = !(diag > T(0));
+        fixed[DIM * n + c] = f;
+        dinv[DIM * n + c] = f ? T(0) : T(1) / l1;
+    }
+}
+
+// Level 0: l1 row sums sum_e E_e sum_j |Ke[row, j]| from the per-row absolute
+// sums of Ke (arow); 0 at fixed DOFs.
+template <typename T, int DIM>
+struct RowAbs {
+    T a[DIM == 3 ? 24 : 8];
+};
+
+template <typename T, int DIM>
+__global__ void k_l1_inv(Dims d, const RowAbs<T, DIM> ra, const T* __restrict__ E, const uint8_t* __restrict__ fixed,
+                         T* __restrict__ dinv) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+    const int iy = (int)(n % d.nny);
+    const long long t = n / d.nny;
+    const int iz = (int)(t % d.nnz);
+    const int ix = (int)(t / d.nnz);
+    T acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int exo = (o >> 2) & 1, ezo = (o >> 1) & 1, eyo = o & 1;
+        if (DIM == 2 && ezo) continue;
+        const int ex = ix - 1 + exo, ey = iy - 1 + eyo, ez = DIM == 3 ? iz - 1 + ezo : 0;
+        if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) continue;
+        const T Ee = E[ey + (long long)d.nely * (ez + (long long)d.nelz * ex)];
+        const int L = local_node(1 - exo, eyo, DIM == 3 ? 1 - ezo : 0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += Ee * ra.a[DIM * L + c];
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dinv[DIM * n + c] = fixed[DIM * n + c] ? T(0) : T(1) / acc[c];
+}
+
+// Coarse-level operator: modes as the fine level. FP32 uses the relative form
+// sum_{m != n} S_nm (u_m - u_n) + R_n u_n (exact rewriting of sum_m S_nm u_m).
+template <typename T, int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict__ S, const T* __restrict__ R,
+                                                    const T* __restrict__ u, const T* __restrict__ r,
+                                                    const T* __restrict__ dinv, T* __restrict__ out,
+                                                    const uint8_t* __restrict__ fixed, T omega,
+                                                    const int* skip) {
+    constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
+    constexpr bool REL = rel_form<T>();
+    if (skip && *skip) return;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+    const int iy = (int)(n % d.nny);
+    const long long t = n / d.nny;
+    const int iz = (int)(t % d.nnz);
+    const int ix = (int)(t / d.nnz);
+    T uc[DIM], acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) uc[c] = u[DIM * n + c];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        acc[c] = T(0);
+        if (REL) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) acc[c] += R[(long long)(c * DIM + k) * d.nnodes + n] * uc[k];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (REL && s == NS / 2) continue;
+        const int dx = DIM == 3 ? s / 9 - 1 : s / 3 - 1;
+        const int dz = DIM == 3 ? (s / 3) % 3 - 1 : 0;
+        const int dy = s % 3 - 1;
+        const int mx = ix + dx, my = iy + dy, mz = iz + dz;
+        if (mx < 0 || mx >= d.nnx || my < 0 || my >= d.nny || mz < 0 || mz >= d.nnz) continue;
+        const long long m = my + (long long)d.nny * (mz + (long long)d.nnz * mx);
+        T um[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) um[k] = REL ? u[DIM * m + k] - uc[k] : u[DIM * m + k];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) acc[c] += S[((long long)s * Q + c * DIM + k) * d.nnodes + n] * um[k];
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        const long long i = DIM * n + c;
+        T o = acc[c];
+        if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - acc[c]);
+        if (MODE == 2) o = r[i] - acc[c];
+        if (fixed[i]) o = T(0);
+        out[i] = o;
+    }
+}
+
+// ------------------------------------------------------- transfer operators
+
+template <typename T, int DIM>
+__global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __restrict__ rc,
+                           const uint8_t* __restrict__ fixed_c, const int* skip) {
+    if (skip && *skip) return;
+    const long long N = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (N >= dc.nnodes) return;
+    const int NY = (int)(N % dc.nny);
+    const long long t = N / dc.nny;
+    const int NZ = (int)(t % dc.nnz);
+    const int NX = (int)(t / dc.nnz);
+    T acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+    for (int ox = -1; ox <= 1; ++ox)
+        for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
+            for (int oy = -1; oy <= 1; ++oy) {
+                const int fx = 2 * NX + ox, fy = 2 * NY + oy, fz = DIM == 3 ? 2 * NZ + oz : 0;
+                if (fx < 0 || fx >= df.nnx || fy < 0 || fy >= df.nny || fz < 0 || fz >= df.nnz) continue;
+                const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+                const long long f = fy + (long long)df.nny * (fz + (long long)df.nnz * fx);
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) acc[c] += w * rf[DIM * f + c];
+            }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) rc[DIM * N + c] = fixed_c[DIM * N + c] ? T(0) : acc[c];
+}
+
+template <typename T, int DIM>
+__global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __restrict__ zf,
+                              const uint8_t* __restrict__ fixed_f, const int* skip) {
+    if (skip && *skip) return;
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= df.nnodes) return;
+    const int fy = (int)(f % df.nny);
+    const long long t = f / df.nny;
+    const int fz = (int)(t % df.nnz);
+    const int fx = (int)(t / df.nnz);
+    T acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+    const int nx = (fx & 1) ? 2 : 1, ny = (fy & 1) ? 2 : 1, nz = (fz & 1) ? 2 : 1;
+    for (int a = 0; a < nx; ++a)
+        for (int b = 0; b < nz; ++b)
+            for (int e = 0; e < ny; ++e) {
+                const int NX = (fx >> 1) + a, NZ = (fz >> 1) + b, NY = (fy >> 1) + e;
+                const T w = (nx == 2 ? T(0.5) : T(1)) * (ny == 2 ? T(0.5) : T(1)) * (nz == 2 ? T(0.5) : T(1));
+                const long long N = NY + (long long)dc.nny * (NZ + (long long)dc.nnz * NX);
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * N + c];
+            }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+        if (!fixed_f[DIM * f + c]) zf[DIM * f + c] += acc[c];
+}
+
+template <typename T>
+__global__ void k_jacobi_first(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
+                               T omega, const int* skip) {
+    if (skip && *skip) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = omega * dinv[i] * r[i];
+}
+
+// ------------------------------------------------------- coarsest level
+
+template <typename T, int DIM>
+__global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const uint8_t* __restrict__ fixed, double* __restrict__ A) {
+    constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+    const long long nc = d.ndof;
+    const int iy = (int)(n % d.nny);
+    const long long t = n / d.nny;
+    const int iz = (int)(t % d.nnz);
+    const int ix = (int)(t / d.nnz);
+    for (int c = 0; c < DIM; ++c) {
+        const long long i = DIM * n + c;
+        double* row = A + i * nc;
+        for (long long j = 0; j < nc; ++j) row[j] = 0.0;
+        if (fixed[i]) {
+            row[i] = 1.0;
+            continue;
+        }
+        for (int s = 0; s < NS; ++s) {
+            const int dx = DIM == 3 ? s / 9 - 1 : s / 3 - 1;
+            const int dz = DIM == 3 ? (s / 3) % 3 - 1 : 0;
+            const int dy = s % 3 - 1;
+            const int mx = ix + dx, my = iy + dy, mz = iz + dz;
+            if (mx < 0 || mx >= d.nnx || my < 0 || my >= d.nny || mz < 0 || mz >= d.nnz) continue;
+            const long long m = my + (long long)d.nny * (mz + (long long)d.nnz * mx);
+            for (int k = 0; k < DIM; ++k)
+                if (!fixed[DIM * m + k]) row[DIM * m + k] = (double)S[((long long)s * Q + c * DIM + k) * d.nnodes + n];
+        }
+    }
+}
+
+// Right-looking Cholesky of the lower triangle of A (row-major, in place) by
+// one CTA. A non-positive pivot is replaced by a tiny positive one and flagged.
+__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, int* status) {
+    __shared__ double piv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) *status = 0;
+    for (int k = 0; k < n; ++k) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double p = A[(long long)k * n + k];
+            if (!(p > 0.0)) {
+                *status = 1;
+                p = 1e-300;
+            }
+            piv = sqrt(p);
+            A[(long long)k * n + k] = piv;
+        }
+        __syncthreads();
+        const double L = piv;
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + k] /= L;
+        __syncthreads();
+        for (int i = k + 1 + warp; i < n; i += nw) {
+            const double aik = A[(long long)i * n + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) A[(long long)i * n + j] -= aik * A[(long long)j * n + k];
+        }
+    }
+}
+
+// Column j of A^{-1} = L^{-T} L^{-1} e_j by one warp; fixed rows/cols are zero.
+template <typename T>
+__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __restrict__ work,
+                               const uint8_t* __restrict__ fixed, T* __restrict__ Ainv) {
+    const int lane = threadIdx.x & 31;
+    const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= n) return;
+    double* y = work + j * n;
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = lane; k < i; k += 32) s += L[(long long)i * n + k] * y[k];
+        s = warp_sum(s);
+        if (lane == 0) y[i] = ((i == j ? 1.0 : 0.0) - s) / L[(long long)i * n + i];
+        __syncwarp();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < n; k += 32) s += L[(long long)k * n + i] * y[k];
+        s = warp_sum(s);
+        if (lane == 0) y[i] = (y[i] - s) / L[(long long)i * n + i];
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32)
+        Ainv[(long long)i * n + j] = (fixed[i] || fixed[j]) ? T(0) : (T)y[i];
+}
+
+template <typename T>
+__global__ void k_dense_apply(int n, const T* __restrict__ Ainv, const T* __restrict__ r, T* __restrict__ z,
+                              const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32) s += (double)Ainv[i * n + k] * (double)r[k];
+    s = warp_sum(s);
+    if (lane == 0) z[i] = (T)s;
+}
+
+// ------------------------------------------------------------ host side
+
+static constexpr long long DENSE_MAX = 2048;
+static constexpr long long COARSE_TARGET = 1500;
+
+template <typename U, typename T>
+static U* mg_alloc(MG<T>* mg, size_t bytes) {
+    void* p = nullptr;
+    TOPO_CUDA(cudaMalloc(&p, bytes + 16));
+    mg->allocs.push_back(p);
+    return (U*)p;
+}
+
+template <typename T>
+MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
+    MG<T>* mg = new MG<T>();
+    try {
+        mg->nu = nu;
+        mg->omega = (T)omega;
+        Dims d = g->d;
+        const int dim = d.dim;
+        mg->lev.push_back(MGLevel<T>());
+        mg->lev[0].d = d;
+        for (;;) {
+            const Dims& c = mg->lev.back().d;
+            const bool even = c.nelx % 2 == 0 && c.nely % 2 == 0 && (dim == 2 || c.nelz % 2 == 0);
+            if (!even || c.ndof <= COARSE_TARGET) break;
+            if (max_levels > 0 && (int)mg->lev.size() >= max_levels) break;
+            MGLevel<T> L;
+            L.d = make_dims(dim, c.nelx / 2, c.nely / 2, dim == 3 ? c.nelz / 2 : 0);
+            mg->lev.push_back(L);
+        }
+        mg->nlev = (int)mg->lev.size();
+        const int D = dim == 3 ? 24 : 8, NS = dim == 3 ? 27 : 9;
+        for (int l = 0; l < mg->nlev; ++l) {
+            MGLevel<T>& L = mg->lev[l];
+            const long long nd = L.d.ndof;
+            L.dinv = mg_alloc<T>(mg, nd * sizeof(T));
+            L.z = mg_alloc<T>(mg, nd * sizeof(T));
+            L.t = mg_alloc<T>(mg, nd * sizeof(T));
+            L.w = mg_alloc<T>(mg, nd * sizeof(T));
+            L.r = l > 0 ? mg_alloc<T>(mg, nd * sizeof(T)) : nullptr;
+            L.fixed = l > 0 ? mg_alloc<uint8_t>(mg, nd) : g->fixed;
+            const bool need_stencil = l > 0 || (mg->nlev == 1 && nd <= DENSE_MAX);
+            if (need_stencil) {
+                L.Kel = mg_alloc<T>(mg, L.d.nel * D * D * sizeof(T));
+                L.S = mg_alloc<T>(mg, (size_t)NS * dim * dim * L.d.nnodes * sizeof(T));
+                L.R = mg_alloc<T>(mg, (size_t)dim * dim * L.d.nnodes * sizeof(T));
+            }
+        }
+        const Dims& dc = mg->lev.back().d;
+        if (dc.ndof <= DENSE_MAX) {
+            mg->nc = (int)dc.ndof;
+            mg->A = mg_alloc<double>(mg, (size_t)mg->nc * mg->nc * sizeof(double));
+            mg->Ainv = mg_alloc<T>(mg, (size_t)mg->nc * mg->nc * sizeof(T));
+            mg->status = mg_alloc<int>(mg, sizeof(int));
+        }
+        if (dim == 3) {
+            const int smem = 2 * 8 * 24 * 24 * (int)sizeof(T);
+            TOPO_CUDA(cudaFuncSetAttribute(k_galerkin<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            TOPO_CUDA(cudaFuncSetAttribute(k_galerkin<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        }
+    } catch (...) {
+        mg_destroy(mg);
+        throw;
+    }
+    return mg;
+}
+
+template <typename T>
+void mg_destroy(MG<T>* mg) {
+    if (!mg) return;
+    for (void* p : mg->allocs) cudaFree(p);
+    delete mg;
+}
+
+template <typename T, int DIM>
+static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
+    constexpr int D = DIM == 3 ? 24 : 8;
+    const int smem = 2 * (DIM == 3 ? 8 : 4) * D * D * (int)sizeof(T);
+    RowAbs<T, DIM> ra;
+    for (int r = 0; r < D; ++r) {
+        double s = 0.0;
+        for (int j = 0; j < D; ++j) s += std::fabs(g->Ke_host[(size_t)r * D + j]);
+        ra.a[r] = (T)s;
+    }
+    k_l1_inv<T, DIM><<<div_up(g->d.nnodes, 256), 256, 0, st>>>(g->d, ra, E, g->fixed, mg->lev[0].dinv);
+    TOPO_CHECK_LAUNCH();
+    for (int l = 0; l < mg->nlev; ++l) {
+        MGLevel<T>& L = mg->lev[l];
+        if (!L.S) continue;
+        if (l == 0) {
+            k_elem_from_E<T, DIM><<<div_up(L.d.nel * D * D, 256), 256, 0, st>>>(L.d, E, g->Ke_dev, L.Kel);
+        } else if (l == 1) {
+            k_galerkin<T, DIM, true><<<(unsigned)L.d.nel, 256, smem, st>>>(L.d, mg->lev[0].d, E, g->Ke_dev, nullptr,
+                                                                       g->fixed, L.Kel);
+        } else {
+            k_galerkin<T, DIM, false><<<(unsigned)L.d.nel, 256, smem, st>>>(L.d, mg->lev[l - 1].d, nullptr, nullptr,
+                                                                        mg->lev[l - 1].Kel, nullptr, L.Kel);
+        }
+        TOPO_CHECK_LAUNCH();
+        k_stencil_build<T, DIM><<<div_up(L.d.nnodes, 128), 128, 0, st>>>(L.d, L.Kel, L.S, L.R);
+        TOPO_CHECK_LAUNCH();
+        if (l > 0) {
+            k_stencil_diag<T, DIM><<<div_up(L.d.nnodes, 256), 256, 0, st>>>(L.d, L.S, L.dinv, L.fixed);
+            TOPO_CHECK_LAUNCH();
+        }
+    }
+    if (mg->nc > 0) {
+        MGLevel<T>& L = mg->lev.back();
+        k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.fixed, mg->A);
+        TOPO_CHECK_LAUNCH();
+        k_cholesky<<<1, 1024, 0, st>>>(mg->nc, mg->A, mg->status);
+        TOPO_CHECK_LAUNCH();
+        // the work columns reuse the level's element-matrix buffer when large enough
+        double* work = nullptr;
+        const size_t need = (size_t)mg->nc * mg->nc * sizeof(double);
+        if (L.Kel && (size_t)L.d.nel * D * D * sizeof(T) >= need) {
+            work = (double*)L.Kel;
+        } else {
+            if (!mg->A_work) mg->A_work = mg_alloc<double>(mg, need);
+            work = mg->A_work;
+        }
+        k_chol_inverse<T><<<div_up((long long)mg->nc * 32, 256), 256, 0, st>>>(mg->nc, mg->A, work, L.fixed, mg->Ainv);
+        TOPO_CHECK_LAUNCH();
+    }
+}
+
+template <typename T>
+void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
+    mg->E = E;
+    if (g->d.dim == 3)
+        setup_dim<T, 3>(g, mg, E, st);
+    else
+        setup_dim<T, 2>(g, mg, E, st);
+}
+
+template <typename T>
+static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T* u, const T* r, T* out,
+                     const int* skip, cudaStream_t st) {
+    MGLevel<T>& L = mg->lev[l];
+    if (l == 0) {
+        launch_fine_op<T>(g, mode, E, u, r, L.dinv, out, mg->omega, skip, nullptr, st);
+        return;
+    }
+    const int nb = div_up(L.d.nnodes, 256);
+    const T w = mg->omega;
+#define TOPO_SOP(DIMV, MODEV)                                                                      \
+    k_stencil_op<T, DIMV, MODEV><<<nb, 256, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip)
+    if (L.d.dim == 3) {
+        if (mode == 1) TOPO_SOP(3, 1); else if (mode == 2) TOPO_SOP(3, 2); else TOPO_SOP(3, 0);
+    } else {
+        if (mode == 1) TOPO_SOP(2, 1); else if (mode == 2) TOPO_SOP(2, 2); else TOPO_SOP(2, 0);
+    }
+#undef TOPO_SOP
+    TOPO_CHECK_LAUNCH();
+}
+
+template <typename T>
+static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, const int* skip, cudaStream_t st) {
+    MGLevel<T>& L = mg->lev[l];
+    const bool coarsest = l == mg->nlev - 1;
+    if (coarsest && mg->nc > 0) {
+        k_dense_apply<T><<<div_up((long long)mg->nc * 32, 256), 256, 0, st>>>(mg->nc, mg->Ainv, rhs, L.z, skip);
+        TOPO_CHECK_LAUNCH();
+        return L.z;
+    }
+    k_jacobi_first<T><<<div_up(L.d.ndof, 256), 256, 0, st>>>(L.d.ndof, L.dinv, rhs, L.z, mg->omega, skip);
+    TOPO_CHECK_LAUNCH();
+    T* cur = L.z;
+    T* oth = L.t;
+    const int nu = coarsest ? 4 * mg->nu : mg->nu;
+    for (int s = 1; s < nu; ++s) {
+        level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st);
+        std::swap(cur, oth);
+    }
+    if (!coarsest) {
+        level_op<T>(g, mg, l, 2, E, cur, rhs, L.w, skip, st);
+        MGLevel<T>& C = mg->lev[l + 1];
+        const int nbc = div_up(C.d.nnodes, 256), nbf = div_up(L.d.nnodes, 256);
+        if (L.d.dim == 3)
+            k_restrict<T, 3><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
+        else
+            k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
+        TOPO_CHECK_LAUNCH();
+        T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st);
+        if (L.d.dim == 3)
+            k_prolong_add<T, 3><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
+        else
+            k_prolong_add<T, 2><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
+        TOPO_CHECK_LAUNCH();
+    }
+    for (int s = 0; s < nu; ++s) {
+        level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st);
+        std::swap(cur, oth);
+    }
+    return cur;
+}
+
+template <typename T>
+T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st) {
+    return vcycle_level<T>(g, mg, 0, mg->E, r, skip, st);
+}
+
+template MG<double>* mg_create<double>(to_grid*, int, int, double);
+template MG<float>* mg_create<float>(to_grid*, int, int, double);
+template void mg_destroy<double>(MG<double>*);
+template void mg_destroy<float>(MG<float>*);
+template void mg_setup<double>(to_grid*, MG<double>*, const double*, cudaStream_t);
+template void mg_setup<float>(to_grid*, MG<float>*, const float*, cudaStream_t);
+template double* mg_vcycle<double>(to_grid*, MG<double>*, const double*, const int*, cudaStream_t);
+template float* mg_vcycle<float>(to_grid*, MG<float>*, const float*, const int*, cudaStream_t);
+
+}  // namespace topo

@@ -1,113 +1,445 @@
 // State solve K(xPhys)(free, free) U = F (Eq. 4) by preconditioned CG on the
-// matrix-free operator. The PCG iteration body is captured once per handle as
-// a CUDA graph of CHUNK iterations; the kernels become no-ops once the device
-// flag `done` is set, so the host only polls the scalars between chunks.
+// matrix-free operator, with a Jacobi or geometric-multigrid preconditioner.
+//
+// Each PCG solve is a handful of set-up kernels followed by ONE launch of a
+// CUDA graph holding a conditional WHILE node: its body is one PCG iteration
+// and its last kernel clears the condition once the device-side residual test
+// (or the iteration cap) sets `done`. The host does not poll.
+//
+// TO_FP64: the PCG and the preconditioner run in FP64.
+// TO_MIXED: FP64 iterative refinement: r = F - K U is formed in FP64, the
+// correction K d = r is solved by an FP32 PCG (FP32 operator and V-cycle,
+// FP64 dot products) to a relative tolerance inner_rtol, and U += d in FP64,
+// until ||F - K U|| <= cg_rtol ||F|| in FP64.
 #include <cmath>
 
 #include "grid.h"
+#include "mg.h"
 
 namespace topo {
 
-struct Solver {
-    // FP64 Jacobi-PCG vectors (nDof)
-    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *b = nullptr,
-           *dinv = nullptr;
-    cudaGraphExec_t chunk = nullptr;
-    int chunk_iters = 0;
+// ------------------------------------------------------------------ kernels
+
+constexpr int KNT = 256;
+
+static int kblocks(long long n) {
+    int nb = div_up(n, KNT * 4);
+    return nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_cast_mask(long long n, const Tin* __restrict__ in, Tout* __restrict__ out,
+                            const uint8_t* __restrict__ fixed) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (fixed && fixed[i]) ? Tout(0) : (Tout)in[i];
+}
+
+// rr = r.r, bb = b.b over free DOFs; start the PCG scalars.
+template <typename T>
+__global__ void __launch_bounds__(KNT) k_gpcg_init(long long n, const T* __restrict__ b, const T* __restrict__ r,
+                                                   const uint8_t* __restrict__ fixed, PcgScalars* s,
+                                                   double* partials, unsigned* counter) {
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
+        const double ri = r[i], bi = fixed[i] ? 0.0 : (double)b[i];
+        v[0] += ri * ri;
+        v[1] += bi * bi;
+    }
+    if (last_block_totals<KNT, 2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        s->rr = tot[0];
+        s->bb = tot[1];
+        s->iters = 0;
+        s->done = (tot[0] <= s->rtol2 * tot[1]) ? 1 : 0;
+        if (!isfinite(tot[0])) s->done = 3;
+    }
+}
+
+// rz = r.z (Jacobi: z = dinv r computed here); FIRST: p = z, else beta = rz / rz_old.
+template <typename T, bool FIRST, bool JAC>
+__global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restrict__ r, T* __restrict__ z,
+                                                 const T* __restrict__ dinv, T* __restrict__ p, PcgScalars* s,
+                                                 double* partials, unsigned* counter) {
+    if (s->done) return;
+    double v[1] = {0.0}, tot[1];
+    for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
+        T zi;
+        if (JAC) {
+            zi = dinv[i] * r[i];
+            z[i] = zi;
+        } else {
+            zi = z[i];
+        }
+        if (FIRST) p[i] = zi;
+        v[0] += (double)r[i] * (double)zi;
+    }
+    if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        if (FIRST) {
+            s->rz = tot[0];
+        } else {
+            s->beta = tot[0] / s->rz;
+            s->rz = tot[0];
+        }
+    }
+}
+
+// x += alpha p; r -= alpha Ap; rr; iteration count and the stopping tests.
+template <typename T>
+__global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x, T* __restrict__ r,
+                                                 const T* __restrict__ p, const T* __restrict__ Ap, PcgScalars* s,
+                                                 double* partials, unsigned* counter) {
+    if (s->done) return;
+    const T alpha = (T)s->alpha;
+    double v[1] = {0.0}, tot[1];
+    for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
+        x[i] += alpha * p[i];
+        const T ri = r[i] - alpha * Ap[i];
+        r[i] = ri;
+        v[0] += (double)ri * (double)ri;
+    }
+    if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        s->iters += 1;
+        s->rr = tot[0];
+        if (!isfinite(tot[0]) || !isfinite(s->alpha))
+            s->done = 3;
+        else if (tot[0] <= s->rtol2 * s->bb)
+            s->done = 1;
+        else if (s->iters >= s->maxit)
+            s->done = 2;
+    }
+}
+
+// p = z + beta p, then set the WHILE condition of the enclosing graph.
+template <typename T>
+__global__ void k_gpcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const PcgScalars* s,
+                         cudaGraphConditionalHandle cond) {
+    const int done = s->done;
+    if (!done) {
+        const T beta = (T)s->beta;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
+            p[i] = z[i] + beta * p[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+}
+
+// Mixed refinement: r64 = b - y (0 at fixed DOFs), r32 = (float) r64, rr, bb.
+__global__ void __launch_bounds__(KNT) k_refine_resid(long long n, const double* __restrict__ b,
+                                                      const double* __restrict__ y, double* __restrict__ r64,
+                                                      float* __restrict__ r32, const uint8_t* __restrict__ fixed,
+                                                      double* res, double* partials, unsigned* counter) {
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
+        const bool f = fixed[i] != 0;
+        const double bi = f ? 0.0 : b[i];
+        const double ri = f ? 0.0 : bi - y[i];
+        r64[i] = ri;
+        if (r32) r32[i] = (float)ri;
+        v[0] += ri * ri;
+        v[1] += bi * bi;
+    }
+    if (last_block_totals<KNT, 2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        res[0] = tot[0];
+        res[1] = tot[1];
+    }
+}
+
+__global__ void k_refine_update(long long n, double* __restrict__ x64, const float* __restrict__ d32) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x64[i] += (double)d32[i];
+}
+
+template <typename T>
+__global__ void k_zero(long long n, T* __restrict__ a) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = T(0);
+}
+
+// ------------------------------------------------------------------ PCG
+
+template <typename T>
+struct Pcg {
+    T *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *zj = nullptr, *dinv_j = nullptr, *b = nullptr;
+    T* E = nullptr;              // modulus in T
+    MG<T>* mg = nullptr;         // nullptr: Jacobi
+    PcgScalars* s = nullptr;     // device
+    cudaGraphExec_t loop = nullptr;
+    long long body_kernels = 0;  // kernels per loop iteration
+    T* z = nullptr;              // preconditioner output buffer (fixed at capture)
 };
 
-static constexpr int CHUNK = 16;
+struct Solver {
+    Pcg<double> p64;
+    Pcg<float> p32;
+    double* y64 = nullptr;       // FP64 K U of the refinement
+    double* res = nullptr;       // device refinement sums [4]
+    double* hres = nullptr;      // pinned mirror
+    PcgScalars* hpcg = nullptr;  // pinned mirror
+    std::vector<void*> allocs;
+};
+
+template <typename T>
+static T* salloc(Solver* s, size_t count) {
+    void* p = nullptr;
+    TOPO_CUDA(cudaMalloc(&p, count * sizeof(T) + 16));
+    s->allocs.push_back(p);
+    return (T*)p;
+}
+
+template <typename T>
+static void pcg_alloc(to_grid* g, Solver* sv, Pcg<T>& P, bool gmg) {
+    const long long n = g->d.ndof;
+    P.x = salloc<T>(sv, n);
+    P.r = salloc<T>(sv, n);
+    P.p = salloc<T>(sv, n);
+    P.Ap = salloc<T>(sv, n);
+    P.zj = salloc<T>(sv, n);
+    P.b = salloc<T>(sv, n);
+    P.dinv_j = salloc<T>(sv, n);
+    P.E = sizeof(T) == 8 ? (T*)g->E : salloc<T>(sv, g->d.nel);
+    P.s = salloc<PcgScalars>(sv, 1);
+    if (gmg) P.mg = mg_create<T>(g, g->p.mg_levels, g->p.mg_nu, g->p.mg_omega);
+}
+
+// The body of one PCG iteration, captured into the WHILE node's body graph.
+template <typename T>
+static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond, cudaStream_t st) {
+    const long long n = g->d.ndof;
+    const int* skip = &P.s->done;
+    launch_fine_op<T>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, T(0), skip, P.s, st);
+    k_gpcg_xr<T><<<kblocks(n), KNT, 0, st>>>(n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter);
+    TOPO_CHECK_LAUNCH();
+    if (P.mg) {
+        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st);
+        k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
+                                                               g->counter);
+    } else {
+        P.z = P.zj;
+        k_gpcg_rz<T, false, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, P.mg ? nullptr : P.dinv_j, nullptr,
+                                                              P.s, g->partials, g->counter);
+    }
+    TOPO_CHECK_LAUNCH();
+    k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(n, P.z, P.p, P.s, cond);
+    TOPO_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void build_loop_graph(to_grid* g, Pcg<T>& P) {
+    cudaGraph_t graph = nullptr;
+    TOPO_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    TOPO_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    TOPO_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    TOPO_CUDA(cudaStreamBeginCaptureToGraph(g->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    try {
+        enqueue_body<T>(g, P, cond, g->st);
+    } catch (...) {
+        set_capturing(false);
+        cudaStreamEndCapture(g->st, &body);
+        cudaGraphDestroy(graph);
+        throw;
+    }
+    set_capturing(false);
+    TOPO_CUDA(cudaStreamEndCapture(g->st, &body));
+    TOPO_CUDA(cudaGraphInstantiate(&P.loop, graph, 0));
+    TOPO_CUDA(cudaGraphDestroy(graph));
+}
+
+// Set up the preconditioner from P.E (when `setup`), r = b - K x (or r = b for
+// x = 0), and run the loop.
+template <typename T>
+static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int maxit, bool x0_zero, bool setup) {
+    const Dims& d = g->d;
+    const long long n = d.ndof;
+    cudaStream_t st = g->st;
+    if (setup) {
+        if (P.mg)
+            mg_setup<T>(g, P.mg, P.E, st);
+        else
+            launch_diag_inv<T>(d, grid_ke3<T>(g), grid_ke2<T>(g), P.E, g->fixed, P.dinv_j, st);
+    }
+    if (!P.loop) {
+        build_loop_graph<T>(g, P);
+        P.body_kernels = captured_launches_reset();
+    }
+    PcgScalars init{};
+    init.rtol2 = rtol * rtol;
+    init.maxit = maxit;
+    TOPO_CUDA(cudaMemcpyAsync(P.s, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+    if (x0_zero) {
+        k_zero<T><<<div_up(n, 256), 256, 0, st>>>(n, P.x);
+        TOPO_CUDA(cudaMemcpyAsync(P.r, P.b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        count_launches(1);
+    } else {
+        launch_fine_op<T>(g, 2, P.E, P.x, P.b, nullptr, P.r, T(0), nullptr, nullptr, st);
+    }
+    k_gpcg_init<T><<<kblocks(n), KNT, 0, st>>>(n, P.b, P.r, g->fixed, P.s, g->partials, g->counter);
+    TOPO_CHECK_LAUNCH();
+    if (P.mg) {
+        T* z = mg_vcycle<T>(g, P.mg, P.r, &P.s->done, st);
+        (void)z;  // the same buffer the captured body uses
+        k_gpcg_rz<T, true, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, P.p, P.s, g->partials,
+                                                              g->counter);
+    } else {
+        k_gpcg_rz<T, true, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.zj, P.dinv_j, P.p, P.s, g->partials,
+                                                             g->counter);
+    }
+    TOPO_CHECK_LAUNCH();
+    TOPO_CUDA(cudaGraphLaunch(P.loop, st));
+    TOPO_CUDA(cudaMemcpyAsync(sv->hpcg, P.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+    PcgScalars h = *sv->hpcg;
+    count_launches((long long)(h.iters > 0 ? h.iters : 1) * P.body_kernels);
+    return h;
+}
+
+// ------------------------------------------------------------------ entry
 
 void solver_init(to_grid* g) {
     Solver* s = new Solver();
     g->solver = s;
-    // v[0..5] are the handle's nDof vectors; v[6] stays free for to_apply_K masking
-    s->x = g->v[0];
-    s->r = g->v[1];
-    s->z = g->v[2];
-    s->p = g->v[3];
-    s->Ap = g->v[4];
-    s->b = g->v[5];
-    TOPO_CUDA(cudaMalloc(&s->dinv, g->d.ndof * sizeof(double)));
+    try {
+        const bool gmg = g->p.precond == TO_PC_GMG;
+        if (g->p.precision == TO_FP64) {
+            pcg_alloc<double>(g, s, s->p64, gmg);
+        } else {
+            pcg_alloc<float>(g, s, s->p32, gmg);
+            s->p64.x = salloc<double>(s, g->d.ndof);
+            s->p64.r = salloc<double>(s, g->d.ndof);
+        }
+        s->y64 = salloc<double>(s, g->d.ndof);
+        s->res = salloc<double>(s, 4);
+        TOPO_CUDA(cudaMallocHost(&s->hres, 4 * sizeof(double)));
+        TOPO_CUDA(cudaMallocHost(&s->hpcg, sizeof(PcgScalars)));
+    } catch (...) {
+        solver_free(g);
+        throw;
+    }
 }
 
 void solver_free(to_grid* g) {
     Solver* s = g->solver;
     if (!s) return;
-    if (s->chunk) cudaGraphExecDestroy(s->chunk);
-    if (s->dinv) cudaFree(s->dinv);
+    if (s->p64.loop) cudaGraphExecDestroy(s->p64.loop);
+    if (s->p32.loop) cudaGraphExecDestroy(s->p32.loop);
+    if (s->p64.mg) mg_destroy(s->p64.mg);
+    if (s->p32.mg) mg_destroy(s->p32.mg);
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->hres) cudaFreeHost(s->hres);
+    if (s->hpcg) cudaFreeHost(s->hpcg);
     delete s;
     g->solver = nullptr;
 }
 
-static void enqueue_iteration(to_grid* g, Solver* s) {
-    const Dims& d = g->d;
-    PcgScalars* sc = &g->ds->pcg;
-    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, s->p, s->Ap, g->fixed, true, sc, g->partials,
-                           g->counter, g->st);
-    launch_pcg_update(d.ndof, s->x, s->r, s->z, s->p, s->Ap, s->dinv, sc, g->partials, g->counter, g->st);
-    launch_pcg_dir(d.ndof, s->z, s->p, sc, g->st);
-}
-
-static void build_chunk_graph(to_grid* g, Solver* s) {
-    cudaGraph_t graph;
-    TOPO_CUDA(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
-    set_capturing(true);
-    try {
-        for (int i = 0; i < CHUNK; ++i) enqueue_iteration(g, s);
-    } catch (...) {
-        set_capturing(false);
-        cudaStreamEndCapture(g->st, &graph);
-        throw;
-    }
-    set_capturing(false);
-    TOPO_CUDA(cudaStreamEndCapture(g->st, &graph));
-    TOPO_CUDA(cudaGraphInstantiate(&s->chunk, graph, 0));
-    TOPO_CUDA(cudaGraphDestroy(graph));
-    s->chunk_iters = CHUNK;
+// ||b - K x|| and ||b|| in FP64 (x, b FP64), into hres[0..1].
+static void true_residual(to_grid* g, Solver* sv, const double* b, const double* x, double* r64, float* r32) {
+    const long long n = g->d.ndof;
+    launch_apply_K<double>(g->d, g->ke3, g->ke2, g->E, x, sv->y64, g->fixed, true, nullptr, nullptr, nullptr, g->st);
+    k_refine_resid<<<kblocks(n), KNT, 0, g->st>>>(n, b, sv->y64, r64, r32, g->fixed, sv->res, g->partials,
+                                                   g->counter);
+    TOPO_CHECK_LAUNCH();
+    TOPO_CUDA(cudaMemcpyAsync(sv->hres, sv->res, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    TOPO_CUDA(cudaStreamSynchronize(g->st));
 }
 
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info) {
-    Solver* s = g->solver;
+    Solver* sv = g->solver;
     const Dims& d = g->d;
+    const long long n = d.ndof;
     cudaStream_t st = g->st;
-    if (!s->chunk) build_chunk_graph(g, s);
-    // b = F (masked inside pcg_init), x = U warm start
-    TOPO_CUDA(cudaMemcpyAsync(s->b, b, d.ndof * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    launch_mask_copy(d.ndof, U, s->x, g->fixed, st);
-    launch_diag_inv<double>(d, g->ke3, g->ke2, g->E, g->fixed, s->dinv, st);
-    PcgScalars init{};
-    init.rtol2 = g->p.cg_rtol * g->p.cg_rtol;
-    init.maxit = g->p.cg_maxit;
-    TOPO_CUDA(cudaMemcpyAsync(&g->ds->pcg, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
-    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, s->x, s->Ap, g->fixed, true, nullptr, nullptr,
-                           nullptr, st);
-    launch_pcg_init(d.ndof, s->b, s->Ap, s->x, s->r, s->z, s->p, s->dinv, g->fixed, &g->ds->pcg,
-                    g->partials, g->counter, st);
-    PcgScalars h{};
-    for (;;) {
-        TOPO_CUDA(cudaMemcpyAsync(&g->hs->pcg, &g->ds->pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
-        TOPO_CUDA(cudaStreamSynchronize(st));
-        h = g->hs->pcg;
-        if (h.done) break;
-        TOPO_CUDA(cudaGraphLaunch(s->chunk, st));
-        count_launches(3LL * s->chunk_iters);
-    }
-    TOPO_CUDA(cudaMemcpyAsync(U, s->x, d.ndof * sizeof(double), cudaMemcpyDeviceToDevice, st));
     to_status status = TO_OK;
-    if (h.done == 2) status = TO_ENOTCONV;
-    if (h.done == 3) status = TO_ENAN;
+    int iters = 0, refinements = 0;
+    double rel = 0.0;
+    if (g->p.precision == TO_FP64) {
+        Pcg<double>& P = sv->p64;
+        TOPO_CUDA(cudaMemcpyAsync(P.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, P.x, g->fixed);
+        TOPO_CHECK_LAUNCH();
+        // The recursive CG residual can drift below the true one; the true FP64
+        // residual decides, and the PCG restarts from the current x if needed.
+        for (int restart = 0;; ++restart) {
+            const PcgScalars h = run_pcg<double>(g, sv, P, g->p.cg_rtol, g->p.cg_maxit - iters, false, restart == 0);
+            iters += h.iters;
+            true_residual(g, sv, P.b, P.x, P.r, nullptr);
+            rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
+            if (h.done == 3 || !std::isfinite(rel)) {
+                status = TO_ENAN;
+                break;
+            }
+            if (rel <= g->p.cg_rtol) break;
+            if (h.done == 2 || restart >= 8 || iters >= g->p.cg_maxit) {
+                status = TO_ENOTCONV;
+                break;
+            }
+            refinements = restart + 1;  // reported as restarts of the FP64 PCG
+        }
+        TOPO_CUDA(cudaMemcpyAsync(U, P.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        Pcg<float>& P = sv->p32;
+        double* x64 = sv->p64.x;
+        double* r64 = sv->p64.r;
+        k_cast_mask<double, float><<<div_up(d.nel, 256), 256, 0, st>>>(d.nel, g->E, P.E, nullptr);
+        k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, x64, g->fixed);
+        TOPO_CHECK_LAUNCH();
+        count_launches(1);
+        bool prepared = false;
+        const int max_ref = 30;
+        for (;;) {
+            true_residual(g, sv, b, x64, r64, P.b);
+            rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
+            if (!std::isfinite(rel)) {
+                status = TO_ENAN;
+                break;
+            }
+            if (rel <= g->p.cg_rtol) break;
+            if (refinements >= max_ref || iters >= g->p.cg_maxit) {
+                status = TO_ENOTCONV;
+                break;
+            }
+            // the preconditioner is set up once per solve
+            const PcgScalars h = run_pcg<float>(g, sv, P, g->p.inner_rtol, g->p.cg_maxit - iters, true, !prepared);
+            prepared = true;
+            iters += h.iters;
+            if (h.done == 3) {
+                status = TO_ENAN;
+                break;
+            }
+            k_refine_update<<<div_up(n, 256), 256, 0, st>>>(n, x64, P.x);
+            TOPO_CHECK_LAUNCH();
+            ++refinements;
+        }
+        TOPO_CUDA(cudaMemcpyAsync(U, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     if (info) {
-        info->iters = h.iters;
-        info->refinements = 0;
-        info->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        info->iters = iters;
+        info->refinements = refinements;
+        info->rel_res = rel;
         info->status = (int)status;
     }
     return status;
 }
 
-void time_apply_K_mixed(to_grid*, const double*, int, cudaEvent_t, cudaEvent_t) {
-    throw Error(TO_EINVAL, "mixed-precision operator not available");
+void time_apply_K_mixed(to_grid* g, const double* xPhys, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+    Solver* sv = g->solver;
+    TOPO_REQUIRE(g->p.precision == TO_MIXED, "handle was created for TO_FP64");
+    const Dims& d = g->d;
+    cudaStream_t st = g->st;
+    Pcg<float>& P = sv->p32;
+    launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, P.E, st);
+    k_zero<float><<<div_up(d.ndof, 256), 256, 0, st>>>(d.ndof, P.p);
+    TOPO_CHECK_LAUNCH();
+    launch_fine_op<float>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, 0.f, nullptr, nullptr, st);
+    TOPO_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r)
+        launch_fine_op<float>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, 0.f, nullptr, nullptr, st);
+    TOPO_CUDA(cudaEventRecord(e1, st));
 }
 
 }  // namespace topo

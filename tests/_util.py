@@ -51,3 +51,15 @@ def make_grid(shape, **kw):
 def simp_field(nel, seed, lo=0.001):
     """A design field with the value mix of a SIMP iterate (mostly near 0 or 1)."""
     return np.clip(I.random_design(nel, seed, "binary"), lo, 1.0)
+
+
+def design_field(shape, seed, rmin=2.5, beta=8.0, lo=0.0):
+    """A coherent design like a SIMP iterate: a random field filtered with the
+    oracle's cone filter and projected (solid and void regions with smooth
+    transitions), values in [lo, 1]."""
+    from oracle import topopt_oracle as O
+    g = O.Grid(*shape)
+    x = O.filter_forward(g, I.random_design(g.nel, seed), rmin, "N")
+    z = (x - np.median(x)) / max(np.std(x), 1e-12)   # unit-variance coherent field
+    x = O.prj(0.5 + 0.25 * z, 0.5, beta)              # mostly solid or void, smooth edges
+    return np.clip(x, lo, 1.0)
