@@ -265,7 +265,10 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "per_step": [{"loop": t["loop"], "ms": round(m, 2), "n_cg": t["n_cg"], "n_refine": t["n_refine"],
-                      "c": t["c"], "rel_res": t["rel_res"], "t_solve_ms": round(t["t_solve_ms"], 2)}
+                      "c": t["c"], "rel_res": t["rel_res"], "t_solve_ms": round(t["t_solve_ms"], 2),
+                      "t_setup_ms": round(t["t_setup_ms"], 2), "t_krylov_ms": round(t["t_krylov_ms"], 2),
+                      "t_resid_ms": round(t["t_resid_ms"], 2),
+                      "t_other_ms": round(t["t_filter_ms"] + t["t_sens_ms"] + t["t_oc_ms"], 2)}
                      for t, m in zip(timed, step_ms)],
         "final": {"c": last["c"], "V": last["V"], "eta": last["eta"]},
         "paper_context": "top3D125 + MGCG, 96x48x48 rmin 2sqrt(3): 14.20 s/it (0.0704 it/s), "

@@ -104,6 +104,9 @@ typedef struct to_solve_info {
     double rel_res;         /* ||F - K U||_2 / ||F||_2 in FP64 at exit */
     int32_t status;         /* to_status of the solve */
     int32_t _pad;
+    double t_setup_ms;      /* preconditioner set-up (CUDA events) */
+    double t_krylov_ms;     /* PCG iterations (the inner FP32 solves in TO_MIXED) */
+    double t_resid_ms;      /* FP64 true residuals and refinement updates */
 } to_solve_info;
 
 /* Design state advanced by to_step. Device pointers are caller-owned, FP64:
@@ -135,6 +138,7 @@ typedef struct to_iter_info {
     double penal, beta, eta, lm;
     double rel_res;         /* final FP64 relative residual of the solve */
     double t_filter_ms, t_solve_ms, t_sens_ms, t_oc_ms;  /* CUDA-event phase times */
+    double t_setup_ms, t_krylov_ms, t_resid_ms;          /* split of t_solve_ms */
 } to_iter_info;
 
 /* Thread-local message of the last failing call ("" if none). */

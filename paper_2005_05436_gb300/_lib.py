@@ -41,7 +41,8 @@ class Params(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("rel_res", C.c_double),
-                ("status", C.c_int32), ("_pad", C.c_int32)]
+                ("status", C.c_int32), ("_pad", C.c_int32), ("t_setup_ms", C.c_double),
+                ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double)]
 
 
 class State(C.Structure):
@@ -56,7 +57,8 @@ class IterInfo(C.Structure):
                 ("c", C.c_double), ("V", C.c_double), ("ch", C.c_double), ("penal", C.c_double),
                 ("beta", C.c_double), ("eta", C.c_double), ("lm", C.c_double),
                 ("rel_res", C.c_double), ("t_filter_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double)]
+                ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double), ("t_setup_ms", C.c_double),
+                ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -552,6 +552,9 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     for (int i = 0; i < 4; ++i) TOPO_CUDA(cudaEventElapsedTime(&ms[i], g->ev_t[i], g->ev_t[i + 1]));
     it.t_filter_ms = ms[0];
     it.t_solve_ms = ms[1];
+    it.t_setup_ms = si.t_setup_ms;
+    it.t_krylov_ms = si.t_krylov_ms;
+    it.t_resid_ms = si.t_resid_ms;
     it.t_sens_ms = ms[2];
     it.t_oc_ms = ms[3];
     // continuation (Sec. 3), post-increment loop counter

@@ -7,7 +7,7 @@
 // trilinear (bilinear) prolongation P masked at the fine Dirichlet DOFs, formed
 // element by element (Kc = sum over the 8 (4) children of P_j^T K_j P_j, which
 // equals P^T K P exactly) and stored as a node stencil for application. The
-// coarsest level is solved with a dense inverse (computed in FP64) when small
+// coarsest level is solved with a dense inverse (computed in the solve's precision) when small
 // enough, else smoothed. Smoother: damped Jacobi, nu pre and nu post sweeps, so
 // the V-cycle is a symmetric positive definite operator usable inside CG.
 #pragma once
@@ -38,9 +38,10 @@ struct MG {
     T omega = T(0.6);
     int nc = 0;             // coarsest DOFs (dense inverse) or 0 (smoothing only)
     std::vector<MGLevel<T>> lev;
-    double* A = nullptr;    // coarsest dense matrix, FP64 [nc * nc]
+    T* A = nullptr;         // coarsest dense matrix and its Cholesky factor [nc * nc]
     T* Ainv = nullptr;      // its inverse [nc * nc]
-    double* A_work = nullptr;  // column workspace of the inverse, when no level buffer is reused
+    T* A_work = nullptr;    // column workspace of the inverse [nc * nc]
+    T* Cj = nullptr;        // P_j^T Ke P_j of the 2^dim children of a coarse element
     int* status = nullptr;  // device: nonzero if the coarse Cholesky met a non-positive pivot
     const T* E = nullptr;   // fine modulus of the current set-up
     std::vector<void*> allocs;

@@ -175,7 +175,15 @@ struct Solver {
     double* hres = nullptr;      // pinned mirror
     PcgScalars* hpcg = nullptr;  // pinned mirror
     std::vector<void*> allocs;
+    cudaEvent_t ev[3] = {};      // phase timers
+    double t_setup = 0, t_krylov = 0, t_resid = 0;
 };
+
+static float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    TOPO_CUDA(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+}
 
 template <typename T>
 static T* salloc(Solver* s, size_t count) {
@@ -259,6 +267,7 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
     const Dims& d = g->d;
     const long long n = d.ndof;
     cudaStream_t st = g->st;
+    TOPO_CUDA(cudaEventRecord(sv->ev[0], st));
     if (setup) {
         if (P.mg)
             mg_setup<T>(g, P.mg, P.E, st);
@@ -269,6 +278,7 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
         build_loop_graph<T>(g, P);
         P.body_kernels = captured_launches_reset();
     }
+    TOPO_CUDA(cudaEventRecord(sv->ev[1], st));
     PcgScalars init{};
     init.rtol2 = rtol * rtol;
     init.maxit = maxit;
@@ -293,8 +303,11 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
     }
     TOPO_CHECK_LAUNCH();
     TOPO_CUDA(cudaGraphLaunch(P.loop, st));
+    TOPO_CUDA(cudaEventRecord(sv->ev[2], st));
     TOPO_CUDA(cudaMemcpyAsync(sv->hpcg, P.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     TOPO_CUDA(cudaStreamSynchronize(st));
+    sv->t_setup += elapsed_ms(sv->ev[0], sv->ev[1]);
+    sv->t_krylov += elapsed_ms(sv->ev[1], sv->ev[2]);
     PcgScalars h = *sv->hpcg;
     count_launches((long long)(h.iters > 0 ? h.iters : 1) * P.body_kernels);
     return h;
@@ -316,6 +329,7 @@ void solver_init(to_grid* g) {
         }
         s->y64 = salloc<double>(s, g->d.ndof);
         s->res = salloc<double>(s, 4);
+        for (int i = 0; i < 3; ++i) TOPO_CUDA(cudaEventCreate(&s->ev[i]));
         TOPO_CUDA(cudaMallocHost(&s->hres, 4 * sizeof(double)));
         TOPO_CUDA(cudaMallocHost(&s->hpcg, sizeof(PcgScalars)));
     } catch (...) {
@@ -332,6 +346,8 @@ void solver_free(to_grid* g) {
     if (s->p64.mg) mg_destroy(s->p64.mg);
     if (s->p32.mg) mg_destroy(s->p32.mg);
     for (void* p : s->allocs) cudaFree(p);
+    for (int i = 0; i < 3; ++i)
+        if (s->ev[i]) cudaEventDestroy(s->ev[i]);
     if (s->hres) cudaFreeHost(s->hres);
     if (s->hpcg) cudaFreeHost(s->hpcg);
     delete s;
@@ -341,12 +357,15 @@ void solver_free(to_grid* g) {
 // ||b - K x|| and ||b|| in FP64 (x, b FP64), into hres[0..1].
 static void true_residual(to_grid* g, Solver* sv, const double* b, const double* x, double* r64, float* r32) {
     const long long n = g->d.ndof;
+    TOPO_CUDA(cudaEventRecord(sv->ev[0], g->st));
     launch_apply_K<double>(g->d, g->ke3, g->ke2, g->E, x, sv->y64, g->fixed, true, nullptr, nullptr, nullptr, g->st);
     k_refine_resid<<<kblocks(n), KNT, 0, g->st>>>(n, b, sv->y64, r64, r32, g->fixed, sv->res, g->partials,
                                                    g->counter);
     TOPO_CHECK_LAUNCH();
+    TOPO_CUDA(cudaEventRecord(sv->ev[1], g->st));
     TOPO_CUDA(cudaMemcpyAsync(sv->hres, sv->res, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
     TOPO_CUDA(cudaStreamSynchronize(g->st));
+    sv->t_resid += elapsed_ms(sv->ev[0], sv->ev[1]);
 }
 
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info) {
@@ -357,6 +376,7 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
     to_status status = TO_OK;
     int iters = 0, refinements = 0;
     double rel = 0.0;
+    sv->t_setup = sv->t_krylov = sv->t_resid = 0.0;
     if (g->p.precision == TO_FP64) {
         Pcg<double>& P = sv->p64;
         TOPO_CUDA(cudaMemcpyAsync(P.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -422,6 +442,9 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         info->refinements = refinements;
         info->rel_res = rel;
         info->status = (int)status;
+        info->t_setup_ms = sv->t_setup;
+        info->t_krylov_ms = sv->t_krylov;
+        info->t_resid_ms = sv->t_resid;
     }
     return status;
 }
