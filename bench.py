@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "gmg"])
     ap.add_argument("--grid", default="96x48x48")
+    ap.add_argument("--ku-impl", default="auto", choices=["auto", "cuda", "tc"],
+                    help="FP32 fine operator of the mixed path: CUDA cores or tcgen05 tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -152,6 +154,7 @@ def run_ours(args):
     p = default_params(3, w["nelx"], w["nely"], w["nelz"], volfrac=w["volfrac"], penal=w["penal"],
                        rmin=w["rmin"], ft=w["ft"], eta=w["eta"], beta=w["beta"], move=w["move"],
                        cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
+                       ku_impl={"auto": 0, "cuda": 1, "tc": 2}[args.ku_impl],
                        penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
     stream = torch.cuda.current_stream()
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
@@ -258,7 +261,7 @@ def run_ours(args):
         "dtype": "f64" if precision == TO_FP64 else "f32+tf32 inner, f64 residual/refinement",
         "data": "synthetic (paper's cantilever load and supports; no dataset)",
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
-                   "precision": args.precision, "precond": args.precond,
+                   "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches),

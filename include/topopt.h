@@ -92,7 +92,9 @@ typedef struct to_params {
     double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3) */
     double mg_omega;        /* GMG l1-Jacobi smoother weight (1.0) */
     int32_t mg_nu;          /* GMG pre- and post-smoothing sweeps per level (2) */
-    int32_t _pad1;
+    int32_t ku_impl;        /* FP32 fine operator of TO_MIXED: 0 auto (the faster one, at
+                               present the CUDA-core kernel), 1 CUDA cores, 2 tensor cores
+                               (tcgen05 TF32 with split operands, 3D only) */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */
@@ -253,6 +255,14 @@ to_status to_oc_update_noalloc(int64_t nel, double* x, const double* dc, const d
                                const int8_t* passive, double volfrac, double move, double oc_tol,
                                int32_t oc_maxit, int64_t deadline_cycles, void* stream,
                                double* lm_out);
+
+/* The FP32 stiffness operator of the TO_MIXED inner solve, y = K(xPhys) u
+ * (masked as to_apply_K with masked = 1), for checking it against the FP64
+ * one: u is rounded to FP32, the product runs on CUDA cores (impl = 1) or
+ * tensor cores (impl = 2, tcgen05 TF32 with split operands, 3D only) and y is
+ * returned widened to FP64. Needs a handle created with TO_MIXED. u[nDof],
+ * y[nDof] device FP64. */
+to_status to_apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int32_t impl);
 
 /* Instrumentation (no counterpart in the paper): number of kernels this library
  * has launched in this process; a CUDA-graph launch counts its kernel nodes. */

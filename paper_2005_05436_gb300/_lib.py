@@ -36,7 +36,7 @@ class Params(C.Structure):
                 ("oc_tol", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("mg_levels", C.c_int32),
                 ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
-                ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("_pad1", C.c_int32)]
+                ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -91,6 +91,7 @@ _SIGS = {
     "to_oc_update_noalloc": (C.c_int, [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                        C.c_int32, C.c_int64, P, C.POINTER(C.c_double)]),
     "to_kernel_launches": (C.c_int64, []),
+    "to_apply_K_fp32": (C.c_int, [P, P, P, P, C.c_int32]),
     "to_time_apply_K": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
 }
 

@@ -143,6 +143,8 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->inner_rtol > 0.0 && p->inner_rtol < 1.0, "inner_rtol must be in (0, 1)");
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
+    TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 2, "ku_impl must be 0, 1 or 2");
+    TOPO_REQUIRE(!(p->ku_impl == 2 && p->dim != 3), "the tensor-core operator is 3D only");
     const long long nnodes = (long long)(p->nelx + 1) * (p->nely + 1) * (p->dim == 3 ? p->nelz + 1 : 1);
     TOPO_REQUIRE(nnodes * p->dim < (1LL << 31) - 1, "grid too large for 32-bit DOF indices");
 }
@@ -239,6 +241,15 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
     g->Ke_host = K;
     g->Ke_dev = dalloc<double>(g, K.size());
     TOPO_CUDA(cudaMemcpyAsync(g->Ke_dev, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
+    if (p->precision == TO_MIXED && d.dim == 3) {
+        std::vector<float> pack;
+        tc_pack_ke(K, pack);
+        g->ke_tc = dalloc<float>(g, pack.size());
+        TOPO_CUDA(cudaMemcpy(g->ke_tc, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+        g->tc_err = dalloc<int>(g, 1);
+        TOPO_CUDA(cudaMemset(g->tc_err, 0, sizeof(int)));
+        g->use_tc = p->ku_impl == 2;  // auto: the CUDA-core operator (faster so far)
+    }
 
     // problem data
     g->F = dalloc<double>(g, d.ndof);

@@ -126,18 +126,21 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV*NT/3
 // Two-level deterministic reduction inside one launch: every block stores its
 // NV partials, the last block to arrive sums them in block order and returns
 // true with the totals in tot (thread 0 valid). partials: [NV * gridDim.x].
+// Blocks are numbered x-fastest over a 1D, 2D or 3D grid.
 template <int NT, int NV>
 __device__ bool last_block_totals(double (&v)[NV], double* partials, unsigned* counter,
                                   double (&tot)[NV]) {
     __shared__ double sm[NV * NT / 32];
     __shared__ bool am_last;
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     block_sum<NT, NV>(v, sm);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        for (int k = 0; k < NV; ++k) partials[k * nb + bid] = v[k];
         __threadfence();
         unsigned t = atomicAdd(counter, 1u);
-        am_last = (t == gridDim.x - 1);
+        am_last = (t == nb - 1);
     }
     __syncthreads();
     if (!am_last) return false;
@@ -146,7 +149,7 @@ __device__ bool last_block_totals(double (&v)[NV], double* partials, unsigned* c
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         s[k] = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) s[k] += __ldcg(&partials[k * gridDim.x + i]);
+        for (int i = threadIdx.x; i < (int)nb; i += NT) s[k] += __ldcg(&partials[k * nb + i]);
     }
     block_sum<NT, NV>(s, sm);
 #pragma unroll

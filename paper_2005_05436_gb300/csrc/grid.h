@@ -68,6 +68,9 @@ struct to_grid {
     topo::DevScalars* hs = nullptr;  // pinned mirror
     int proj_blocks = 0, oc_blocks = 0;
     void* scan_tmp = nullptr;  // CSR assembly scan workspace (lazy)
+    float* ke_tc = nullptr;    // Ke packed as the tensor-core B operand (TO_MIXED, 3D)
+    int* tc_err = nullptr;     // device error word of the tensor-core operator
+    bool use_tc = false;       // the FP32 fine operator runs on tensor cores
 
     topo::Solver* solver = nullptr;
 };
@@ -93,6 +96,12 @@ void solver_init(to_grid* g);
 void solver_free(to_grid* g);
 // Solve K(E)(free, free) U = b with g->E already set; U: warm start in, solution out.
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info);
+// Tensor-core FP32 fine operator (ku_tc.cu); modes as launch_fine_op.
+void launch_fine_op_tc(const to_grid* g, int mode, const float* E, const float* u, const float* r, const float* dinv,
+                       float* out, float omega, const int* skip, PcgScalars* pcg, cudaStream_t st);
+void tc_pack_ke(const std::vector<double>& Ke, std::vector<float>& pack);
+// y = K(xPhys) u by the FP32 operator of the mixed path (impl 1 CUDA cores, 2 tensor cores).
+void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int impl);
 // Enqueue `reps` launches of the mixed-precision K u kernel between events e0, e1.
 void time_apply_K_mixed(to_grid* g, const double* xPhys, int reps, cudaEvent_t e0, cudaEvent_t e1);
 }  // namespace topo

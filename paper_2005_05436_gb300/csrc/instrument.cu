@@ -33,6 +33,18 @@ extern "C" {
 
 int64_t to_kernel_launches(void) { return (int64_t)launches_total(); }
 
+to_status to_apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int32_t impl) {
+    if (!g || !xPhys || !u || !y || u == y) return TO_EINVAL;
+    try {
+        grid_sync_in(g);
+        apply_K_fp32(g, xPhys, u, y, impl);
+        grid_sync_out(g);
+    } catch (const topo::Error& e) {
+        return e.code;
+    }
+    return TO_OK;
+}
+
 to_status to_time_apply_K(to_grid* g, const double* xPhys, int32_t precision, int32_t reps, double* us) {
     if (!g || !xPhys || !us || reps < 1) return TO_EINVAL;
     try {

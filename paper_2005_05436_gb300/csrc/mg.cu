@@ -101,6 +101,12 @@ static void fine_op_dispatch(const to_grid* g, const T* E, const T* u, const T* 
 template <typename T>
 void launch_fine_op(const to_grid* g, int mode, const T* E, const T* u, const T* r, const T* dinv, T* out,
                     T omega, const int* skip, PcgScalars* pcg, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (g->use_tc) {
+            launch_fine_op_tc(g, mode, E, u, r, dinv, out, omega, skip, pcg, st);
+            return;
+        }
+    }
     if (mode == 0 && pcg)
         fine_op_dispatch<T, 0, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
     else if (mode == 0)

@@ -436,6 +436,12 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             ++refinements;
         }
         TOPO_CUDA(cudaMemcpyAsync(U, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (g->tc_err) {
+            int herr = 0;
+            TOPO_CUDA(cudaMemcpyAsync(&herr, g->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TOPO_CUDA(cudaStreamSynchronize(st));
+            if (herr) status = TO_ETIMEOUT;
+        }
     }
     if (info) {
         info->iters = iters;
@@ -447,6 +453,37 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         info->t_resid_ms = sv->t_resid;
     }
     return status;
+}
+
+// y = K u with the FP32 operator of the mixed path (impl 1: CUDA cores, 2: tensor cores).
+void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int impl) {
+    Solver* sv = g->solver;
+    TOPO_REQUIRE(g->p.precision == TO_MIXED, "handle was created for TO_FP64");
+    TOPO_REQUIRE(impl == 1 || (impl == 2 && g->ke_tc), "impl must be 1, or 2 on a 3D grid");
+    const Dims& d = g->d;
+    const long long n = d.ndof;
+    cudaStream_t st = g->st;
+    Pcg<float>& P = sv->p32;
+    launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, P.E, st);
+    k_cast_mask<double, float><<<div_up(n, 256), 256, 0, st>>>(n, u, P.p, g->fixed);
+    TOPO_CHECK_LAUNCH();
+    const bool saved = g->use_tc;
+    g->use_tc = impl == 2;
+    try {
+        launch_fine_op<float>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, 0.f, nullptr, nullptr, st);
+    } catch (...) {
+        g->use_tc = saved;
+        throw;
+    }
+    g->use_tc = saved;
+    k_cast_mask<float, double><<<div_up(n, 256), 256, 0, st>>>(n, P.Ap, y, nullptr);
+    TOPO_CHECK_LAUNCH();
+    if (g->tc_err) {
+        int h = 0;
+        TOPO_CUDA(cudaMemcpyAsync(&h, g->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TOPO_CUDA(cudaStreamSynchronize(st));
+        if (h) throw Error(TO_ETIMEOUT, "tensor-core operator: mbarrier wait passed its limit");
+    }
 }
 
 void time_apply_K_mixed(to_grid* g, const double* xPhys, int reps, cudaEvent_t e0, cudaEvent_t e1) {
