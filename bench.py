@@ -43,13 +43,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "gmg"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="gmg", choices=["jacobi", "gmg"])
     ap.add_argument("--grid", default="96x48x48")
     ap.add_argument("--ku-impl", default="auto", choices=["auto", "cuda", "tc"],
                     help="FP32 fine operator of the mixed path: CUDA cores or tcgen05 tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
     return ap.parse_args()
 
 
@@ -68,7 +69,7 @@ def workload_name(w):
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -83,7 +84,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -126,14 +127,42 @@ class ClockSampler:
 
 # ------------------------------------------------------------ our GPU arm --
 
+def _make_design(args, w, precision, precond, ku_impl, stream):
+    import torch
+
+    from paper_2005_05436_gb300 import TO_CNT_MUL, default_params, inputs as I
+    from paper_2005_05436_gb300.topopt import Design, Grid
+    F, fixed = I.cantilever_3d(w["nelx"], w["nely"], w["nelz"])
+    p = default_params(3, w["nelx"], w["nely"], w["nelz"], volfrac=w["volfrac"], penal=w["penal"],
+                       rmin=w["rmin"], ft=w["ft"], eta=w["eta"], beta=w["beta"], move=w["move"],
+                       cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
+                       ku_impl=ku_impl, penal_cnt=(1, 3.0, 25, 0.25),
+                       beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+    g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
+    d = Design(g, torch.from_numpy(I.initial_design(g.nel, w["volfrac"])).cuda())
+    return g, d
+
+
+def _timed_steps(d, steps, flush, stream):
+    """Design steps timed one by one with CUDA events on the stream; L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    for k in range(steps):
+        flush.fill_(float(k))  # evict the working set from L2 between steps
+        ev[k][0].record(stream)
+        infos.append(d.step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return infos, [a.elapsed_time(b) for a, b in ev]
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2005_05436_gb300 import TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI
-    from paper_2005_05436_gb300 import build as B, default_params, inputs as I, load
-    from paper_2005_05436_gb300.topopt import Design, Grid
+    from paper_2005_05436_gb300 import TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI
+    from paper_2005_05436_gb300 import build as B, load
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -150,42 +179,24 @@ def run_ours(args):
     w = workload(args.grid)
     precision = TO_MIXED if args.precision == "mixed" else TO_FP64
     precond = TO_PC_GMG if args.precond == "gmg" else TO_PC_JACOBI
-    F, fixed = I.cantilever_3d(w["nelx"], w["nely"], w["nelz"])
-    p = default_params(3, w["nelx"], w["nely"], w["nelz"], volfrac=w["volfrac"], penal=w["penal"],
-                       rmin=w["rmin"], ft=w["ft"], eta=w["eta"], beta=w["beta"], move=w["move"],
-                       cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
-                       ku_impl={"auto": 0, "cuda": 1, "tc": 2}[args.ku_impl],
-                       penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+    ku_impl = {"auto": 0, "cuda": 1, "tc": 2}[args.ku_impl]
     stream = torch.cuda.current_stream()
-    g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
-    x0 = torch.from_numpy(I.initial_design(g.nel, w["volfrac"])).cuda()
-    d = Design(g, x0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    infos = []
+    g, d = _make_design(args, w, precision, precond, ku_impl, stream)
     for _ in range(args.warmup):
-        infos.append(d.step())
+        d.step()
     torch.cuda.synchronize()
     snap = [t.clone() for t in (d.x, d.xPhys, d.xOld, d.U)]
     snap_sc = (d.st.eta, d.st.penal, d.st.beta, d.st.loop)
 
-    # ---- device-timed steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    # ---- device-timed steps of the headline configuration
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = lib.to_kernel_launches()
-    timed = []
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict the working set from L2 between steps
-            ev[k][0].record(stream)
-            timed.append(d.step())
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        timed, step_ms = _timed_steps(d, args.steps, flush, stream)
     launches = lib.to_kernel_launches() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -194,25 +205,25 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1000.0)
 
-    # ---- roofline of the dominant kernel (matrix-free K u), same process
+    # ---- roofline of the dominant kernel (the fine-level matrix-free K u)
     us = g.time_apply_K(d.xPhys, precision, reps=30)
     nel, ndof = g.nel, g.ndof
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     if precision == TO_FP64:
-        flops = 2.0 * 24 * 24 * nel
-        achieved = flops / (us * 1e-6) / 1e12
-        roof = {"kernel": "k_apply_K3<double> (node-centric FP64 K u)", "bound": "alu",
+        achieved = 2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12
+        roof = {"kernel": "k_apply_K3<double> / k_fine_op3<double> (node-centric FP64 K u)", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                "us_per_launch": round(us, 2),
-                "peak_source": "FP64 FMA units: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
+                "peak_source": "derived: FP64 FMA units 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
-        nbytes = 4.0 * (2 * ndof + nel)
-        achieved = nbytes / (us * 1e-6) / 1e9
+        achieved = 4.0 * (2 * ndof + nel) / (us * 1e-6) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "mixed K u", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "us_per_launch": round(us, 2), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        kern = "k_fine_op3_tc (tcgen05)" if args.ku_impl == "tc" else "k_fine_op3<float> (CUDA cores)"
+        roof = {"kernel": kern + ", FP32 K u of the inner solve", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "us_per_launch": round(us, 2),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_bytes": "4 (2 nDof + nEl) per launch (u read, y write, E read)"}
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -227,21 +238,35 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        cs = []
         for k in range(args.steps):
             d.x.copy_(x_host, non_blocking=True)
-            info = d.step()
+            d.step()
             out_host.copy_(d.x, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             x_host.copy_(out_host)
-            cs.append(info["c"])
         e2e_s = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": round(world * args.steps / e2e_s, 4), "unit": UNIT,
-               "h2d_bytes_per_step": nel * 8, "d2h_bytes_per_step": nel * 8 + 8 * 18}
+               "h2d_bytes_per_step": nel * 8, "d2h_bytes_per_step": nel * 8 + 8 * 21}
+    g.close()
+
+    # ---- the plain FP64 paths on the same design iterations (comparison, not timed above)
+    compare = {}
+    if not args.no_compare and precision != TO_FP64:
+        for name, pc in (("plain_fp64_gmg", TO_PC_GMG), ("plain_fp64_jacobi", TO_PC_JACOBI)):
+            g2, d2 = _make_design(args, w, TO_FP64, pc, 0, stream)
+            for _ in range(args.warmup):
+                d2.step()
+            infos2, ms2 = _timed_steps(d2, args.steps, flush, stream)
+            g2.close()
+            v2 = args.steps / (sum(ms2) / 1000.0)
+            cdiff = max(abs(a["c"] - b["c"]) / abs(b["c"]) for a, b in zip(timed, infos2))
+            compare[name] = {"value": round(v2, 4), "ms_per_step": round(sum(ms2) / args.steps, 2),
+                             "n_cg": [t["n_cg"] for t in infos2], "speedup_of_headline": round(value / world / v2, 2),
+                             "max_rel_diff_c": cdiff}
 
     if rank != 0:
         if world > 1:
@@ -250,22 +275,24 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        n_cg = [t["n_cg"] for t in timed] if precision == TO_FP64 and args.precond == "jacobi" else None
-        cpu = cpu_baseline(args.grid, n_cg_hint=n_cg)
+        hint = compare.get("plain_fp64_jacobi", {}).get("n_cg")
+        if precision == TO_FP64 and args.precond == "jacobi":
+            hint = [t["n_cg"] for t in timed]
+        cpu = cpu_baseline(args.grid, n_cg_hint=hint)
 
     last = timed[-1]
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == TO_FP64 else "f32+tf32 inner, f64 residual/refinement",
+        "dtype": "f64" if precision == TO_FP64 else "f32 inner PCG + GMG, f64 residual/refinement/dots",
         "data": "synthetic (paper's cantilever load and supports; no dataset)",
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "cpu_baseline": cpu, "compare": compare,
         "clocks": clk.summary(),
         "per_step": [{"loop": t["loop"], "ms": round(m, 2), "n_cg": t["n_cg"], "n_refine": t["n_refine"],
                       "c": t["c"], "rel_res": t["rel_res"], "t_solve_ms": round(t["t_solve_ms"], 2),
