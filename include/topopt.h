@@ -95,6 +95,11 @@ typedef struct to_params {
     int32_t ku_impl;        /* FP32 fine operator of TO_MIXED: 0 auto (the faster one, at
                                present the CUDA-core kernel), 1 CUDA cores, 2 tensor cores
                                (tcgen05 TF32 with split operands, 3D only) */
+    int32_t loop_mode;      /* PCG loop: 0 one CUDA-graph launch with a conditional WHILE node
+                               (default); 1 the same kernels launched from a host loop, polled
+                               every 8 iterations (for profilers that do not follow
+                               device-side graph iterations) */
+    int32_t _pad2;
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

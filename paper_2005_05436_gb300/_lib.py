@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("oc_tol", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("mg_levels", C.c_int32),
                 ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
-                ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32)]
+                ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
+                ("loop_mode", C.c_int32), ("_pad2", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

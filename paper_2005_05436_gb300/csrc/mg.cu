@@ -507,61 +507,164 @@ __global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const uint8_t*
     }
 }
 
-// Right-looking Cholesky of the lower triangle of A (row-major, in place) by
-// one CTA, in the solve's precision T. A pivot that is not positive (rounding
-// in a near-singular coarse operator) is replaced by 1e-6 of the original
-// diagonal, which keeps the factor that of an SPD matrix, and flagged.
+// Coarsest-level dense inverse, in the solve's precision T, in four kernels:
+//  1. blocked right-looking Cholesky A = L L^T by one CTA: the NB x NB diagonal
+//     block is factored by one warp in shared memory, the column panel below it
+//     is solved row by row and staged in shared memory, then the trailing lower
+//     triangle is updated from the staged panel (n/NB barrier phases instead of
+//     3 n). A pivot below 1e-6 of the original diagonal is floored there and
+//     flagged, which keeps the factor that of an SPD matrix.
+//  2. inverses of the diagonal blocks of L (one CTA each);
+//  3. W = L^{-1} block column by block column (one CTA per block column);
+//  4. A^{-1} = W^T W, zero on fixed rows and columns.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_cholesky(int n, T* A, T* diag0, int* status) {
-    __shared__ T piv;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) *status = 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
-    for (int k = 0; k < n; ++k) {
+struct CholNB {
+    static constexpr int v = sizeof(T) == 8 ? 16 : 32;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, int* status) {
+    constexpr int NB = CholNB<T>::v, LD = NB + 1;
+    extern __shared__ __align__(16) unsigned char chol_smem[];
+    T* Dg = (T*)chol_smem;  // NB x LD diagonal block
+    T* Pn = Dg + NB * LD;   // up to n x LD panel
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) *status = 0;
+    for (int k = tid; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int kw = min(NB, n - k0), k1 = k0 + kw, m = n - k1;
+        for (int i = tid; i < kw * kw; i += blockDim.x) {
+            const int r = i / kw, c = i % kw;
+            Dg[r * LD + c] = c <= r ? A[(long long)(k0 + r) * n + k0 + c] : T(0);
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            T p = A[(long long)k * n + k];
-            if (!(p > T(1e-6) * diag0[k])) {
-                *status = 1;
-                p = T(1e-6) * diag0[k];
+        if (warp == 0) {
+            for (int j = 0; j < kw; ++j) {
+                if (lane == 0) {
+                    T p = Dg[j * LD + j];
+                    const T fl = T(1e-6) * diag0[k0 + j];
+                    if (!(p > fl)) {
+                        *status = 1;
+                        p = fl > T(0) ? fl : T(1);
+                    }
+                    Dg[j * LD + j] = sqrt(p);
+                }
+                __syncwarp();
+                if (lane > j && lane < kw) Dg[lane * LD + j] /= Dg[j * LD + j];
+                __syncwarp();
+                if (lane > j && lane < kw)
+                    for (int l = j + 1; l <= lane; ++l) Dg[lane * LD + l] -= Dg[lane * LD + j] * Dg[l * LD + j];
+                __syncwarp();
             }
-            piv = sqrt(p);
-            A[(long long)k * n + k] = piv;
         }
         __syncthreads();
-        const T L = piv;
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + k] /= L;
-        __syncthreads();
-        for (int i = k + 1 + warp; i < n; i += nw) {
-            const T aik = A[(long long)i * n + k];
-            for (int j = k + 1 + lane; j <= i; j += 32) A[(long long)i * n + j] -= aik * A[(long long)j * n + k];
+        for (int i = tid; i < kw * kw; i += blockDim.x) {
+            const int r = i / kw, c = i % kw;
+            if (c <= r) A[(long long)(k0 + r) * n + k0 + c] = Dg[r * LD + c];
         }
+        // panel rows k1..n-1: x L_kk^T = a  (forward substitution per row)
+        for (int i = tid; i < m; i += blockDim.x) {
+            T x[NB];
+            const long long row = (long long)(k1 + i) * n + k0;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j < kw) {
+                    T s = A[row + j];
+                    for (int l = 0; l < j; ++l) s -= x[l] * Dg[j * LD + l];
+                    x[j] = s / Dg[j * LD + j];
+                    Pn[i * LD + j] = x[j];
+                    A[row + j] = x[j];
+                }
+            }
+        }
+        __syncthreads();
+        // trailing update of the lower triangle from the staged panel
+        for (int i = warp; i < m; i += nw) {
+            const T* pi = Pn + i * LD;
+            for (int j = lane; j <= i; j += 32) {
+                const T* pj = Pn + j * LD;
+                T s = T(0);
+                for (int l = 0; l < kw; ++l) s += pi[l] * pj[l];
+                A[(long long)(k1 + i) * n + k1 + j] -= s;
+            }
+        }
+        __syncthreads();
     }
 }
 
-// Column j of A^{-1} = L^{-T} L^{-1} e_j by one warp; fixed rows/cols are zero.
+// Inverse of diagonal block b of the lower-triangular L: one CTA per block,
+// thread c solves column c.
 template <typename T>
-__global__ void k_chol_inverse(int n, const T* __restrict__ L, T* __restrict__ work,
-                               const uint8_t* __restrict__ fixed, T* __restrict__ Ainv) {
-    const int lane = threadIdx.x & 31;
-    const long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void k_chol_diag_inv(int n, const T* __restrict__ L, T* __restrict__ Dinv) {
+    constexpr int NB = CholNB<T>::v;
+    const int b = blockIdx.x, k0 = b * NB, kw = min(NB, n - k0), c = threadIdx.x;
+    if (c >= NB) return;
+    T* out = Dinv + (long long)b * NB * NB;
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        T s = T(0);
+        if (r < kw && c < kw) {
+            s = (r == c) ? T(1) : T(0);
+            for (int l = 0; l < r; ++l) s -= L[(long long)(k0 + r) * n + k0 + l] * x[l];
+            s /= L[(long long)(k0 + r) * n + k0 + r];
+        }
+        x[r] = s;
+        out[r * NB + c] = s;
+    }
+}
+
+// Block column jb of W = L^{-1}: W_jj = inv(L_jj); W_ij = -inv(L_ii) sum_{k=j}^{i-1} L_ik W_kj.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chol_trinv(int n, const T* __restrict__ L, const T* __restrict__ Dinv,
+                                                     T* __restrict__ W) {
+    constexpr int NB = CholNB<T>::v, LD = NB + 1;
+    extern __shared__ __align__(16) unsigned char trinv_smem[];
+    const int nblk = (n + NB - 1) / NB, jb = blockIdx.x;
+    T* Wc = (T*)trinv_smem;        // [nblk][NB][LD] blocks of this column
+    T* S = Wc + nblk * NB * LD;    // NB x LD
+    const int r = threadIdx.x / NB, c = threadIdx.x % NB;  // NB x NB threads
+    const bool act = threadIdx.x < NB * NB;
+    if (act) Wc[(jb * NB + r) * LD + c] = Dinv[(long long)jb * NB * NB + r * NB + c];
+    __syncthreads();
+    for (int ib = jb + 1; ib < nblk; ++ib) {
+        if (act) {
+            T s = T(0);
+            const int gi = ib * NB + r;
+            if (gi < n)
+                for (int kb = jb; kb < ib; ++kb)
+                    for (int mm = 0; mm < NB; ++mm) {
+                        const int gk = kb * NB + mm;
+                        if (gk < n) s += L[(long long)gi * n + gk] * Wc[(kb * NB + mm) * LD + c];
+                    }
+            S[r * LD + c] = s;
+        }
+        __syncthreads();
+        if (act) {
+            T s = T(0);
+            for (int mm = 0; mm < NB; ++mm) s += Dinv[(long long)ib * NB * NB + r * NB + mm] * S[mm * LD + c];
+            Wc[(ib * NB + r) * LD + c] = -s;
+        }
+        __syncthreads();
+    }
+    // write the column of blocks: W[gi][jb*NB + c]
+    for (int i = threadIdx.x; i < nblk * NB * NB; i += blockDim.x) {
+        const int bi = i / (NB * NB), rr = (i / NB) % NB, cc = i % NB;
+        const int gi = bi * NB + rr, gj = jb * NB + cc;
+        if (gi < n && gj < n) W[(long long)gi * n + gj] = (bi >= jb) ? Wc[(bi * NB + rr) * LD + cc] : T(0);
+    }
+}
+
+// A^{-1} = W^T W (W = L^{-1} lower triangular); fixed rows and columns zero.
+template <typename T>
+__global__ void k_chol_wtw(int n, const T* __restrict__ W, const uint8_t* __restrict__ fixed, T* __restrict__ Ainv) {
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    T* y = work + j * n;
-    for (int i = 0; i < n; ++i) {
-        T s = T(0);
-        for (int k = lane; k < i; k += 32) s += L[(long long)i * n + k] * y[k];
-        s = warp_sum(s);
-        if (lane == 0) y[i] = ((i == j ? T(1) : T(0)) - s) / L[(long long)i * n + i];
-        __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        T s = T(0);
-        for (int k = i + 1 + lane; k < n; k += 32) s += L[(long long)k * n + i] * y[k];
-        s = warp_sum(s);
-        if (lane == 0) y[i] = (y[i] - s) / L[(long long)i * n + i];
-        __syncwarp();
-    }
-    for (int i = lane; i < n; i += 32) Ainv[(long long)i * n + j] = (fixed[i] || fixed[j]) ? T(0) : y[i];
+    T s = T(0);
+    if (!fixed[i] && !fixed[j])
+        for (int k = max(i, j); k < n; ++k) s += W[(long long)k * n + i] * W[(long long)k * n + j];
+    Ainv[(long long)i * n + j] = s;
 }
 
 template <typename T>
@@ -579,7 +682,7 @@ __global__ void k_dense_apply(int n, const T* __restrict__ Ainv, const T* __rest
 
 // ------------------------------------------------------------ host side
 
-static constexpr long long DENSE_MAX = 2048;
+static constexpr long long DENSE_MAX = 1024;
 static constexpr long long COARSE_TARGET = 1500;
 
 template <typename U, typename T>
@@ -709,11 +812,21 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
         MGLevel<T>& L = mg->lev.back();
         k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.fixed, mg->A);
         TOPO_CHECK_LAUNCH();
-        // the inverse's workspace holds the original diagonal during the factorization
-        k_cholesky<T><<<1, 1024, 0, st>>>(mg->nc, mg->A, mg->A_work, mg->status);
+        // A_work holds the original diagonal during the factorization, then W = L^{-1};
+        // Ainv holds the diagonal-block inverses until the final product overwrites it
+        constexpr int NB = CholNB<T>::v;
+        const int nc = mg->nc, nblk = (nc + NB - 1) / NB;
+        const int smem_chol = (NB * (NB + 1) + nc * (NB + 1)) * (int)sizeof(T);
+        const int smem_trinv = (nblk * NB * (NB + 1) + NB * (NB + 1)) * (int)sizeof(T);
+        TOPO_CUDA(cudaFuncSetAttribute(k_chol_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
+        TOPO_CUDA(cudaFuncSetAttribute(k_chol_trinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trinv));
+        k_chol_blocked<T><<<1, 1024, smem_chol, st>>>(nc, mg->A, mg->A_work, mg->status);
         TOPO_CHECK_LAUNCH();
-        k_chol_inverse<T><<<div_up((long long)mg->nc * 32, 256), 256, 0, st>>>(mg->nc, mg->A, mg->A_work, L.fixed,
-                                                                              mg->Ainv);
+        k_chol_diag_inv<T><<<nblk, 32, 0, st>>>(nc, mg->A, mg->Ainv);
+        TOPO_CHECK_LAUNCH();
+        k_chol_trinv<T><<<nblk, NB * NB, smem_trinv, st>>>(nc, mg->A, mg->Ainv, mg->A_work);
+        TOPO_CHECK_LAUNCH();
+        k_chol_wtw<T><<<dim3(div_up(nc, 128), nc), 128, 0, st>>>(nc, mg->A_work, L.fixed, mg->Ainv);
         TOPO_CHECK_LAUNCH();
     }
 }

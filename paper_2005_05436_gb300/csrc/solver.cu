@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
 // p = z + beta p, then set the WHILE condition of the enclosing graph.
 template <typename T>
 __global__ void k_gpcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const PcgScalars* s,
-                         cudaGraphConditionalHandle cond) {
+                         cudaGraphConditionalHandle cond, int set_cond) {
     const int done = s->done;
     if (!done) {
         const T beta = (T)s->beta;
@@ -119,7 +119,7 @@ __global__ void k_gpcg_p(long long n, const T* __restrict__ z, T* __restrict__ p
              i += (long long)gridDim.x * blockDim.x)
             p[i] = z[i] + beta * p[i];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
 }
 
 // Mixed refinement: r64 = b - y (0 at fixed DOFs), r32 = (float) r64, rr, bb.
@@ -210,7 +210,7 @@ static void pcg_alloc(to_grid* g, Solver* sv, Pcg<T>& P, bool gmg) {
 
 // The body of one PCG iteration, captured into the WHILE node's body graph.
 template <typename T>
-static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond, cudaStream_t st) {
+static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st) {
     const long long n = g->d.ndof;
     const int* skip = &P.s->done;
     launch_fine_op<T>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, T(0), skip, P.s, st);
@@ -226,7 +226,7 @@ static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond,
                                                               P.s, g->partials, g->counter);
     }
     TOPO_CHECK_LAUNCH();
-    k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(n, P.z, P.p, P.s, cond);
+    k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(n, P.z, P.p, P.s, cond, set_cond);
     TOPO_CHECK_LAUNCH();
 }
 
@@ -247,7 +247,7 @@ static void build_loop_graph(to_grid* g, Pcg<T>& P) {
     TOPO_CUDA(cudaStreamBeginCaptureToGraph(g->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
     try {
-        enqueue_body<T>(g, P, cond, g->st);
+        enqueue_body<T>(g, P, cond, 1, g->st);
     } catch (...) {
         set_capturing(false);
         cudaStreamEndCapture(g->st, &body);
@@ -302,14 +302,24 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
                                                              g->counter);
     }
     TOPO_CHECK_LAUNCH();
-    TOPO_CUDA(cudaGraphLaunch(P.loop, st));
+    if (g->p.loop_mode == 0) {
+        TOPO_CUDA(cudaGraphLaunch(P.loop, st));
+    } else {
+        // the same body kernels from a host loop, polled every 8 iterations
+        for (;;) {
+            for (int k = 0; k < 8; ++k) enqueue_body<T>(g, P, cudaGraphConditionalHandle{}, 0, st);
+            TOPO_CUDA(cudaMemcpyAsync(sv->hpcg, P.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+            TOPO_CUDA(cudaStreamSynchronize(st));
+            if (sv->hpcg->done) break;
+        }
+    }
     TOPO_CUDA(cudaEventRecord(sv->ev[2], st));
     TOPO_CUDA(cudaMemcpyAsync(sv->hpcg, P.s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     TOPO_CUDA(cudaStreamSynchronize(st));
     sv->t_setup += elapsed_ms(sv->ev[0], sv->ev[1]);
     sv->t_krylov += elapsed_ms(sv->ev[1], sv->ev[2]);
     PcgScalars h = *sv->hpcg;
-    count_launches((long long)(h.iters > 0 ? h.iters : 1) * P.body_kernels);
+    if (g->p.loop_mode == 0) count_launches((long long)(h.iters > 0 ? h.iters : 1) * P.body_kernels);
     return h;
 }
 
