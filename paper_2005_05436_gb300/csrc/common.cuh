@@ -102,6 +102,35 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Per-thread dot-product accumulator. For double it is a plain FMA chain. For
+// float it keeps the sum as an unevaluated pair (hi, lo): each product a*b is
+// split exactly into p + e (e = fma(a, b, -p)), p is added to hi by Knuth's
+// TwoSum and all rounding errors collect in lo, giving about 48 significant
+// bits. FP64 enters only when the thread's pair is handed to the block
+// reduction, which keeps FP64 instructions (slow on this part) out of the
+// per-element work of the FP32 solver.
+template <typename T>
+struct DotAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);  // never contracted into an FMA
+        const float e = fmaf(a, b, -p);
+        const float s = hi + p;
+        const float bb = s - hi;
+        const float err = (hi - (s - bb)) + (p - bb);
+        hi = s;
+        lo += err + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Deterministic block sum of NV values per thread; result valid in thread 0.
 template <int NT, int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV*NT/32 */) {

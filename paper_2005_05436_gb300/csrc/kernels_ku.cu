@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) k_apply_K3(Dims d, const KeP<T, 24> ke, c
     double dot = 0.0;
     if (n < d.nnodes) {
         T a0, a1, a2;
-        ku3_node<T, true>(ke, E, u, n, d, a0, a1, a2);
+        ku3_node_clamped<T>(ke, E, u, (int)n, d, a0, a1, a2);
         if (mask_out) {
             if (fixed[3 * n + 0]) a0 = T(0);
             if (fixed[3 * n + 1]) a1 = T(0);

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(tc::NT, 2) k_fine_op3_tc(Dims d, const float* 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
     }
     // owned nodes: sum the rows of their 8 elements, fused epilogue
-    double dot = 0.0;
+    DotAcc<float> dot;
     const float* R = Ahi;
     for (int item = tid; item < OY * OZ * OX * 3; item += NT) {
         const int o = item / 3, c = item % 3;
@@ -285,10 +285,10 @@ __global__ void __launch_bounds__(tc::NT, 2) k_fine_op3_tc(Dims d, const float* 
         if (MODE == 2) o_ = r[i] - a;
         if (fixed[i]) o_ = 0.f;
         out[i] = o_;
-        if (PCG) dot += (double)u[i] * (double)o_;
+        if (PCG) dot.add(u[i], o_);
     }
     if (PCG) {
-        double v[1] = {dot}, tot[1];
+        double v[1] = {dot.value()}, tot[1];
         if (last_block_totals<tc::NT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
             pcg->pAp = tot[0];
             pcg->alpha = pcg->rz / tot[0];

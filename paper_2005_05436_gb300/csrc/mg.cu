@@ -24,13 +24,10 @@ __global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, c
                                                   unsigned* counter) {
     if (skip && *skip) return;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double dot = 0.0;
+    DotAcc<T> dot;
     if (n < d.nnodes) {
         T a[3];
-        if constexpr (sizeof(T) == 4)
-            ku3_node_regs<T>(ke, E, u, n, d, a[0], a[1], a[2]);  // register-cached neighbourhood
-        else
-            ku3_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1], a[2]);
+        ku3_node_clamped<T>(ke, E, u, (int)n, d, a[0], a[1], a[2]);  // register-cached, branch-free
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long i = 3 * n + c;
@@ -39,11 +36,11 @@ __global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, c
             if (MODE == 2) o = r[i] - a[c];
             if (fixed[i]) o = T(0);
             out[i] = o;
-            if (PCG) dot += (double)u[i] * (double)o;
+            if (PCG) dot.add(u[i], o);
         }
     }
     if (PCG) {
-        double v[1] = {dot}, tot[1];
+        double v[1] = {dot.value()}, tot[1];
         if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
             pcg->pAp = tot[0];
             pcg->alpha = pcg->rz / tot[0];
@@ -60,7 +57,7 @@ __global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, co
                                                   unsigned* counter) {
     if (skip && *skip) return;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double dot = 0.0;
+    DotAcc<T> dot;
     if (n < d.nnodes) {
         T a[2];
         ku2_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1]);
@@ -72,11 +69,11 @@ __global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, co
             if (MODE == 2) o = r[i] - a[c];
             if (fixed[i]) o = T(0);
             out[i] = o;
-            if (PCG) dot += (double)u[i] * (double)o;
+            if (PCG) dot.add(u[i], o);
         }
     }
     if (PCG) {
-        double v[1] = {dot}, tot[1];
+        double v[1] = {dot.value()}, tot[1];
         if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
             pcg->pAp = tot[0];
             pcg->alpha = pcg->rz / tot[0];
@@ -409,6 +406,68 @@ __global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict_
     }
 }
 
+// 3D coarse-level operator with nine threads per node: thread (tx, ty) serves
+// node blockIdx.x*32 + tx, output component c = ty / 3 and the stencil plane
+// dx = ty % 3 - 1 (9 of the 27 blocks). The three plane partials are summed in
+// plane order in shared memory, so the result does not depend on scheduling.
+// A single thread per node issues 243 dependent-latency loads; splitting them
+// gives the small coarse grids enough warps in flight.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restrict__ S, const T* __restrict__ R,
+                                                      const T* __restrict__ u, const T* __restrict__ r,
+                                                      const T* __restrict__ dinv, T* __restrict__ out,
+                                                      const uint8_t* __restrict__ fixed, T omega,
+                                                      const int* skip) {
+    constexpr int Q = 9;
+    constexpr bool REL = rel_form<T>();
+    __shared__ T part[9][32];
+    if (skip && *skip) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = ty / 3, pl = ty % 3;
+    const long long n = (long long)blockIdx.x * 32 + tx;
+    T acc = T(0);
+    if (n < d.nnodes) {
+        const int iy = (int)(n % d.nny);
+        const long long t = n / d.nny;
+        const int iz = (int)(t % d.nnz);
+        const int ix = (int)(t / d.nnz);
+        T uc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uc[k] = u[3 * n + k];
+        if (REL && pl == 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc += R[(long long)(c * 3 + k) * d.nnodes + n] * uc[k];
+        }
+        const int mx = ix + pl - 1;
+        if (mx >= 0 && mx < d.nnx) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int s = pl * 9 + j;
+                if (REL && s == 13) continue;
+                const int dz = j / 3 - 1, dy = j % 3 - 1;
+                const int my = iy + dy, mz = iz + dz;
+                if (my < 0 || my >= d.nny || mz < 0 || mz >= d.nnz) continue;
+                const long long m = my + (long long)d.nny * (mz + (long long)d.nnz * mx);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T um = REL ? u[3 * m + k] - uc[k] : u[3 * m + k];
+                    acc += S[((long long)s * Q + c * 3 + k) * d.nnodes + n] * um;
+                }
+            }
+        }
+    }
+    part[ty][tx] = acc;
+    __syncthreads();
+    if (pl != 0 || n >= d.nnodes) return;
+    const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
+    const long long i = 3 * n + c;
+    T o = a;
+    if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a);
+    if (MODE == 2) o = r[i] - a;
+    if (fixed[i]) o = T(0);
+    out[i] = o;
+}
+
 // ------------------------------------------------------- transfer operators
 
 template <typename T, int DIM>
@@ -436,6 +495,47 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
             }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) rc[DIM * N + c] = fixed_c[DIM * N + c] ? T(0) : acc[c];
+}
+
+// 3D restriction with nine threads per coarse node: thread (tx, ty) sums the
+// nine fine nodes of plane ox = ty % 3 - 1 for component c = ty / 3; the plane
+// partials are added in plane order in shared memory (same result as k_restrict
+// up to the order of the three plane sums, fixed for every launch).
+template <typename T>
+__global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* __restrict__ rf,
+                                                    T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
+                                                    const int* skip) {
+    __shared__ T part[9][32];
+    if (skip && *skip) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = ty / 3, ox = ty % 3 - 1;
+    const long long N = (long long)blockIdx.x * 32 + tx;
+    T acc = T(0);
+    if (N < dc.nnodes) {
+        const int NY = (int)(N % dc.nny);
+        const long long t = N / dc.nny;
+        const int NZ = (int)(t % dc.nnz);
+        const int NX = (int)(t / dc.nnz);
+        const int fx = 2 * NX + ox;
+        if (fx >= 0 && fx < df.nnx) {
+            const T wx = ox ? T(0.5) : T(1);
+#pragma unroll
+            for (int oz = -1; oz <= 1; ++oz)
+#pragma unroll
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int fy = 2 * NY + oy, fz = 2 * NZ + oz;
+                    if (fy < 0 || fy >= df.nny || fz < 0 || fz >= df.nnz) continue;
+                    const T w = wx * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+                    const long long f = fy + (long long)df.nny * (fz + (long long)df.nnz * fx);
+                    acc += w * rf[3 * f + c];
+                }
+        }
+    }
+    part[ty][tx] = acc;
+    __syncthreads();
+    if (ty % 3 != 0 || N >= dc.nnodes) return;
+    const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
+    rc[3 * N + c] = fixed_c[3 * N + c] ? T(0) : a;
 }
 
 template <typename T, int DIM>
@@ -853,7 +953,14 @@ static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T
 #define TOPO_SOP(DIMV, MODEV)                                                                      \
     k_stencil_op<T, DIMV, MODEV><<<nb, 256, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip)
     if (L.d.dim == 3) {
-        if (mode == 1) TOPO_SOP(3, 1); else if (mode == 2) TOPO_SOP(3, 2); else TOPO_SOP(3, 0);
+        const dim3 blk(32, 9);
+        const int nbs = div_up(L.d.nnodes, 32);
+        if (mode == 1)
+            k_stencil_op3s<T, 1><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
+        else if (mode == 2)
+            k_stencil_op3s<T, 2><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
+        else
+            k_stencil_op3s<T, 0><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
     } else {
         if (mode == 1) TOPO_SOP(2, 1); else if (mode == 2) TOPO_SOP(2, 2); else TOPO_SOP(2, 0);
     }
@@ -884,7 +991,7 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         MGLevel<T>& C = mg->lev[l + 1];
         const int nbc = div_up(C.d.nnodes, 256), nbf = div_up(L.d.nnodes, 256);
         if (L.d.dim == 3)
-            k_restrict<T, 3><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
+            k_restrict3s<T><<<div_up(C.d.nnodes, 32), dim3(32, 9), 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
         else
             k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
         TOPO_CHECK_LAUNCH();

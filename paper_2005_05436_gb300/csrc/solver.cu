@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restric
                                                  const T* __restrict__ dinv, T* __restrict__ p, PcgScalars* s,
                                                  double* partials, unsigned* counter) {
     if (s->done) return;
-    double v[1] = {0.0}, tot[1];
+    DotAcc<T> acc;
+    double tot[1];
     for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
         T zi;
         if (JAC) {
@@ -70,8 +71,9 @@ __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restric
             zi = z[i];
         }
         if (FIRST) p[i] = zi;
-        v[0] += (double)r[i] * (double)zi;
+        acc.add(r[i], zi);
     }
+    double v[1] = {acc.value()};
     if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
         if (FIRST) {
             s->rz = tot[0];
@@ -89,13 +91,15 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
                                                  double* partials, unsigned* counter) {
     if (s->done) return;
     const T alpha = (T)s->alpha;
-    double v[1] = {0.0}, tot[1];
+    DotAcc<T> acc;
+    double tot[1];
     for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * Ap[i];
         r[i] = ri;
-        v[0] += (double)ri * (double)ri;
+        acc.add(ri, ri);
     }
+    double v[1] = {acc.value()};
     if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
         s->iters += 1;
         s->rr = tot[0];
