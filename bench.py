@@ -35,6 +35,10 @@ UNIT = "design iterations/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak from unit counts: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# dense TF32 : BF16 tensor throughput (nominal 1.1 : 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def parse_args():
@@ -222,14 +226,26 @@ def run_ours(args):
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
                 "peak_source": "derived: FP64 FMA units 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
-        achieved = 4.0 * (2 * ndof + nel) / (us * 1e-6) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        kern = "k_fine_op3_tc (tcgen05)" if args.ku_impl == "tc" else "k_fine_op3<float> (CUDA cores)"
-        roof = {"kernel": kern + ", FP32 K u of the inner solve", "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "us_per_launch": round(us, 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "algorithmic_bytes": "4 (2 nDof + nEl) per launch (u read, y write, E read)"}
+        flops = 2.0 * 24 * 24 * nel  # the element contraction, counted once (algorithmic)
+        gbs = 4.0 * (2 * ndof + nel) / (us * 1e-6) / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        hbm_eq = {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
+                  "algorithmic_bytes": "4 (2 nDof + nEl) per launch (u read, y write, E read)"}
+        if args.ku_impl == "tc":
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
+            achieved = flops / (us * 1e-6) / 1e12
+            roof = {"kernel": "k_fine_op3_tc (tcgen05 TF32, split operands), FP32 K u of the inner solve",
+                    "bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None, "us_per_launch": round(us, 2),
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio (of measured)",
+                    "hbm_equivalent": hbm_eq}
+        else:
+            achieved = flops / (us * 1e-6) / 1e12
+            roof = {"kernel": "k_fine_op3<float> (CUDA cores), FP32 K u of the inner solve", "bound": "alu",
+                    "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                    "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
+                    "peak_source": "derived: FP32 FMA lanes 152 SM x 128 x 2 flop x 2.07 GHz",
+                    "algorithmic_flops": "2 x 24 x 24 per element per launch", "hbm_equivalent": hbm_eq}
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
