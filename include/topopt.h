@@ -280,6 +280,103 @@ int64_t to_kernel_launches(void);
  * configuration the solver uses. */
 to_status to_time_apply_K(to_grid* g, const double* xPhys, int32_t precision, int32_t reps, double* us);
 
+/* ------------------------------------------------------------------------
+ * Batched uneven 2D instances (no counterpart in the paper, which solves one
+ * problem at a time). Each instance is an independent 2D Q4 problem of Sec. 3
+ * with its own grid, volume fraction, filter radius, loads and supports; all
+ * share the material, the projection/continuation settings and the solver
+ * controls of a base to_params. One to_batch_step advances every instance by
+ * one design iteration (RL.1-RL.4: filter, eta Newton and projection, state
+ * solve, sensitivities, back-filter, OC, continuation) with ONE CUDA-graph
+ * launch. Inside it each kernel covers all instances through a table of
+ * element or node tiles (a tile never straddles two instances); per-instance
+ * sums are reduced by the last tile of the instance in tile order, so results
+ * do not depend on scheduling; the eta Newton, the FP64 refinement with its
+ * FP32 inner Jacobi-PCG, and the lambda bisection run as conditional WHILE
+ * nodes until every instance has met its own stopping test.
+ *
+ * Layout: instance k's elements occupy [el_off[k], el_off[k+1]) of every
+ * element array, in the paper's column-major order (e = iy + nely ix); its DOFs
+ * occupy [dof_off[k], dof_off[k+1]) of every DOF array (DOF 2 n + c,
+ * n = iy + (nely + 1) ix). Offsets: to_batch_offsets.
+ * ------------------------------------------------------------------------ */
+
+typedef struct to_instance {
+    int32_t nelx, nely;     /* Q4 elements per axis (>= 1) */
+    double volfrac;         /* volume fraction of this instance, in (0, 1) */
+    double rmin;            /* filter radius of this instance (> 0), 'N' padding */
+} to_instance;
+
+typedef struct to_batch to_batch;  /* opaque: instance table, tiles, workspaces, graph */
+
+/* Element-tile shape search (to_batch_autotune): candidate k is a tile of
+ * cand_ty[k] rows (along y, the fast index) x cand_tx[k] columns, one thread
+ * per node (node kernels) or element (element kernels). */
+typedef struct to_tile_info {
+    int32_t node_ty, node_tx;   /* chosen node-tile shape */
+    int32_t elem_ty, elem_tx;   /* chosen element-tile shape */
+    int32_t n_candidates;
+    int32_t cand_ty[8], cand_tx[8];
+    double node_us[8];          /* batched FP32 K u, microseconds per launch */
+    double elem_us[8];          /* batched forward filter, microseconds per launch */
+} to_tile_info;
+
+/* Record of one batched design iteration. */
+typedef struct to_batch_info {
+    int32_t loop;               /* design iteration counter after the step (1-based) */
+    int32_t status;             /* TO_OK, or TO_ENOTCONV when an instance stopped at the
+                                   refinement cap above cg_rtol */
+    int32_t max_refinements;    /* max over instances of the FP64 refinement steps */
+    int32_t max_inner_iters;    /* max over instances of the inner PCG iterations (all refinements) */
+    int32_t newton_passes;      /* lockstep passes of the eta loop (all instances) */
+    int32_t inner_passes;       /* lockstep passes of the inner PCG loop */
+    int32_t oc_passes;          /* lockstep passes of the lambda loop */
+    int32_t _pad;
+    double max_rel_res;         /* max over instances of ||F - K U|| / ||F|| (FP64) at exit */
+    double penal, beta;         /* after the continuation of this iteration */
+    double ms;                  /* device time of the graph launch (CUDA events) */
+    int64_t kernels;            /* kernels executed by the graph launch */
+} to_batch_info;
+
+/* Creates the batch. base: dim 2, precision TO_MIXED, ftBC 'N'; its nelx,
+ * nely, volfrac and rmin are ignored (per instance instead). inst: host array
+ * [count]. F, fixed: device arrays over the concatenated DOFs (F FP64, fixed
+ * 1 = Dirichlet DOF), read at every step (caller-owned, must stay valid).
+ * stream: cudaStream_t or NULL. Initial state: eta = base eta, penal and beta
+ * the base values, loop 0; tile shapes 32 x 4 until to_batch_autotune.
+ * TO_EINVAL on bad arguments; TO_ENOMEM. */
+to_status to_batch_init(const to_params* base, int32_t count, const to_instance* inst, const double* F,
+                        const uint8_t* fixed, void* stream, to_batch** out);
+
+/* Host arrays [count + 1] of element and DOF offsets (either may be NULL). */
+to_status to_batch_offsets(const to_batch* b, int64_t* el_off, int64_t* dof_off);
+
+/* Times every candidate tile shape on the batch (reps launches each of the
+ * batched FP32 K u and forward filter at a uniform design), keeps the fastest
+ * node and element shapes, and reports the timings in info (may be NULL). */
+to_status to_batch_autotune(to_batch* b, int32_t reps, to_tile_info* info);
+
+/* One design iteration of every instance. Device FP64 arrays over the
+ * concatenated layout, caller-owned: x (in/out design variables), xPhys
+ * (out), xOld (in/out previous xPhys, all ones before the first step), U
+ * (in warm start / out displacements). The graph is captured on the first
+ * call and re-captured when a pointer or the tile shapes change. */
+to_status to_batch_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U, to_batch_info* info);
+
+/* Per-instance results of the last step into host arrays [count] (any may be
+ * NULL): compliance c = F^T U, V = mean(xPhys), ch, eta, lm (the OC
+ * multiplier sqrt(lambda)), inner PCG iterations, refinements, FP64 relative
+ * residual. */
+to_status to_batch_results(const to_batch* b, double* c, double* V, double* ch, double* eta, double* lm,
+                           int32_t* inner_iters, int32_t* refinements, double* rel_res);
+
+void to_batch_destroy(to_batch* b);
+
+/* Struct sizes, for bindings that mirror these layouts. */
+size_t to_sizeof_instance(void);
+size_t to_sizeof_tile_info(void);
+size_t to_sizeof_batch_info(void);
+
 #ifdef __cplusplus
 }
 #endif

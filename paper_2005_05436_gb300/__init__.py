@@ -10,7 +10,7 @@ from ._lib import (TO_CNT_ADD, TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_J
 
 
 def __getattr__(name):
-    if name in ("Grid", "Design"):
+    if name in ("Grid", "Design", "Batch"):
         from . import topopt
         return getattr(topopt, name)
     raise AttributeError(name)

@@ -65,6 +65,23 @@ class IterInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Instance(C.Structure):
+    _fields_ = [("nelx", C.c_int32), ("nely", C.c_int32), ("volfrac", C.c_double), ("rmin", C.c_double)]
+
+
+class TileInfo(C.Structure):
+    _fields_ = [("node_ty", C.c_int32), ("node_tx", C.c_int32), ("elem_ty", C.c_int32), ("elem_tx", C.c_int32),
+                ("n_candidates", C.c_int32), ("cand_ty", C.c_int32 * 8), ("cand_tx", C.c_int32 * 8),
+                ("node_us", C.c_double * 8), ("elem_us", C.c_double * 8)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("loop", C.c_int32), ("status", C.c_int32), ("max_refinements", C.c_int32),
+                ("max_inner_iters", C.c_int32), ("newton_passes", C.c_int32), ("inner_passes", C.c_int32),
+                ("oc_passes", C.c_int32), ("_pad", C.c_int32), ("max_rel_res", C.c_double),
+                ("penal", C.c_double), ("beta", C.c_double), ("ms", C.c_double), ("kernels", C.c_int64)]
+
+
 class TopoptError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -94,6 +111,15 @@ _SIGS = {
     "to_kernel_launches": (C.c_int64, []),
     "to_apply_K_fp32": (C.c_int, [P, P, P, P, C.c_int32]),
     "to_time_apply_K": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "to_batch_init": (C.c_int, [C.POINTER(Params), C.c_int32, C.POINTER(Instance), P, P, P, C.POINTER(P)]),
+    "to_batch_offsets": (C.c_int, [P, P, P]),
+    "to_batch_autotune": (C.c_int, [P, C.c_int32, C.POINTER(TileInfo)]),
+    "to_batch_step": (C.c_int, [P, P, P, P, P, C.POINTER(BatchInfo)]),
+    "to_batch_results": (C.c_int, [P, P, P, P, P, P, P, P, P]),
+    "to_batch_destroy": (None, [P]),
+    "to_sizeof_instance": (C.c_size_t, []),
+    "to_sizeof_tile_info": (C.c_size_t, []),
+    "to_sizeof_batch_info": (C.c_size_t, []),
 }
 
 _lib = None
@@ -113,6 +139,9 @@ def load(path=LIB_PATH):
         fn.argtypes = args
     assert lib.to_sizeof_params() == C.sizeof(Params), "to_params layout mismatch"
     assert lib.to_sizeof_state() == C.sizeof(State), "to_state layout mismatch"
+    assert lib.to_sizeof_instance() == C.sizeof(Instance), "to_instance layout mismatch"
+    assert lib.to_sizeof_tile_info() == C.sizeof(TileInfo), "to_tile_info layout mismatch"
+    assert lib.to_sizeof_batch_info() == C.sizeof(BatchInfo), "to_batch_info layout mismatch"
     assert lib.to_sizeof_iter_info() == C.sizeof(IterInfo), "to_iter_info layout mismatch"
     _lib = lib
     return lib

@@ -18,6 +18,10 @@ static to_status fail(to_status s, const std::string& msg) {
     return s;
 }
 
+namespace topo {
+to_status api_fail(to_status s, const std::string& msg) { return fail(s, msg); }
+}  // namespace topo
+
 #define TOPO_API_BEGIN try {
 #define TOPO_API_END                                                  \
     }                                                                 \
@@ -30,7 +34,7 @@ namespace topo {
 
 // Unit-element stiffness by Gauss quadrature (2x2 / 2x2x2 points): bilinear Q4 in
 // plane stress, trilinear H8 isotropic; local node order of local_node().
-static void element_matrix(int dim, double nu, std::vector<double>& K) {
+void element_matrix(int dim, double nu, std::vector<double>& K) {
     const int nn = dim == 2 ? 4 : 8, D = dim * nn;
     K.assign((size_t)D * D, 0.0);
     int X[8][3];

@@ -1,0 +1,1166 @@
+// Batched uneven 2D instances: one CUDA graph per design iteration advances
+// every instance through the steps of Sec. 3 (RL.1-RL.4): the cone filter
+// (Eq. 2, 'N' padding) and its chain rule (Eq. 7), the Heaviside projection with
+// the volume-preserving eta (Eqs. 1, 8, 15; Newton with the bisection fallback),
+// the state solve K(xPhys) U = F (Eq. 4) as an FP32 Jacobi-PCG inside FP64
+// iterative refinement, the sensitivities (Eq. 6), the OC update with the
+// lambda# bracket (Eqs. 13-14, 17) and the continuation.
+//
+// Every kernel covers all instances through a tile table: tile t is a
+// TY x TX block of nodes (or elements) of one instance, processed by CTA t with
+// one thread per node (element). Per-instance sums are reduced by the last CTA
+// of the instance to finish, which adds the tile partials in tile order (the
+// result does not depend on scheduling) and then runs the instance's scalar
+// logic (Newton step, PCG alpha/beta and stopping test, bisection bracket).
+// Loops run as conditional WHILE nodes until every instance has stopped;
+// instances that have stopped return at the top of each kernel.
+#include "batch.cuh"
+
+namespace topo {
+namespace bt {
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void kb_iter_begin(BG* G, BS* S, int count, int eta_loop, cudaGraphConditionalHandle h_eta) {
+    if (threadIdx.x == 0) {
+        G->loop += 1;
+        G->status = 0;
+        for (int q = 0; q < 4; ++q) {
+            G->active[q] = 0;
+            G->body_exec[q] = 0ull;
+        }
+        G->active[LOOP_ETA] = eta_loop ? count : 0;
+        if (eta_loop) cudaGraphSetConditional(h_eta, count > 0 ? 1u : 0u);
+    }
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        S[i].eta_done = eta_loop ? 0 : 1;
+        S[i].eta_mode = ETA_NEWTON;
+        S[i].eta_it = 0;
+        S[i].eta_bis = 0;
+        S[i].oc_steps = 0;
+        S[i].oc_grow = 0;
+        S[i].inner_total = 0;
+        S[i].n_ref = 0;
+    }
+}
+
+// Sets a loop's WHILE condition (any instance still running); body = count the
+// execution of the loop body.
+__global__ void kb_cond(BG* G, int which, int body, cudaGraphConditionalHandle h) {
+    if (body) G->body_exec[which] += 1ull;
+    cudaGraphSetConditional(h, G->active[which] > 0 ? 1u : 0u);
+}
+
+// Density filter (Eq. 2), 'N' padding by repeated reflection. Forward:
+// out = (A in) / Hs. Backward (chain rule of Eq. 7, A symmetric under 'N'):
+// out = A (dprj .* in) / Hs and out2 = dV A dprj / Hs with dV = 1 / (nEl f).
+template <bool BWD>
+__global__ void kb_filter(BK k, const int2* __restrict__ toff, const double* __restrict__ tw,
+                          const double* __restrict__ in, const double* __restrict__ dprj,
+                          double* __restrict__ out, double* __restrict__ out2) {
+    B_TILE(k)
+    (void)S;
+    const int ex = tx_, ey = ty_;
+    if (ex >= I.nelx || ey >= I.nely) return;
+    const long long b = I.el0;
+    double s = 0.0, s2 = 0.0;
+    for (int j = 0; j < I.ntap; ++j) {
+        const int2 o = toff[I.tap0 + j];
+        int jx = ex + o.x, jy = ey + o.y;
+        if (jx < 0 || jx >= I.nelx) jx = mirror_index(jx, I.nelx);
+        if (jy < 0 || jy >= I.nely) jy = mirror_index(jy, I.nely);
+        const long long m = b + jy + (long long)I.nely * jx;
+        const double w = tw[I.tap0 + j];
+        if (BWD) {
+            const double d = dprj[m];
+            s += w * (d * in[m]);
+            s2 += w * d;
+        } else {
+            s += w * in[m];
+        }
+    }
+    const long long e = b + ey + (long long)I.nely * ex;
+    out[e] = s / I.Hs;
+    if (BWD) out2[e] = I.dv * s2 / I.Hs;
+}
+
+// One pass of the eta search (Sec. 3.2) at the instance's current eta: sums of
+// prj and deta; the last tile takes the Newton step (or the bisection step once
+// Newton has failed) and the stopping test.
+__global__ void kb_eta_pass(BK k, const double* __restrict__ xt, double tol, int maxit) {
+    B_TILE(k)
+    if (S.eta_done) return;
+    const double beta = k.G->beta, eta = S.eta;
+    double v[2] = {0.0, 0.0}, tot[2];
+    if (tx_ < I.nelx && ty_ < I.nely) {
+        const double x = xt[I.el0 + ty_ + (long long)I.nely * tx_];
+        v[0] = b_prj(x, eta, beta);
+        v[1] = b_deta(x, eta, beta);
+    }
+    if (!seg_reduce<2>(k, I.te0, I.ten, &k.counters[inst], v, tot) || threadIdx.x) return;
+    const double nel = (double)I.nel;
+    const double f = tot[0] / nel - I.volfrac;
+    bool done = false;
+    if (S.eta_mode == ETA_NEWTON) {
+        if (fabs(f) <= tol) {
+            done = true;
+        } else if (S.eta_it >= maxit) {
+            S.eta_mode = ETA_BISECT;
+            S.lo = 0.0;
+            S.hi = 1.0;
+            S.eta = 0.5;
+        } else {
+            const double en = eta - f / (tot[1] / nel);
+            S.eta_it += 1;
+            if (!(en >= 0.0 && en <= 1.0)) {  // left [0, 1] (or NaN): bisection on [0, 1]
+                S.eta_mode = ETA_BISECT;
+                S.lo = 0.0;
+                S.hi = 1.0;
+                S.eta = 0.5;
+            } else {
+                S.eta = en;
+            }
+        }
+    } else {
+        if (fabs(f) <= tol || S.hi - S.lo <= 1e-16) {
+            done = true;
+        } else {
+            if (f > 0.0)
+                S.lo = eta;
+            else
+                S.hi = eta;
+            S.eta_it += 1;
+            S.eta_bis += 1;
+            if (S.eta_bis >= 200)
+                done = true;
+            else
+                S.eta = 0.5 * (S.lo + S.hi);
+        }
+    }
+    if (done) {
+        S.eta_done = 1;
+        atomicSub(&k.G->active[LOOP_ETA], 1);
+    }
+}
+
+// xPhys = prj(xTilde, eta) (ft >= 2) or xTilde (ft = 1), dprj, and the change
+// ||xPhys - xOld|| / sqrt(nEl) and volume mean(xPhys); xOld <- xPhys.
+__global__ void kb_project(BK k, int ft, const double* __restrict__ xt, double* __restrict__ xPhys,
+                           double* __restrict__ dprj, double* __restrict__ xOld) {
+    B_TILE(k)
+    const double beta = k.G->beta, eta = S.eta;
+    double v[2] = {0.0, 0.0}, tot[2];
+    if (tx_ < I.nelx && ty_ < I.nely) {
+        const long long e = I.el0 + ty_ + (long long)I.nely * tx_;
+        const double x = xt[e];
+        double xp = x, dp = 1.0;
+        if (ft > 1) {
+            xp = b_prj(x, eta, beta);
+            dp = b_dprj(x, eta, beta);
+        }
+        const double d = xp - xOld[e];
+        v[0] = d * d;
+        v[1] = xp;
+        xPhys[e] = xp;
+        dprj[e] = dp;
+        xOld[e] = xp;
+    }
+    if (!seg_reduce<2>(k, I.te0, I.ten, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.ch = sqrt(tot[0] / (double)I.nel);
+    S.V = tot[1] / (double)I.nel;
+}
+
+// SIMP modulus (Eq. 5) in FP64 (refinement residual) and FP32 (inner solve).
+__global__ void kb_modulus(long long n, const double* __restrict__ xPhys, const BG* G, double E0, double Emin,
+                           double* __restrict__ E64, float* __restrict__ E32) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double e = Emin + pow(xPhys[i], G->penal) * (E0 - Emin);
+    E64[i] = e;
+    E32[i] = (float)e;
+}
+
+// Jacobi diagonal of K (FP32), inverted; 0 at Dirichlet DOFs.
+__global__ void kb_diag(BK k, const KeP<float, 8> ke, const float* __restrict__ E32,
+                        const uint8_t* __restrict__ fixed, float* __restrict__ dinv) {
+    B_TILE(k)
+    (void)S;
+    const int ix = tx_, iy = ty_;
+    if (ix >= I.nnx || iy >= I.nny) return;
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int EXO = q >> 1, EYO = q & 1;
+        const int ex = ix - 1 + EXO, ey = iy - 1 + EYO;
+        if (ex < 0 || ex >= I.nelx || ey < 0 || ey >= I.nely) continue;
+        const float Ee = E32[I.el0 + ey + (long long)I.nely * ex];
+        const int L = local_node(1 - EXO, EYO, 0);
+        d0 += Ee * ke.k[(2 * L) * 8 + 2 * L];
+        d1 += Ee * ke.k[(2 * L + 1) * 8 + 2 * L + 1];
+    }
+    const long long i = 2 * (I.node0 + iy + (long long)I.nny * ix);
+    dinv[i] = fixed[i] ? 0.f : 1.f / d0;
+    dinv[i + 1] = fixed[i + 1] ? 0.f : 1.f / d1;
+}
+
+__global__ void kb_mask(long long n, double* __restrict__ U, const uint8_t* __restrict__ fixed) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && fixed[i]) U[i] = 0.0;
+}
+
+__global__ void kb_begin_solve(BG* G, BS* S, int count, cudaGraphConditionalHandle h_ref) {
+    if (threadIdx.x == 0) {
+        G->active[LOOP_REF] = count;
+        G->active[LOOP_INNER] = 0;
+        cudaGraphSetConditional(h_ref, count > 0 ? 1u : 0u);
+    }
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        S[i].ref_done = 0;
+        S[i].n_ref = 0;
+        S[i].f_has_prev = 0;
+    }
+}
+
+// FP64 refinement test: r = F - K(E64) U on free DOFs; ||r|| / ||F||. Instances
+// at or below rtol (or at max_ref refinements) stop; the others keep r (FP64)
+// and get r32 = (float) r and x32 = 0 for the next inner solve.
+__global__ void kb_resid(BK k, const KeP<double, 8> ke, const double* __restrict__ E64,
+                         const double* __restrict__ U, const double* __restrict__ F,
+                         const uint8_t* __restrict__ fixed, double* __restrict__ r64, float* __restrict__ r32,
+                         float* __restrict__ x32, double rtol, int max_ref) {
+    B_TILE(k)
+    if (S.ref_done) return;
+    double v[2] = {0.0, 0.0}, tot[2];
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        double a[2];
+        bku2<double>(ke, E64 + I.el0, U + 2 * I.node0, tx_, ty_, I.nelx, I.nely, a[0], a[1]);
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const bool f = fixed[i + c] != 0;
+            const double b = f ? 0.0 : F[i + c];
+            const double r = f ? 0.0 : b - a[c];
+            r64[i + c] = r;
+            r32[i + c] = (float)r;
+            x32[i + c] = 0.f;
+            v[0] += r * r;
+            v[1] += b * b;
+        }
+    }
+    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    const double rel = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : 0.0;
+    S.rel_res = rel;
+    if (!isfinite(rel)) k.G->status = (int)TO_ENAN;
+    if (!(rel > rtol) || S.n_ref >= max_ref) {
+        S.ref_done = 1;
+        atomicSub(&k.G->active[LOOP_REF], 1);
+    } else {
+        S.n_ref += 1;
+    }
+}
+
+// Inner PCG start: z = D^-1 r, p = z, rz, ||r||^2 (float-float sums).
+__global__ void kb_inner_init(BK k, const float* __restrict__ dinv, const float* __restrict__ r32,
+                              float* __restrict__ z32, float* __restrict__ p32) {
+    B_TILE(k)
+    if (S.ref_done) return;
+    DotAcc<float> rz, rr;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float r = r32[i + c], z = dinv[i + c] * r;
+            z32[i + c] = z;
+            p32[i + c] = z;
+            rz.add(r, z);
+            rr.add(r, r);
+        }
+    }
+    double v[2] = {rz.value(), rr.value()}, tot[2];
+    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.rz = tot[0];
+    S.irr0 = tot[1];
+    S.inner_it = 0;
+    S.inner_done = tot[1] > 0.0 ? 0 : 1;
+    if (!S.inner_done) atomicAdd(&k.G->active[LOOP_INNER], 1);
+}
+
+// Ap = K(E32) p (Dirichlet rows 0); alpha = rz / p.Ap.
+__global__ void kb_ku32(BK k, const KeP<float, 8> ke, const float* __restrict__ E32,
+                        const float* __restrict__ p32, float* __restrict__ Ap32,
+                        const uint8_t* __restrict__ fixed) {
+    B_TILE(k)
+    if (S.ref_done || S.inner_done) return;
+    DotAcc<float> pap;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        float a[2];
+        bku2<float>(ke, E32 + I.el0, p32 + 2 * I.node0, tx_, ty_, I.nelx, I.nely, a[0], a[1]);
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float y = fixed[i + c] ? 0.f : a[c];
+            Ap32[i + c] = y;
+            pap.add(p32[i + c], y);
+        }
+    }
+    double v[1] = {pap.value()}, tot[1];
+    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    if (tot[0] > 0.0 && isfinite(tot[0])) {
+        S.alpha = S.rz / tot[0];
+    } else {  // breakdown: stop this inner solve, the FP64 test decides
+        S.alpha = 0.0;
+        S.inner_done = 1;
+        atomicSub(&k.G->active[LOOP_INNER], 1);
+    }
+}
+
+// x += alpha p, r -= alpha Ap, z = D^-1 r; stopping test ||r|| <= inner_rtol ||r0||.
+__global__ void kb_inner_update(BK k, const float* __restrict__ dinv, float* __restrict__ x32,
+                                float* __restrict__ r32, float* __restrict__ z32, const float* __restrict__ p32,
+                                const float* __restrict__ Ap32, double inner_rtol, int maxit) {
+    B_TILE(k)
+    if (S.ref_done || S.inner_done) return;
+    const float alpha = (float)S.alpha;
+    DotAcc<float> rr, rz;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            x32[i + c] += alpha * p32[i + c];
+            const float r = r32[i + c] - alpha * Ap32[i + c];
+            r32[i + c] = r;
+            const float z = dinv[i + c] * r;
+            z32[i + c] = z;
+            rr.add(r, r);
+            rz.add(r, z);
+        }
+    }
+    double v[2] = {rr.value(), rz.value()}, tot[2];
+    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.inner_it += 1;
+    S.inner_total += 1;
+    if (!(tot[0] > inner_rtol * inner_rtol * S.irr0) || S.inner_it >= maxit) {
+        S.inner_done = 1;
+        atomicSub(&k.G->active[LOOP_INNER], 1);
+    } else {
+        S.beta_cg = tot[1] / S.rz;
+        S.rz = tot[1];
+    }
+}
+
+// p = z + beta p; sets the inner WHILE condition.
+__global__ void kb_inner_p(BK k, const float* __restrict__ z32, float* __restrict__ p32,
+                           cudaGraphConditionalHandle h) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        k.G->body_exec[LOOP_INNER] += 1ull;
+        cudaGraphSetConditional(h, k.G->active[LOOP_INNER] > 0 ? 1u : 0u);
+    }
+    B_TILE(k)
+    if (S.ref_done || S.inner_done) return;
+    if (tx_ >= I.nnx || ty_ >= I.nny) return;
+    const float b = (float)S.beta_cg;
+    const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+    p32[i] = z32[i] + b * p32[i];
+    p32[i + 1] = z32[i + 1] + b * p32[i + 1];
+}
+
+// Multigrid-preconditioned inner PCG (z from a V-cycle): start p = z, rz,
+// ||r||^2.
+__global__ void kb_mg_init(BK k, const float* __restrict__ r32, const float* __restrict__ z,
+                           float* __restrict__ p32) {
+    B_TILE(k)
+    if (S.ref_done) return;
+    DotAcc<float> rz, rr;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float r = r32[i + c], zz = z[i + c];
+            p32[i + c] = zz;
+            rz.add(r, zz);
+            rr.add(r, r);
+        }
+    }
+    double v[2] = {rz.value(), rr.value()}, tot[2];
+    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.rz = tot[0];
+    S.irr0 = tot[1];
+    S.inner_it = 0;
+    S.inner_done = tot[1] > 0.0 && tot[0] > 0.0 ? 0 : 1;
+    if (!S.inner_done) atomicAdd(&k.G->active[LOOP_INNER], 1);
+}
+
+// x += alpha p, r -= alpha Ap; stopping test ||r|| <= inner_rtol ||r0||.
+__global__ void kb_mg_xr(BK k, float* __restrict__ x32, float* __restrict__ r32, const float* __restrict__ p32,
+                         const float* __restrict__ Ap32, double inner_rtol, int maxit) {
+    B_TILE(k)
+    if (S.ref_done || S.inner_done) return;
+    const float alpha = (float)S.alpha;
+    DotAcc<float> rr;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            x32[i + c] += alpha * p32[i + c];
+            const float r = r32[i + c] - alpha * Ap32[i + c];
+            r32[i + c] = r;
+            rr.add(r, r);
+        }
+    }
+    double v[1] = {rr.value()}, tot[1];
+    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.inner_it += 1;
+    S.inner_total += 1;
+    if (!(tot[0] > inner_rtol * inner_rtol * S.irr0) || S.inner_it >= maxit) {
+        S.inner_done = 1;
+        atomicSub(&k.G->active[LOOP_INNER], 1);
+    }
+}
+
+// rz = r.z after the V-cycle; beta = rz / rz_old.
+__global__ void kb_mg_rz(BK k, const float* __restrict__ r32, const float* __restrict__ z) {
+    B_TILE(k)
+    if (S.ref_done || S.inner_done) return;
+    DotAcc<float> rz;
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+        rz.add(r32[i], z[i]);
+        rz.add(r32[i + 1], z[i + 1]);
+    }
+    double v[1] = {rz.value()}, tot[1];
+    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.beta_cg = tot[0] / S.rz;
+    S.rz = tot[0];
+}
+
+// FP64 outer iteration as a flexible CG with one previous direction: the FP32
+// inner solution d (x32) is K-orthogonalised against the previous direction,
+// p = d + beta p_prev with beta = -(d . K p_prev) / (p_prev . K p_prev), and
+// taken with the exact FP64 line search alpha = (p . r) / (p . K p). Every step
+// minimises the energy norm of the error along p, so the error cannot grow even
+// when an FP32 inner solve is poor (high-contrast designs push the condition
+// number of K far beyond the reach of FP32 refinement).
+__global__ void kb_fcg_beta(BK k, const float* __restrict__ x32, const double* __restrict__ Kp64) {
+    B_TILE(k)
+    if (S.ref_done || !S.f_has_prev) return;
+    double v[1] = {0.0}, tot[1];
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+        v[0] = (double)x32[i] * Kp64[i] + (double)x32[i + 1] * Kp64[i + 1];
+    }
+    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.f_beta = S.f_pkp > 0.0 ? -tot[0] / S.f_pkp : 0.0;
+}
+
+__global__ void kb_fcg_dir(BK k, const float* __restrict__ x32, double* __restrict__ p64) {
+    B_TILE(k)
+    if (S.ref_done) return;
+    if (tx_ >= I.nnx || ty_ >= I.nny) return;
+    const double beta = S.f_has_prev ? S.f_beta : 0.0;
+    const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+    p64[i] = (double)x32[i] + beta * p64[i];
+    p64[i + 1] = (double)x32[i + 1] + beta * p64[i + 1];
+}
+
+// Kp = K(E64) p (Dirichlet rows 0); alpha = (p . r) / (p . Kp).
+__global__ void kb_fcg_kp(BK k, const KeP<double, 8> ke, const double* __restrict__ E64,
+                          const double* __restrict__ p64, const double* __restrict__ r64,
+                          double* __restrict__ Kp64, const uint8_t* __restrict__ fixed) {
+    B_TILE(k)
+    if (S.ref_done) return;
+    double v[2] = {0.0, 0.0}, tot[2];
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        double a[2];
+        bku2<double>(ke, E64 + I.el0, p64 + 2 * I.node0, tx_, ty_, I.nelx, I.nely, a[0], a[1]);
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const double y = fixed[i + c] ? 0.0 : a[c];
+            Kp64[i + c] = y;
+            v[0] += p64[i + c] * r64[i + c];
+            v[1] += p64[i + c] * y;
+        }
+    }
+    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    const bool ok = tot[1] > 0.0 && isfinite(tot[0]) && isfinite(tot[1]);
+    S.f_alpha = ok ? tot[0] / tot[1] : 0.0;
+    S.f_pkp = ok ? tot[1] : 0.0;
+    S.f_has_prev = ok ? 1 : 0;
+}
+
+// U += alpha p in FP64; sets the refinement WHILE condition.
+__global__ void kb_refine(BK k, const double* __restrict__ p64, double* __restrict__ U,
+                          cudaGraphConditionalHandle h) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        k.G->body_exec[LOOP_REF] += 1ull;
+        k.G->active[LOOP_INNER] = 0;
+        cudaGraphSetConditional(h, k.G->active[LOOP_REF] > 0 ? 1u : 0u);
+    }
+    B_TILE(k)
+    if (S.ref_done) return;
+    if (tx_ >= I.nnx || ty_ >= I.nny) return;
+    const double alpha = S.f_alpha;
+    const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+    U[i] += alpha * p64[i];
+    U[i + 1] += alpha * p64[i + 1];
+}
+
+// Compliance c = F^T U (Eq. 3).
+__global__ void kb_compliance(BK k, const double* __restrict__ F, const double* __restrict__ U) {
+    B_TILE(k)
+    double v[1] = {0.0}, tot[1];
+    if (tx_ < I.nnx && ty_ < I.nny) {
+        const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
+        v[0] = F[i] * U[i] + F[i + 1] * U[i + 1];
+    }
+    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.c = tot[0];
+}
+
+// dc = -p (E0 - Emin) xPhys^(p-1) u_e^T Ke u_e (Eq. 6).
+__global__ void kb_sens(BK k, const KeP<double, 8> ke, const double* __restrict__ xPhys,
+                        const double* __restrict__ U, double* __restrict__ dc, double E0, double Emin) {
+    B_TILE(k)
+    (void)S;
+    const int ex = tx_, ey = ty_;
+    if (ex >= I.nelx || ey >= I.nely) return;
+    const int nny = I.nny;
+    double ue[8];
+#pragma unroll
+    for (int M = 0; M < 4; ++M) {
+        const long long n = I.node0 + (ey + 1 - lny(M)) + (long long)nny * (ex + lnx(M));
+        ue[2 * M] = U[2 * n];
+        ue[2 * M + 1] = U[2 * n + 1];
+    }
+    double ce = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) s += ke.k[a * 8 + b] * ue[b];
+        ce += ue[a] * s;
+    }
+    const double p = k.G->penal;
+    const long long e = I.el0 + ey + (long long)I.nely * ex;
+    dc[e] = -p * (E0 - Emin) * pow(xPhys[e], p - 1.0) * ce;
+}
+
+// ocP = x sqrt(max(0, -dc / dV0)); bracket [0, mean(ocP) / f] (Eq. 17).
+__global__ void kb_oc_init(BK k, const double* __restrict__ x, const double* __restrict__ dc,
+                           const double* __restrict__ dV0, double* __restrict__ ocP) {
+    B_TILE(k)
+    double v[1] = {0.0}, tot[1];
+    if (tx_ < I.nelx && ty_ < I.nely) {
+        const long long e = I.el0 + ty_ + (long long)I.nely * tx_;
+        const double o = x[e] * sqrt(fmax(0.0, -dc[e] / dV0[e]));
+        ocP[e] = o;
+        v[0] = o;
+    }
+    if (!seg_reduce<1>(k, I.te0, I.ten, &k.counters[inst], v, tot) || threadIdx.x) return;
+    S.l1 = 0.0;
+    S.l2 = tot[0] / (double)I.nel / I.volfrac;
+    S.lm = 0.0;
+    S.oc_steps = 0;
+    S.oc_grow = 0;
+    if (S.l2 > 0.0) {
+        S.oc_state = OC_EXPAND;
+        atomicAdd(&k.G->active[LOOP_OC], 1);
+    } else {
+        S.oc_state = OC_SKIP;  // nothing to scale: x stays
+    }
+}
+
+// One evaluation of mean(x(lm)): while expanding, at the upper end (doubled
+// while the volume is still exceeded); then bisection of [l1, l2].
+__global__ void kb_oc_pass(BK k, const double* __restrict__ x, const double* __restrict__ ocP, double move,
+                           double tol, int maxit) {
+    B_TILE(k)
+    const int st = S.oc_state;
+    if (st != OC_EXPAND && st != OC_BISECT) return;
+    const double lm = st == OC_EXPAND ? S.l2 : 0.5 * (S.l1 + S.l2);
+    double v[1] = {0.0}, tot[1];
+    if (tx_ < I.nelx && ty_ < I.nely) {
+        const long long e = I.el0 + ty_ + (long long)I.nely * tx_;
+        v[0] = b_oc(x[e], ocP[e], lm, move);
+    }
+    if (!seg_reduce<1>(k, I.te0, I.ten, &k.counters[inst], v, tot) || threadIdx.x) return;
+    const double mean = tot[0] / (double)I.nel;
+    bool done = false;
+    if (st == OC_EXPAND) {
+        if (mean > I.volfrac && S.oc_grow < 60) {
+            S.l1 = S.l2;
+            S.l2 = 2.0 * S.l2;
+            S.oc_grow += 1;
+        } else {
+            S.lm = S.l2;
+            if ((S.l2 - S.l1) / (S.l1 + S.l2) > tol && S.oc_steps < maxit)
+                S.oc_state = OC_BISECT;
+            else
+                done = true;
+        }
+    } else {
+        S.lm = lm;
+        if (mean > I.volfrac)
+            S.l1 = lm;
+        else
+            S.l2 = lm;
+        S.oc_steps += 1;
+        if (!((S.l2 - S.l1) / (S.l1 + S.l2) > tol && S.oc_steps < maxit)) done = true;
+    }
+    if (done) {
+        S.oc_state = OC_DONE;
+        atomicSub(&k.G->active[LOOP_OC], 1);
+    }
+}
+
+__global__ void kb_oc_final(BK k, double* __restrict__ x, const double* __restrict__ ocP, double move) {
+    B_TILE(k)
+    if (S.oc_state != OC_DONE) return;
+    if (tx_ >= I.nelx || ty_ >= I.nely) return;
+    const long long e = I.el0 + ty_ + (long long)I.nely * tx_;
+    x[e] = b_oc(x[e], ocP[e], S.lm, move);
+}
+
+__global__ void kb_iter_end(BG* G, to_continuation pc, to_continuation bc) {
+    G->penal = b_cont(G->penal, pc, G->loop);
+    G->beta = b_cont(G->beta, bc, G->loop);
+}
+
+// Uniform field for the autotuner's timing launches.
+__global__ void kb_fill(long long n, double* __restrict__ a, double v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+__global__ void kb_fill32(long long n, float* __restrict__ a, float v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+__global__ void kb_bench_state(BS* S, int count) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        S[i].ref_done = 0;
+        S[i].inner_done = 0;
+        S[i].rz = 1.0;
+    }
+}
+
+constexpr int INNER_CAP = 1000;  // FP32 inner iterations per refinement
+constexpr int MAX_REFINE = 200;  // FP64 refinements per solve
+
+constexpr int N_CAND = 8;
+constexpr int CAND_TY[N_CAND] = {32, 64, 16, 32, 64, 128, 16, 256};
+constexpr int CAND_TX[N_CAND] = {4, 2, 8, 8, 4, 2, 16, 1};
+
+}  // namespace bt
+}  // namespace topo
+
+using namespace topo;
+using namespace topo::bt;
+
+namespace topo {
+namespace bt {
+
+template <typename T>
+T* balloc(to_batch* b, size_t count) {
+    void* p = nullptr;
+    TOPO_CUDA(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)));
+    b->allocs.push_back(p);
+    return (T*)p;
+}
+
+long long tiles_for(const to_batch* b, int ty, int tx, bool nodes) {
+    long long n = 0;
+    for (const BInst& I : b->hI) {
+        const int nx = nodes ? I.nnx : I.nelx, ny = nodes ? I.nny : I.nely;
+        n += (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+    }
+    return n;
+}
+
+// Tile table of one kind; records each instance's tile range.
+void build_tiles(to_batch* b, int ty, int tx, bool nodes, std::vector<int4>& t) {
+    t.clear();
+    for (int i = 0; i < b->count; ++i) {
+        BInst& I = b->hI[i];
+        const int nx = nodes ? I.nnx : I.nelx, ny = nodes ? I.nny : I.nely;
+        const int first = (int)t.size();
+        for (int x0 = 0; x0 < nx; x0 += tx)
+            for (int y0 = 0; y0 < ny; y0 += ty) t.push_back(make_int4(i, x0, y0, 0));
+        if (nodes) {
+            I.tn0 = first;
+            I.tnn = (int)t.size() - first;
+        } else {
+            I.te0 = first;
+            I.ten = (int)t.size() - first;
+        }
+    }
+}
+
+void upload_tiles(to_batch* b) {
+    std::vector<int4> tn, te;
+    build_tiles(b, b->nty, b->ntx, true, tn);
+    build_tiles(b, b->ety, b->etx, false, te);
+    TOPO_REQUIRE((long long)tn.size() <= b->tile_cap && (long long)te.size() <= b->tile_cap, "tile table overflow");
+    b->n_nt = (int)tn.size();
+    b->n_et = (int)te.size();
+    TOPO_CUDA(cudaMemcpyAsync(b->ntiles, tn.data(), tn.size() * sizeof(int4), cudaMemcpyHostToDevice, b->st));
+    TOPO_CUDA(cudaMemcpyAsync(b->etiles, te.data(), te.size() * sizeof(int4), cudaMemcpyHostToDevice, b->st));
+    TOPO_CUDA(cudaMemcpyAsync(b->dI, b->hI.data(), b->hI.size() * sizeof(BInst), cudaMemcpyHostToDevice, b->st));
+    TOPO_CUDA(cudaStreamSynchronize(b->st));
+    bmg_tiles(b);
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+}
+
+BK node_k(const to_batch* b) {
+    return BK{b->dI, b->dS, b->dG, b->ntiles, b->nty, b->partials, b->tile_cap, b->counters};
+}
+BK elem_k(const to_batch* b) {
+    return BK{b->dI, b->dS, b->dG, b->etiles, b->ety, b->partials, b->tile_cap, b->counters};
+}
+
+// Creates a conditional handle in the graph that `st` is capturing into.
+cudaGraphConditionalHandle make_handle(cudaStream_t st) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    TOPO_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    TOPO_REQUIRE(cs == cudaStreamCaptureStatusActive && g, "stream is not capturing");
+    cudaGraphConditionalHandle h;
+    TOPO_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    return h;
+}
+
+// Appends a WHILE node on h at the capture position of st and captures its
+// body on stream bs with body(bs).
+template <class Fn>
+void add_while(cudaStream_t st, cudaStream_t bs, cudaGraphConditionalHandle h, Fn body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    TOPO_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    TOPO_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    TOPO_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    TOPO_CUDA(cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        body(bs);
+    } catch (...) {
+        cudaStreamEndCapture(bs, &bg);
+        throw;
+    }
+    TOPO_CUDA(cudaStreamEndCapture(bs, &bg));
+}
+
+#define KB_LAUNCH(kern, grid, block, stream, ...)                  \
+    do {                                                           \
+        kern<<<(grid), (block), 0, (stream)>>>(__VA_ARGS__);       \
+        TOPO_CHECK_LAUNCH();                                       \
+    } while (0)
+
+void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U) {
+    const to_params& p = b->p;
+    const BK kn = node_k(b), ke = elem_k(b);
+    const int nb_n = b->n_nt, nb_e = b->n_et, tn = b->nty * b->ntx, te = b->ety * b->etx;
+    const int ft = p.ft;
+    // Each FP32 inner solve restarts from the FP64 residual after at most
+    // INNER_CAP iterations: long FP32 Krylov runs lose orthogonality on
+    // high-contrast designs and can return a correction that raises the FP64
+    // residual; a restarted run still reduces the energy-norm error.
+    const int inner_cap = b->mg ? p.cg_maxit : std::min(p.cg_maxit, INNER_CAP);
+    const int max_ref = MAX_REFINE;
+    cudaStream_t st = b->st;
+    captured_launches_reset();
+    set_capturing(true);
+    cudaGraph_t graph = nullptr;
+    TOPO_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    b->k_static = 0;
+    for (long long& kb : b->k_body) kb = 0;
+    try {
+        const cudaGraphConditionalHandle h_eta = ft == 3 ? make_handle(st) : cudaGraphConditionalHandle{};
+        const cudaGraphConditionalHandle h_ref = make_handle(st);
+        const cudaGraphConditionalHandle h_oc = make_handle(st);
+        KB_LAUNCH(kb_iter_begin, 1, 256, st, b->dG, b->dS, b->count, ft == 3 ? 1 : 0, h_eta);
+        // RL.1: filter, eta, projection, change
+        KB_LAUNCH(kb_filter<false>, nb_e, te, st, ke, b->toff, b->tw, x, nullptr, b->xt, nullptr);
+        if (ft == 3) {
+            b->k_static += captured_launches_reset();
+            add_while(st, b->sb[0], h_eta, [&](cudaStream_t s) {
+                KB_LAUNCH(kb_eta_pass, nb_e, te, s, ke, b->xt, p.newton_tol, p.newton_maxit);
+                KB_LAUNCH(kb_cond, 1, 1, s, b->dG, (int)LOOP_ETA, 1, h_eta);
+            });
+            b->k_body[LOOP_ETA] = captured_launches_reset();
+        }
+        KB_LAUNCH(kb_project, nb_e, te, st, ke, ft, b->xt, xPhys, b->dprj, xOld);
+        // RL.2: modulus, Jacobi diagonal, refinement loop around the FP32 PCG
+        KB_LAUNCH(kb_modulus, div_up(b->nel, 256), 256, st, b->nel, xPhys, b->dG, p.E0, p.Emin, b->E64, b->E32);
+        if (b->mg)
+            bmg_setup(b, st);
+        else
+            KB_LAUNCH(kb_diag, nb_n, tn, st, kn, b->ke32, b->E32, b->fixed, b->dinv);
+        KB_LAUNCH(kb_mask, div_up(2 * b->nnode, 256), 256, st, 2 * b->nnode, U, b->fixed);
+        KB_LAUNCH(kb_begin_solve, 1, 256, st, b->dG, b->dS, b->count, h_ref);
+        b->k_static += captured_launches_reset();
+        add_while(st, b->sb[0], h_ref, [&](cudaStream_t s) {
+            KB_LAUNCH(kb_resid, nb_n, tn, s, kn, b->ke64, b->E64, U, b->F, b->fixed, b->r64, b->r32, b->x32,
+                      p.cg_rtol, max_ref);
+            float* zmg = nullptr;
+            if (b->mg) {
+                zmg = bmg_vcycle(b, s, b->r32, 0);
+                KB_LAUNCH(kb_mg_init, nb_n, tn, s, kn, b->r32, zmg, b->p32);
+            } else {
+                KB_LAUNCH(kb_inner_init, nb_n, tn, s, kn, b->dinv, b->r32, b->z32, b->p32);
+            }
+            const cudaGraphConditionalHandle h_in = make_handle(s);
+            KB_LAUNCH(kb_cond, 1, 1, s, b->dG, (int)LOOP_INNER, 0, h_in);
+            b->k_body[LOOP_REF] = captured_launches_reset();
+            add_while(s, b->sb[1], h_in, [&](cudaStream_t s2) {
+                KB_LAUNCH(kb_ku32, nb_n, tn, s2, kn, b->ke32, b->E32, b->p32, b->Ap32, b->fixed);
+                if (b->mg) {
+                    KB_LAUNCH(kb_mg_xr, nb_n, tn, s2, kn, b->x32, b->r32, b->p32, b->Ap32, p.inner_rtol, inner_cap);
+                    float* z = bmg_vcycle(b, s2, b->r32, 1);
+                    TOPO_REQUIRE(z == zmg, "V-cycle output buffer");
+                    KB_LAUNCH(kb_mg_rz, nb_n, tn, s2, kn, b->r32, z);
+                    KB_LAUNCH(kb_inner_p, nb_n, tn, s2, kn, z, b->p32, h_in);
+                } else {
+                    KB_LAUNCH(kb_inner_update, nb_n, tn, s2, kn, b->dinv, b->x32, b->r32, b->z32, b->p32, b->Ap32,
+                              p.inner_rtol, inner_cap);
+                    KB_LAUNCH(kb_inner_p, nb_n, tn, s2, kn, b->z32, b->p32, h_in);
+                }
+            });
+            b->k_body[LOOP_INNER] = captured_launches_reset();
+            KB_LAUNCH(kb_fcg_beta, nb_n, tn, s, kn, b->x32, b->Kp64);
+            KB_LAUNCH(kb_fcg_dir, nb_n, tn, s, kn, b->x32, b->p64);
+            KB_LAUNCH(kb_fcg_kp, nb_n, tn, s, kn, b->ke64, b->E64, b->p64, b->r64, b->Kp64, b->fixed);
+            KB_LAUNCH(kb_refine, nb_n, tn, s, kn, b->p64, U, h_ref);
+            b->k_body[LOOP_REF] += captured_launches_reset();
+        });
+        // RL.3: compliance, sensitivities, back-filter
+        KB_LAUNCH(kb_compliance, nb_n, tn, st, kn, b->F, U);
+        KB_LAUNCH(kb_sens, nb_e, te, st, ke, b->ke64, xPhys, U, b->dc, p.E0, p.Emin);
+        KB_LAUNCH(kb_filter<true>, nb_e, te, st, ke, b->toff, b->tw, b->dc, b->dprj, b->dcf, b->dV0);
+        // RL.4: OC with the lambda# bracket, continuation
+        KB_LAUNCH(kb_oc_init, nb_e, te, st, ke, x, b->dcf, b->dV0, b->ocP);
+        KB_LAUNCH(kb_cond, 1, 1, st, b->dG, (int)LOOP_OC, 0, h_oc);
+        b->k_static += captured_launches_reset();
+        add_while(st, b->sb[0], h_oc, [&](cudaStream_t s) {
+            KB_LAUNCH(kb_oc_pass, nb_e, te, s, ke, x, b->ocP, p.move, p.oc_tol, p.oc_maxit);
+            KB_LAUNCH(kb_cond, 1, 1, s, b->dG, (int)LOOP_OC, 1, h_oc);
+        });
+        b->k_body[LOOP_OC] = captured_launches_reset();
+        KB_LAUNCH(kb_oc_final, nb_e, te, st, ke, x, b->ocP, p.move);
+        KB_LAUNCH(kb_iter_end, 1, 1, st, b->dG, p.penal_cnt, p.beta_cnt);
+        b->k_static += captured_launches_reset();
+    } catch (...) {
+        set_capturing(false);
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    set_capturing(false);
+    TOPO_CUDA(cudaStreamEndCapture(st, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TOPO_CUDA(e);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = exec;
+    b->cap[0] = x;
+    b->cap[1] = xPhys;
+    b->cap[2] = xOld;
+    b->cap[3] = U;
+}
+
+void sync_in(to_batch* b) {
+    TOPO_CUDA(cudaEventRecord(b->ev_in, b->ust));
+    TOPO_CUDA(cudaStreamWaitEvent(b->st, b->ev_in, 0));
+}
+void sync_out(to_batch* b) {
+    TOPO_CUDA(cudaEventRecord(b->ev_out, b->st));
+    TOPO_CUDA(cudaStreamWaitEvent(b->ust, b->ev_out, 0));
+}
+
+void destroy(to_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b->mg;
+    for (void* p : b->allocs) cudaFree(p);
+    for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev0, b->ev1})
+        if (e) cudaEventDestroy(e);
+    if (b->st) cudaStreamDestroy(b->st);
+    for (cudaStream_t s : b->sb)
+        if (s) cudaStreamDestroy(s);
+    delete b;
+}
+
+}  // namespace bt
+}  // namespace topo
+
+#define TOPO_BATCH_BEGIN try {
+#define TOPO_BATCH_END                                                                     \
+    }                                                                                      \
+    catch (const topo::Error& e) { return topo::api_fail(e.code, e.what()); }              \
+    catch (const std::bad_alloc&) { return topo::api_fail(TO_ENOMEM, "host allocation failed"); } \
+    catch (const std::exception& e) { return topo::api_fail(TO_ECUDA, e.what()); }         \
+    return TO_OK;
+
+extern "C" {
+
+to_status to_batch_init(const to_params* base, int32_t count, const to_instance* inst, const double* F,
+                        const uint8_t* fixed, void* stream, to_batch** out) {
+    if (!base || !inst || !F || !fixed || !out || count < 1) return api_fail(TO_EINVAL, "NULL argument or count < 1");
+    *out = nullptr;
+    if (base->dim != 2) return api_fail(TO_EINVAL, "batched instances are 2D (dim = 2)");
+    if (base->precision != TO_MIXED) return api_fail(TO_EINVAL, "batched solve is TO_MIXED (FP32 + FP64 refinement)");
+    if (base->ftBC != 'N') return api_fail(TO_EINVAL, "batched filter supports 'N' padding only");
+    if (base->ft < 1 || base->ft > 3) return api_fail(TO_EINVAL, "ft must be 1, 2 or 3");
+    if (!(base->inner_rtol > 0.0 && base->inner_rtol < 1.0) || base->cg_maxit < 1 || !(base->cg_rtol > 0.0))
+        return api_fail(TO_EINVAL, "bad solver tolerances");
+    to_batch* b = new to_batch();
+    TOPO_BATCH_BEGIN
+    try {
+        b->p = *base;
+        b->count = count;
+        b->ust = (cudaStream_t)stream;
+        TOPO_CUDA(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+        for (cudaStream_t& s : b->sb) TOPO_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&b->ev_in, &b->ev_out}) TOPO_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        TOPO_CUDA(cudaEventCreate(&b->ev0));
+        TOPO_CUDA(cudaEventCreate(&b->ev1));
+        // instance table and filter taps (Eq. 2: w = max(0, rmin - dist), window +-(ceil(rmin) - 1))
+        std::vector<int2> toff;
+        std::vector<double> tw;
+        b->hI.resize(count);
+        long long el = 0, nd = 0;
+        for (int i = 0; i < count; ++i) {
+            const to_instance& q = inst[i];
+            TOPO_REQUIRE(q.nelx >= 1 && q.nely >= 1, "instance grid must have >= 1 element per axis");
+            TOPO_REQUIRE(q.volfrac > 0.0 && q.volfrac < 1.0, "instance volfrac must be in (0, 1)");
+            TOPO_REQUIRE(q.rmin > 0.0 && q.rmin < 1e4, "instance rmin must be positive");
+            BInst& I = b->hI[i];
+            I = BInst{};
+            I.nelx = q.nelx;
+            I.nely = q.nely;
+            I.nnx = q.nelx + 1;
+            I.nny = q.nely + 1;
+            I.el0 = el;
+            I.node0 = nd;
+            I.nel = (long long)q.nelx * q.nely;
+            I.volfrac = q.volfrac;
+            I.rmin = q.rmin;
+            I.dv = 1.0 / ((double)I.nel * q.volfrac);
+            const int R = (int)std::ceil(q.rmin) - 1;
+            I.tap0 = (int)toff.size();
+            double hs = 0.0;
+            for (int ox = -R; ox <= R; ++ox)
+                for (int oy = -R; oy <= R; ++oy) {
+                    const double w = q.rmin - std::sqrt((double)(ox * ox + oy * oy));
+                    if (w <= 0.0) continue;
+                    toff.push_back(make_int2(ox, oy));
+                    tw.push_back(w);
+                    hs += w;
+                }
+            I.ntap = (int)toff.size() - I.tap0;
+            I.Hs = hs;
+            el += I.nel;
+            nd += (long long)I.nnx * I.nny;
+        }
+        TOPO_REQUIRE(2 * nd < (1LL << 31) && el < (1LL << 31), "batch too large for 32-bit indices");
+        b->nel = el;
+        b->nnode = nd;
+        b->F = F;
+        b->fixed = fixed;
+        // tile tables sized for the largest candidate count
+        long long cap = tiles_for(b, 32, 4, true);
+        for (int c = 0; c < N_CAND; ++c)
+            cap = std::max({cap, tiles_for(b, CAND_TY[c], CAND_TX[c], true), tiles_for(b, CAND_TY[c], CAND_TX[c], false)});
+        b->tile_cap = cap;
+        b->dI = balloc<BInst>(b, count);
+        b->dS = balloc<BS>(b, count);
+        b->dG = balloc<BG>(b, 1);
+        b->toff = balloc<int2>(b, toff.size());
+        b->tw = balloc<double>(b, tw.size());
+        b->ntiles = balloc<int4>(b, cap);
+        b->etiles = balloc<int4>(b, cap);
+        b->partials = balloc<double>(b, 2 * cap);
+        b->counters = balloc<unsigned>(b, count);
+        for (double** a : {&b->xt, &b->dprj, &b->dc, &b->dcf, &b->dV0, &b->ocP, &b->E64}) *a = balloc<double>(b, el);
+        b->E32 = balloc<float>(b, el);
+        for (float** a : {&b->dinv, &b->r32, &b->z32, &b->p32, &b->Ap32, &b->x32}) *a = balloc<float>(b, 2 * nd);
+        for (double** a : {&b->r64, &b->p64, &b->Kp64}) *a = balloc<double>(b, 2 * nd);
+        TOPO_CUDA(cudaMemcpyAsync(b->toff, toff.data(), toff.size() * sizeof(int2), cudaMemcpyHostToDevice, b->st));
+        TOPO_CUDA(cudaMemcpyAsync(b->tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, b->st));
+        TOPO_CUDA(cudaMemsetAsync(b->counters, 0, count * sizeof(unsigned), b->st));
+        std::vector<double> K;
+        element_matrix(2, base->nu, K);
+        for (int i = 0; i < 64; ++i) {
+            b->ke64.k[i] = K[i];
+            b->ke32.k[i] = (float)K[i];
+        }
+        std::vector<BS> s0(count);
+        for (BS& s : s0) {
+            s = BS{};
+            s.eta = base->eta;
+            s.oc_state = OC_SKIP;
+        }
+        TOPO_CUDA(cudaMemcpyAsync(b->dS, s0.data(), count * sizeof(BS), cudaMemcpyHostToDevice, b->st));
+        b->hG = BG{};
+        b->hG.penal = base->penal;
+        b->hG.beta = base->beta;
+        TOPO_CUDA(cudaMemcpyAsync(b->dG, &b->hG, sizeof(BG), cudaMemcpyHostToDevice, b->st));
+        b->hS = s0;
+        if (base->precond == TO_PC_GMG) bmg_create(b);
+        upload_tiles(b);  // synchronizes
+        *out = b;
+    } catch (...) {
+        destroy(b);
+        throw;
+    }
+    TOPO_BATCH_END
+}
+
+to_status to_batch_offsets(const to_batch* b, int64_t* el_off, int64_t* dof_off) {
+    if (!b) return api_fail(TO_EINVAL, "NULL handle");
+    for (int i = 0; i <= b->count; ++i) {
+        const bool end = i == b->count;
+        if (el_off) el_off[i] = end ? b->nel : b->hI[i].el0;
+        if (dof_off) dof_off[i] = 2 * (end ? b->nnode : b->hI[i].node0);
+    }
+    return TO_OK;
+}
+
+to_status to_batch_autotune(to_batch* b, int32_t reps, to_tile_info* info) {
+    if (!b || reps < 1) return api_fail(TO_EINVAL, "NULL handle or reps < 1");
+    TOPO_BATCH_BEGIN
+    sync_in(b);
+    cudaStream_t st = b->st;
+    KB_LAUNCH(kb_fill, div_up(b->nel, 256), 256, st, b->nel, b->xt, 0.5);
+    KB_LAUNCH(kb_fill32, div_up(b->nel, 256), 256, st, b->nel, b->E32, 0.5f);
+    KB_LAUNCH(kb_fill32, div_up(2 * b->nnode, 256), 256, st, 2 * b->nnode, b->p32, 1.0f);
+    double node_us[N_CAND], elem_us[N_CAND];
+    int best_n = 0, best_e = 0;
+    for (int c = 0; c < N_CAND; ++c) {
+        b->nty = b->ety = CAND_TY[c];
+        b->ntx = b->etx = CAND_TX[c];
+        upload_tiles(b);
+        const BK kn = node_k(b), ke = elem_k(b);
+        const int th = CAND_TY[c] * CAND_TX[c];
+        for (int pass = 0; pass < 2; ++pass) {  // pass 0: warm-up
+            KB_LAUNCH(kb_bench_state, 1, 256, st, b->dS, b->count);
+            TOPO_CUDA(cudaEventRecord(b->ev0, st));
+            for (int r = 0; r < reps; ++r)
+                KB_LAUNCH(kb_ku32, b->n_nt, th, st, kn, b->ke32, b->E32, b->p32, b->Ap32, b->fixed);
+            TOPO_CUDA(cudaEventRecord(b->ev1, st));
+            TOPO_CUDA(cudaEventSynchronize(b->ev1));
+            float ms = 0.f;
+            TOPO_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+            node_us[c] = 1e3 * ms / reps;
+            TOPO_CUDA(cudaEventRecord(b->ev0, st));
+            for (int r = 0; r < reps; ++r)
+                KB_LAUNCH(kb_filter<false>, b->n_et, th, st, ke, b->toff, b->tw, b->xt, nullptr, b->dc, nullptr);
+            TOPO_CUDA(cudaEventRecord(b->ev1, st));
+            TOPO_CUDA(cudaEventSynchronize(b->ev1));
+            TOPO_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+            elem_us[c] = 1e3 * ms / reps;
+        }
+        if (node_us[c] < node_us[best_n]) best_n = c;
+        if (elem_us[c] < elem_us[best_e]) best_e = c;
+    }
+    b->nty = CAND_TY[best_n];
+    b->ntx = CAND_TX[best_n];
+    b->ety = CAND_TY[best_e];
+    b->etx = CAND_TX[best_e];
+    upload_tiles(b);
+    // the timing launches left solver state behind: restore the instance states
+    TOPO_CUDA(cudaMemcpyAsync(b->dS, b->hS.data(), b->count * sizeof(BS), cudaMemcpyHostToDevice, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        *info = to_tile_info{};
+        info->node_ty = b->nty;
+        info->node_tx = b->ntx;
+        info->elem_ty = b->ety;
+        info->elem_tx = b->etx;
+        info->n_candidates = N_CAND;
+        for (int c = 0; c < N_CAND; ++c) {
+            info->cand_ty[c] = CAND_TY[c];
+            info->cand_tx[c] = CAND_TX[c];
+            info->node_us[c] = node_us[c];
+            info->elem_us[c] = elem_us[c];
+        }
+    }
+    sync_out(b);
+    TOPO_BATCH_END
+}
+
+to_status to_batch_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U, to_batch_info* info) {
+    if (!b || !x || !xPhys || !xOld || !U) return api_fail(TO_EINVAL, "NULL argument");
+    TOPO_BATCH_BEGIN
+    sync_in(b);
+    if (!b->exec || b->cap[0] != x || b->cap[1] != xPhys || b->cap[2] != xOld || b->cap[3] != U)
+        capture_step(b, x, xPhys, xOld, U);
+    TOPO_CUDA(cudaEventRecord(b->ev0, b->st));
+    TOPO_CUDA(cudaGraphLaunch(b->exec, b->st));
+    TOPO_CUDA(cudaEventRecord(b->ev1, b->st));
+    TOPO_CUDA(cudaMemcpyAsync(&b->hG, b->dG, sizeof(BG), cudaMemcpyDeviceToHost, b->st));
+    TOPO_CUDA(cudaMemcpyAsync(b->hS.data(), b->dS, b->count * sizeof(BS), cudaMemcpyDeviceToHost, b->st));
+    TOPO_CUDA(cudaStreamSynchronize(b->st));
+    const BG& G = b->hG;
+    long long kernels = b->k_static;
+    for (int q = 0; q < 4; ++q) kernels += (long long)G.body_exec[q] * b->k_body[q];
+    count_launches(kernels);
+    sync_out(b);
+    if (info) {
+        *info = to_batch_info{};
+        info->loop = G.loop;
+        info->status = G.status;
+        info->newton_passes = (int)G.body_exec[LOOP_ETA];
+        info->inner_passes = (int)G.body_exec[LOOP_INNER];
+        info->oc_passes = (int)G.body_exec[LOOP_OC];
+        info->penal = G.penal;
+        info->beta = G.beta;
+        float ms = 0.f;
+        TOPO_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        info->ms = ms;
+        info->kernels = kernels;
+        for (const BS& s : b->hS) {
+            info->max_refinements = std::max(info->max_refinements, s.n_ref);
+            info->max_inner_iters = std::max(info->max_inner_iters, s.inner_total);
+            info->max_rel_res = std::max(info->max_rel_res, s.rel_res);
+        }
+        if (info->status == 0 && info->max_rel_res > b->p.cg_rtol) info->status = (int32_t)TO_ENOTCONV;
+    }
+    if (G.status != 0) return api_fail((to_status)G.status, "non-finite residual in a batched solve");
+    TOPO_BATCH_END
+}
+
+to_status to_batch_results(const to_batch* b, double* c, double* V, double* ch, double* eta, double* lm,
+                           int32_t* inner_iters, int32_t* refinements, double* rel_res) {
+    if (!b) return api_fail(TO_EINVAL, "NULL handle");
+    for (int i = 0; i < b->count; ++i) {
+        const BS& s = b->hS[i];
+        if (c) c[i] = s.c;
+        if (V) V[i] = s.V;
+        if (ch) ch[i] = s.ch;
+        if (eta) eta[i] = s.eta;
+        if (lm) lm[i] = s.lm;
+        if (inner_iters) inner_iters[i] = s.inner_total;
+        if (refinements) refinements[i] = s.n_ref;
+        if (rel_res) rel_res[i] = s.rel_res;
+    }
+    return TO_OK;
+}
+
+void to_batch_destroy(to_batch* b) { destroy(b); }
+
+size_t to_sizeof_instance(void) { return sizeof(to_instance); }
+size_t to_sizeof_tile_info(void) { return sizeof(to_tile_info); }
+size_t to_sizeof_batch_info(void) { return sizeof(to_batch_info); }
+
+}  // extern "C"

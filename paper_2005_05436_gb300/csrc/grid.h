@@ -21,6 +21,11 @@ struct DevScalars {
 
 struct Solver;  // solver.cu
 
+// Unit-element stiffness by 2x2(x2) Gauss quadrature, row-major D x D (api.cu).
+void element_matrix(int dim, double nu, std::vector<double>& K);
+// Records msg as the thread's last error and returns s (api.cu).
+to_status api_fail(to_status s, const std::string& msg);
+
 }  // namespace topo
 
 struct to_grid {

@@ -149,3 +149,81 @@ class Design:
     @property
     def loop(self):
         return self.st.loop
+
+
+class Batch:
+    """A to_batch handle: uneven 2D instances advanced together (to_batch_init ...
+    to_batch_destroy). F and fixed are concatenated over the instances' DOFs;
+    the state tensors x, xPhys, xOld, U are created here in the same layout."""
+
+    def __init__(self, params: L.Params, instances, F, fixed, x0, stream=None):
+        self.lib = L.load()
+        self.params = params
+        self.count = len(instances)
+        arr = (L.Instance * self.count)()
+        for k, (nelx, nely, volfrac, rmin) in enumerate(instances):
+            arr[k] = L.Instance(int(nelx), int(nely), float(volfrac), float(rmin))
+        self.instances = arr
+        self.nel = sum(int(a) * int(b) for a, b, _, _ in instances)
+        self.ndof = sum(2 * (int(a) + 1) * (int(b) + 1) for a, b, _, _ in instances)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.F = F
+        self.fixed = fixed
+        h = C.c_void_p()
+        L.check(self.lib.to_batch_init(C.byref(params), self.count, arr,
+                                       _ptr(F, torch.float64, self.ndof, "F"),
+                                       _ptr(fixed, torch.uint8, self.ndof, "fixed"),
+                                       C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        el = (C.c_int64 * (self.count + 1))()
+        dof = (C.c_int64 * (self.count + 1))()
+        L.check(self.lib.to_batch_offsets(self.h, el, dof))
+        self.el_off = list(el)
+        self.dof_off = list(dof)
+        dev = F.device
+        _ptr(x0, torch.float64, self.nel, "x0")
+        self.x = x0.clone()
+        self.xPhys = x0.clone()
+        self.xOld = torch.ones(self.nel, dtype=torch.float64, device=dev)
+        self.U = torch.zeros(self.ndof, dtype=torch.float64, device=dev)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.to_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, reps=10):
+        info = L.TileInfo()
+        L.check(self.lib.to_batch_autotune(self.h, int(reps), C.byref(info)))
+        n = info.n_candidates
+        return {"node": (info.node_ty, info.node_tx), "elem": (info.elem_ty, info.elem_tx),
+                "candidates": [(info.cand_ty[k], info.cand_tx[k]) for k in range(n)],
+                "node_us": [info.node_us[k] for k in range(n)], "elem_us": [info.elem_us[k] for k in range(n)]}
+
+    def step(self, check=True):
+        info = L.BatchInfo()
+        s = self.lib.to_batch_step(self.h, C.c_void_p(self.x.data_ptr()), C.c_void_p(self.xPhys.data_ptr()),
+                                   C.c_void_p(self.xOld.data_ptr()), C.c_void_p(self.U.data_ptr()),
+                                   C.byref(info))
+        if check:
+            L.check(s)
+        return {k: getattr(info, k) for k, _ in L.BatchInfo._fields_ if not k.startswith("_")}
+
+    def results(self):
+        n = self.count
+        c, V, ch, eta, lm, rr = ((C.c_double * n)() for _ in range(6))
+        it, ref = (C.c_int32 * n)(), (C.c_int32 * n)()
+        L.check(self.lib.to_batch_results(self.h, c, V, ch, eta, lm, it, ref, rr))
+        return {"c": list(c), "V": list(V), "ch": list(ch), "eta": list(eta), "lm": list(lm),
+                "inner_iters": list(it), "refinements": list(ref), "rel_res": list(rr)}
+
+    def instance(self, k, t):
+        """The slice of a concatenated element (nEl-long) or DOF (nDof-long) tensor for instance k."""
+        off = self.el_off if t.numel() == self.nel else self.dof_off
+        return t[off[k]:off[k + 1]]

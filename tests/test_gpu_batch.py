@@ -1,0 +1,167 @@
+"""Batched uneven 2D instances against the FP64 oracle, instance by instance.
+
+One to_batch_step advances every instance by one design iteration with one
+CUDA-graph launch; each instance must follow the oracle's own design_step
+(filter, eta Newton, projection, direct solve, sensitivities, back-filter, OC,
+continuation) to the tolerances of the single-grid parity tests, with the
+batched FP32 + FP64-refinement solve run to 1e-12 (1e-11 where the FP64
+residual of a soft design floors near 2e-12).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import topopt_oracle as O
+from paper_2005_05436_gb300 import inputs as I
+from tests._util import rel, to_cuda
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2005_05436_gb300 import build
+    build.build()
+
+
+def _batch(insts, **kw):
+    from paper_2005_05436_gb300 import TO_MIXED, default_params
+    from paper_2005_05436_gb300.topopt import Batch
+    p = default_params(2, 8, 4, precision=TO_MIXED, **kw)
+    F = np.concatenate([q.F for q in insts])
+    fixed = np.concatenate([q.fixed for q in insts])
+    x0 = np.concatenate([I.initial_design(q.nelx * q.nely, q.volfrac) for q in insts])
+    b = Batch(p, [(q.nelx, q.nely, q.volfrac, q.rmin) for q in insts], to_cuda(F), to_cuda(fixed),
+              to_cuda(x0))
+    return b, p
+
+
+def _oracle_params(p, q):
+    cnt = lambda c: (c.istart, c.maxpar, c.isteps, c.delta)  # noqa: E731
+    return O.Params.parity(nelx=q.nelx, nely=q.nely, nelz=0, volfrac=q.volfrac, penal=p.penal,
+                           rmin=q.rmin, beta=p.beta, eta=p.eta, move=p.move, ft=p.ft, ftBC="N",
+                           penal_cnt=cnt(p.penal_cnt), beta_cnt=cnt(p.beta_cnt),
+                           penal_kind="add" if p.penal_cnt.kind == 0 else "mul",
+                           beta_kind="add" if p.beta_cnt.kind == 0 else "mul")
+
+
+def _run(insts, n_iter, **kw):
+    b, p = _batch(insts, **kw)
+    Ke = O.element_stiffness(2)
+    ops = [_oracle_params(p, q) for q in insts]
+    states = [O.initial_state(op) for op in ops]
+    worst = 0.0
+    for it in range(n_iter):
+        info = b.step()
+        res = b.results()
+        assert info["loop"] == it + 1
+        assert info["max_rel_res"] <= p.cg_rtol
+        xphys = b.xPhys.cpu().numpy()
+        x = b.x.cpu().numpy()
+        for k, q in enumerate(insts):
+            ref = O.design_step(ops[k], states[k], q.F, q.fixed, None, Ke)
+            sl = slice(b.el_off[k], b.el_off[k + 1])
+            e_x = rel(xphys[sl], states[k].xphys)
+            worst = max(worst, e_x)
+            assert e_x <= 1e-8, (it, k, e_x)
+            assert rel(x[sl], states[k].x) <= 1e-8, (it, k)
+            assert abs(res["c"][k] - ref["c"]) <= 1e-8 * abs(ref["c"]), (it, k, res["c"][k], ref["c"])
+            assert abs(res["eta"][k] - ref["eta"]) <= 1e-9, (it, k)
+            assert abs(res["V"][k] - ref["V"]) <= 1e-10
+            assert abs(res["ch"][k] - ref["ch"]) <= 1e-8 * max(1.0, ref["ch"])
+        assert info["penal"] == ref["penal"] and info["beta"] == ref["beta"]
+    return b, worst
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "gmg"])
+def test_uneven_batch_matches_oracle(precond):
+    """Six uneven instances (nelx 12..40, aspect 2..4, own volfrac, rmin, loads,
+    supports) for 8 design iterations in parity mode, with the Jacobi and the
+    batched multigrid preconditioner."""
+    from paper_2005_05436_gb300 import TO_PC_GMG, TO_PC_JACOBI
+    insts = I.batched_instances(6, seed=11, nelx_range=(12, 40))
+    # filter windows from 1 tap to 7x7 (the 0.02 nelx radius of the generator is
+    # below 1 at these sizes, which makes the filter the identity)
+    insts = [dataclasses.replace(q, rmin=r) for q, r in zip(insts, (0.5, 1.2, 1.5, 2.4, 3.1, 4.0))]
+    assert len({(q.nelx, q.nely) for q in insts}) > 3
+    _run(insts, 8, newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=20000,
+         precond=TO_PC_GMG if precond == "gmg" else TO_PC_JACOBI)
+
+
+def test_batch_continuation_and_paper_tolerances():
+    """Continuation of p (additive) and beta (doubling) every 3 iterations."""
+    from paper_2005_05436_gb300 import TO_PC_GMG
+    insts = [dataclasses.replace(q, rmin=1.8) for q in I.batched_instances(4, seed=5, nelx_range=(10, 30))]
+    _run(insts, 7, penal=1.0, penal_cnt=(1, 3.0, 3, 0.5), beta_cnt=(1, 16.0, 3, 2.0, 1),
+         newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-11, cg_maxit=20000, precond=TO_PC_GMG)
+
+
+def test_batch_gmg_odd_grids_and_deep_hierarchies():
+    """Multigrid on odd grids (ceil coarsening with children outside the grid)
+    and instances of different depth in one batch: 5 iterations vs the oracle."""
+    from paper_2005_05436_gb300 import TO_PC_GMG
+    base = I.batched_instances(4, seed=21, nelx_range=(20, 90))
+    sizes = [(37, 13), (61, 23), (90, 31), (25, 9)]
+    insts = []
+    for q, (nx, ny) in zip(base, sizes):
+        F, fixed = I.mbb_half_beam(nx, ny)
+        insts.append(dataclasses.replace(q, nelx=nx, nely=ny, rmin=2.0, F=F, fixed=fixed))
+    _run(insts, 5, newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-11, cg_maxit=20000, precond=TO_PC_GMG)
+
+
+def test_single_instance_batch_and_ft1():
+    insts = I.batched_instances(1, seed=2, nelx_range=(20, 20))
+    _run(insts, 4, ft=1, newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=20000)
+
+
+def test_autotune_keeps_results():
+    """The tile shape changes only the grouping of partial sums: two batches run
+    with different shapes agree to rounding."""
+    insts = I.batched_instances(5, seed=3, nelx_range=(16, 48))
+    kw = dict(cg_rtol=1e-10, cg_maxit=20000)
+    b1, _ = _batch(insts, **kw)
+    b2, _ = _batch(insts, **kw)
+    tune = b2.autotune(reps=3)
+    assert len(tune["candidates"]) == 8
+    assert tune["node"] in tune["candidates"] and tune["elem"] in tune["candidates"]
+    assert all(t > 0 for t in tune["node_us"] + tune["elem_us"])
+    for _ in range(3):
+        b1.step()
+        b2.step()
+    assert rel(b2.xPhys.cpu().numpy(), b1.xPhys.cpu().numpy()) <= 1e-9
+    r1, r2 = b1.results(), b2.results()
+    assert np.allclose(r2["c"], r1["c"], rtol=1e-9, atol=0)
+
+
+def test_one_graph_launch_per_iteration_counts_its_kernels():
+    from paper_2005_05436_gb300 import load
+    lib = load()
+    insts = I.batched_instances(3, seed=9, nelx_range=(12, 24))
+    b, _ = _batch(insts, cg_rtol=1e-8, cg_maxit=20000)
+    b.step()  # captures the graph
+    k0 = lib.to_kernel_launches()
+    info = b.step()
+    assert lib.to_kernel_launches() - k0 == info["kernels"] > 0
+    assert info["inner_passes"] >= info["max_inner_iters"] > 0
+    assert info["oc_passes"] > 0 and info["newton_passes"] > 0
+
+
+def test_bad_arguments_are_rejected():
+    import ctypes as C
+    from paper_2005_05436_gb300 import TO_FP64, TO_MIXED, TopoptError, default_params
+    from paper_2005_05436_gb300.topopt import Batch
+    insts = I.batched_instances(2, seed=1, nelx_range=(10, 12))
+    F = to_cuda(np.concatenate([q.F for q in insts]))
+    fixed = to_cuda(np.concatenate([q.fixed for q in insts]))
+    x0 = to_cuda(np.concatenate([I.initial_design(q.nelx * q.nely, q.volfrac) for q in insts]))
+    shapes = [(q.nelx, q.nely, q.volfrac, q.rmin) for q in insts]
+    with pytest.raises(TopoptError):
+        Batch(default_params(2, 8, 4, precision=TO_FP64), shapes, F, fixed, x0)
+    with pytest.raises(TopoptError):
+        Batch(default_params(2, 8, 4, precision=TO_MIXED, ftBC="D"), shapes, F, fixed, x0)
+    bad = [(0, 4, 0.3, 1.5)] + shapes[1:]
+    with pytest.raises((TopoptError, ValueError)):
+        Batch(default_params(2, 8, 4, precision=TO_MIXED), bad, F, fixed, x0)
+    assert C.sizeof(C.c_int) == 4
