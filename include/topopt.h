@@ -372,7 +372,59 @@ to_status to_batch_results(const to_batch* b, double* c, double* V, double* ch, 
 
 void to_batch_destroy(to_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper): a small 3D convolutional
+ * encoder-decoder, trained on (xPhys, F, U) triples that the method itself
+ * produces, predicts a displacement direction from the node density and the
+ * load; the state solve then starts from its energy-optimal multiple (see
+ * to_learned_warm_start). The converged relative residual is unchanged: only
+ * the starting point, and so the iteration count, can differ.
+ *
+ * Network (levels 3, base channels c, 3x3x3 convolutions with zero padding,
+ * 2x2x2 mean pooling, nearest 2x upsampling, additive skips):
+ *   e0 = relu(conv(relu(conv(x, 4->c)), c->c))
+ *   e1 = relu(conv(relu(conv(pool(e0), c->2c)), 2c->2c))
+ *   e2 = relu(conv(relu(conv(pool(e1), 2c->4c)), 4c->4c))
+ *   d1 = relu(conv(relu(conv(up(e2), 4c->2c)) + e1, 2c->2c))
+ *   d0 = relu(conv(relu(conv(up(d1), 2c->c)) + e0, c->c))
+ *   y  = conv(d0, c->3)
+ * Tensors are device FP32 arrays [N][D][H][W][C] (channels last) with D, H, W
+ * multiples of 4. Parameters: one flat FP32 vector, layer by layer
+ * W[27][cin][cout] then b[cout], tap t = (dx+1)*9 + (dy+1)*3 + (dz+1).
+ * ------------------------------------------------------------------------ */
+
+typedef struct to_net to_net;
+
+typedef struct to_net_cfg {
+    int32_t base;   /* channels of the first level (16): a multiple of 4, at most 64 */
+    int32_t bf16;   /* 1: activations and convolution weights in BF16 (products
+                       accumulated in FP32); 0: FP32 throughout */
+    int32_t in_ch;  /* 4: node density and the three load components */
+    int32_t out_ch; /* 3: the displacement direction */
+} to_net_cfg;
+
+/* Creates a network with all parameters 0 (set them with to_net_set_params). */
+to_status to_net_create(const to_net_cfg* cfg, void* stream, to_net** out);
+int64_t to_net_param_count(const to_net* net);
+/* theta: device FP32 [to_net_param_count]; resets the Adam moments. */
+to_status to_net_set_params(to_net* net, const float* theta);
+to_status to_net_get_params(const to_net* net, float* theta);
+/* y[N][D][H][W][3] = network(x[N][D][H][W][4]). */
+to_status to_net_forward(to_net* net, const float* x, int32_t N, int32_t D, int32_t H, int32_t W, float* y);
+/* Adds the gradient of L = mean over valid entries of (y - target)^2 (mask:
+ * uint8 [N][D][H][W], 1 = valid voxel) to the internal gradient; loss (host
+ * out, may be NULL) receives L. */
+to_status to_net_accumulate(to_net* net, const float* x, const float* target, const uint8_t* mask, int32_t N,
+                            int32_t D, int32_t H, int32_t W, double* loss);
+to_status to_net_get_grad(const to_net* net, float* grad);
+to_status to_net_zero_grad(to_net* net);
+/* One Adam step (bias-corrected) with gradient grad_scale * internal gradient;
+ * the internal gradient is zeroed. */
+to_status to_net_adam(to_net* net, double lr, double beta1, double beta2, double eps, double grad_scale);
+void to_net_destroy(to_net* net);
+
 /* Struct sizes, for bindings that mirror these layouts. */
+size_t to_sizeof_net_cfg(void);
 size_t to_sizeof_instance(void);
 size_t to_sizeof_tile_info(void);
 size_t to_sizeof_batch_info(void);

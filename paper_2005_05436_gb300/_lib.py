@@ -82,6 +82,10 @@ class BatchInfo(C.Structure):
                 ("penal", C.c_double), ("beta", C.c_double), ("ms", C.c_double), ("kernels", C.c_int64)]
 
 
+class NetCfg(C.Structure):
+    _fields_ = [("base", C.c_int32), ("bf16", C.c_int32), ("in_ch", C.c_int32), ("out_ch", C.c_int32)]
+
+
 class TopoptError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -118,6 +122,18 @@ _SIGS = {
     "to_batch_results": (C.c_int, [P, P, P, P, P, P, P, P, P]),
     "to_batch_destroy": (None, [P]),
     "to_sizeof_instance": (C.c_size_t, []),
+    "to_sizeof_net_cfg": (C.c_size_t, []),
+    "to_net_create": (C.c_int, [C.POINTER(NetCfg), P, C.POINTER(P)]),
+    "to_net_param_count": (C.c_int64, [P]),
+    "to_net_set_params": (C.c_int, [P, P]),
+    "to_net_get_params": (C.c_int, [P, P]),
+    "to_net_forward": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]),
+    "to_net_accumulate": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_double)]),
+    "to_net_get_grad": (C.c_int, [P, P]),
+    "to_net_zero_grad": (C.c_int, [P]),
+    "to_net_adam": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "to_net_destroy": (None, [P]),
     "to_sizeof_tile_info": (C.c_size_t, []),
     "to_sizeof_batch_info": (C.c_size_t, []),
 }
@@ -140,6 +156,7 @@ def load(path=LIB_PATH):
     assert lib.to_sizeof_params() == C.sizeof(Params), "to_params layout mismatch"
     assert lib.to_sizeof_state() == C.sizeof(State), "to_state layout mismatch"
     assert lib.to_sizeof_instance() == C.sizeof(Instance), "to_instance layout mismatch"
+    assert lib.to_sizeof_net_cfg() == C.sizeof(NetCfg), "to_net_cfg layout mismatch"
     assert lib.to_sizeof_tile_info() == C.sizeof(TileInfo), "to_tile_info layout mismatch"
     assert lib.to_sizeof_batch_info() == C.sizeof(BatchInfo), "to_batch_info layout mismatch"
     assert lib.to_sizeof_iter_info() == C.sizeof(IterInfo), "to_iter_info layout mismatch"
