@@ -146,6 +146,10 @@ typedef struct to_iter_info {
     double rel_res;         /* final FP64 relative residual of the solve */
     double t_filter_ms, t_solve_ms, t_sens_ms, t_oc_ms;  /* CUDA-event phase times */
     double t_setup_ms, t_krylov_ms, t_resid_ms;          /* split of t_solve_ms */
+    double t_warm_ms;       /* learned warm start (inside t_solve_ms), 0 without a network */
+    double warm_a, warm_b;  /* its starting point: warm_a U_prev + warm_b U_net */
+    double warm_err_prev;   /* energy-norm error of U_prev relative to that of U = 0: ||U_prev - U||_K^2 / ||U||_K^2 */
+    double warm_err;        /* the same for the warm start actually used (<= warm_err_prev) */
 } to_iter_info;
 
 /* Thread-local message of the last failing call ("" if none). */
@@ -422,6 +426,23 @@ to_status to_net_zero_grad(to_net* net);
  * the internal gradient is zeroed. */
 to_status to_net_adam(to_net* net, double lr, double beta1, double beta2, double eps, double grad_scale);
 void to_net_destroy(to_net* net);
+
+/* Attaches a network to a 3D grid (NULL detaches; the grid does not own it):
+ * every to_step then starts its state solve from the minimiser of the
+ * potential energy 1/2 U^T K U - F^T U over span{U, U_net}, U the previous
+ * solution and U_net the network's output on the step's xPhys (a 2 x 2
+ * Rayleigh-Ritz step with FP64 operator products; U is kept when the network
+ * adds nothing). The solve still runs to cg_rtol. */
+to_status to_set_warm_start(to_grid* g, to_net* net);
+/* Network input of the grid at xPhys: x[D][H][W][4] on the node grid padded
+ * to multiples of 4 (D = nnx, H = nnz, W = nny rounded up): the mean density
+ * of the elements around each node (-1 at nodes with a Dirichlet DOF) and
+ * F / max|F|; zero in the padding.
+ * dims (host out [3], may be NULL) = D, H, W; x = NULL only queries dims. */
+to_status to_learned_features(to_grid* g, const double* xPhys, float* x, int32_t* dims);
+/* Training target for displacements U: t[D][H][W][3] = U / rms(U) on the
+ * nodes, 0 in the padding; mask[D][H][W] = 1 on nodes. */
+to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask);
 
 /* Struct sizes, for bindings that mirror these layouts. */
 size_t to_sizeof_net_cfg(void);

@@ -59,7 +59,8 @@ class IterInfo(C.Structure):
                 ("beta", C.c_double), ("eta", C.c_double), ("lm", C.c_double),
                 ("rel_res", C.c_double), ("t_filter_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double), ("t_setup_ms", C.c_double),
-                ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double)]
+                ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_warm_ms", C.c_double), ("warm_a", C.c_double), ("warm_b", C.c_double),
+                ("warm_err_prev", C.c_double), ("warm_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,6 +135,9 @@ _SIGS = {
     "to_net_zero_grad": (C.c_int, [P]),
     "to_net_adam": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
     "to_net_destroy": (None, [P]),
+    "to_set_warm_start": (C.c_int, [P, P]),
+    "to_learned_features": (C.c_int, [P, P, P, P]),
+    "to_learned_target": (C.c_int, [P, P, P, P]),
     "to_sizeof_tile_info": (C.c_size_t, []),
     "to_sizeof_batch_info": (C.c_size_t, []),
 }

@@ -361,6 +361,7 @@ void to_destroy(to_grid* g) {
     if (!g) return;
     if (g->st) cudaStreamSynchronize(g->st);
     solver_free(g);
+    warm_free(g);
     for (void* p : g->allocs) cudaFree(p);
     if (g->hs) cudaFreeHost(g->hs);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
@@ -530,6 +531,14 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     TOPO_CUDA(cudaEventRecord(g->ev_t[1], st));
     // RL.2 modulus and state solve (warm start from s->U)
     launch_modulus<double>(d.nel, s->xPhys, s->penal, p.E0, p.Emin, g->E, st);
+    double wen[2] = {0.0, 0.0};
+    if (g->net) {
+        double coef[2] = {1.0, 0.0}, wms = 0.0;
+        learned_warm_start(g, s->xPhys, s->U, coef, &wms, wen);
+        it.warm_a = coef[0];
+        it.warm_b = coef[1];
+        it.t_warm_ms = wms;
+    }
     to_solve_info si{};
     const to_status sst = solve_state(g, g->F, s->U, &si);
     TOPO_CUDA(cudaEventRecord(g->ev_t[2], st));
@@ -555,6 +564,10 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     it.n_refine = si.refinements;
     it.rel_res = si.rel_res;
     it.c = h.c;
+    if (g->net && h.c > 0.0) {  // energy errors relative to the zero start: (E(U) - E*) / (-E*), E* = -c / 2
+        it.warm_err_prev = (wen[0] + 0.5 * h.c) / (0.5 * h.c);
+        it.warm_err = (wen[1] + 0.5 * h.c) / (0.5 * h.c);
+    }
     it.V = h.change[1] / (double)d.nel;
     it.ch = std::sqrt(h.change[0]) / std::sqrt((double)d.nel);
     if (p.ft > 1) {

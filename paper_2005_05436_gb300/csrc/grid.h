@@ -78,6 +78,8 @@ struct to_grid {
     bool use_tc = false;       // the FP32 fine operator runs on tensor cores
 
     topo::Solver* solver = nullptr;
+    to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned
+    void* warm = nullptr;      // its workspace (warm.cu)
 };
 
 namespace topo {
@@ -96,6 +98,8 @@ template <>
 inline const KeP<float, 8>& grid_ke2<float>(const to_grid* g) { return g->ke2f; }
 
 void grid_sync_in(to_grid* g);
+void warm_free(to_grid* g);
+void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy);
 void grid_sync_out(to_grid* g);
 void solver_init(to_grid* g);
 void solver_free(to_grid* g);

@@ -605,6 +605,24 @@ void destroy_net(to_net* n) {
 
 }  // namespace
 
+namespace topo {
+// Forward pass on the caller's stream (for the warm start inside to_step).
+void net_forward_on(to_net* n, const float* x, int N, int D, int H, int W, float* y, cudaStream_t st) {
+    check_shape(n, N, D, H, W);
+    const Shape s{N, D, H, W};
+    TOPO_CUDA(cudaEventRecord(n->ev_in, st));
+    TOPO_CUDA(cudaStreamWaitEvent(n->st, n->ev_in, 0));
+    ensure_ws(n, s);
+    if (n->cfg.bf16)
+        forward<bf16>(n, x, s);
+    else
+        forward<float>(n, x, s);
+    TOPO_CUDA(cudaMemcpyAsync(y, n->y, s.vox() * 3 * sizeof(float), cudaMemcpyDeviceToDevice, n->st));
+    TOPO_CUDA(cudaEventRecord(n->ev_out, n->st));
+    TOPO_CUDA(cudaStreamWaitEvent(st, n->ev_out, 0));
+}
+}  // namespace topo
+
 #define TOPO_NET_BEGIN try {
 #define TOPO_NET_END                                                                       \
     }                                                                                      \

@@ -1,0 +1,244 @@
+// The learned warm start inside the design iteration (no counterpart in the
+// paper): node features -> network -> displacement direction U_h, and the
+// starting point of the state solve is the minimiser of the potential energy
+// 1/2 U^T K U - F^T U over span{U_prev, U_h} (a 2 x 2 Rayleigh-Ritz step with
+// FP64 operator products). Its energy never exceeds that of U_prev, and the
+// solve that follows runs to the same tolerance, so the solution does not
+// depend on the network; only the iteration count can.
+#include <cmath>
+
+#include "grid.h"
+
+namespace topo {
+
+void net_forward_on(to_net* n, const float* x, int N, int D, int H, int W, float* y, cudaStream_t st);  // net.cu
+
+namespace {
+
+struct WarmWS {
+    int D = 0, H = 0, W = 0;
+    float *x = nullptr, *y = nullptr;
+    double *Uh = nullptr, *KUh = nullptr, *Up = nullptr, *KUp = nullptr, *dots = nullptr, *hdots = nullptr;
+    unsigned* fmax = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+inline int pad4(int n) { return (n + 3) / 4 * 4; }
+
+__global__ void kw_absmax(long long n, const double* __restrict__ F, unsigned* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, __float_as_uint((float)fabs(F[i])));  // non-negative floats order as integers
+}
+
+// Network input on the padded node grid [D = nnx][H = nnz][W = nny] (the node
+// numbering's order): the mean physical density of the elements around the node
+// (-1 at nodes with a Dirichlet DOF, so that supports are visible to the
+// network) and the load scaled by 1 / max |F|; zero in the padding.
+__global__ void kw_features(Dims d, int D, int H, int W, const double* __restrict__ xPhys,
+                            const double* __restrict__ F, const uint8_t* __restrict__ fixed,
+                            const unsigned* __restrict__ fmax, float* __restrict__ x) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (long long)D * H * W) return;
+    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ix < d.nnx && iz < d.nnz && iy < d.nny) {
+        double s = 0.0;
+        int cnt = 0;
+        for (int o = 0; o < 8; ++o) {
+            const int ex = ix - 1 + (o >> 2), ez = iz - 1 + ((o >> 1) & 1), ey = iy - 1 + (o & 1);
+            if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) continue;
+            s += xPhys[ey + (long long)d.nely * (ez + (long long)d.nelz * ex)];
+            ++cnt;
+        }
+        const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
+        const float fm = __uint_as_float(*fmax);
+        const float sc = fm > 0.f ? 1.f / fm : 0.f;
+        const bool sup = fixed[3 * n] || fixed[3 * n + 1] || fixed[3 * n + 2];
+        f[0] = sup ? -1.f : (cnt ? (float)(s / cnt) : 0.f);
+        for (int c = 0; c < 3; ++c) f[1 + c] = (float)F[3 * n + c] * sc;
+    }
+    for (int c = 0; c < 4; ++c) x[v * 4 + c] = f[c];
+}
+
+// Training target: U / rms(U) on the padded node grid and the node mask.
+__global__ void kw_target(Dims d, int D, int H, int W, const double* __restrict__ U, const double* __restrict__ sumsq,
+                          float* __restrict__ t, uint8_t* __restrict__ mask) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (long long)D * H * W) return;
+    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
+    const bool in = ix < d.nnx && iz < d.nnz && iy < d.nny;
+    const double ss = *sumsq;
+    const double inv = ss > 0.0 ? 1.0 / sqrt(ss / (double)d.ndof) : 0.0;
+    const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
+    for (int c = 0; c < 3; ++c) t[v * 3 + c] = in ? (float)(U[3 * n + c] * inv) : 0.f;
+    mask[v] = in ? 1 : 0;
+}
+
+__global__ void kw_crop(Dims d, int D, int H, int W, const float* __restrict__ y, const uint8_t* __restrict__ fixed,
+                        double* __restrict__ Uh) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.nnodes) return;
+    const int iy = (int)(n % d.nny), iz = (int)((n / d.nny) % d.nnz), ix = (int)(n / ((long long)d.nny * d.nnz));
+    const long long v = ((long long)ix * H + iz) * W + iy;
+    for (int c = 0; c < 3; ++c) Uh[3 * n + c] = fixed[3 * n + c] ? 0.0 : (double)y[v * 3 + c];
+}
+
+__global__ void kw_combine(long long n, double a, const double* __restrict__ Up, double b,
+                           const double* __restrict__ Uh, double* __restrict__ U) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) U[i] = a * Up[i] + b * Uh[i];
+}
+
+template <typename T>
+T* walloc(to_grid* g, long long count) {
+    void* p = nullptr;
+    TOPO_CUDA(cudaMalloc(&p, std::max<long long>(count, 1) * sizeof(T)));
+    g->allocs.push_back(p);
+    return (T*)p;
+}
+
+WarmWS* warm_ws(to_grid* g) {
+    if (g->warm) return (WarmWS*)g->warm;
+    TOPO_REQUIRE(g->d.dim == 3, "the learned warm start works on 3D grids");
+    WarmWS* w = new WarmWS();
+    g->warm = w;
+    w->D = pad4(g->d.nnx);
+    w->H = pad4(g->d.nnz);
+    w->W = pad4(g->d.nny);
+    const long long V = (long long)w->D * w->H * w->W;
+    w->x = walloc<float>(g, V * 4);
+    w->y = walloc<float>(g, V * 3);
+    for (double** a : {&w->Uh, &w->KUh, &w->Up, &w->KUp}) *a = walloc<double>(g, g->d.ndof);
+    w->dots = walloc<double>(g, 8);
+    w->fmax = walloc<unsigned>(g, 1);
+    TOPO_CUDA(cudaMallocHost(&w->hdots, 8 * sizeof(double)));
+    TOPO_CUDA(cudaEventCreate(&w->e0));
+    TOPO_CUDA(cudaEventCreate(&w->e1));
+    return w;
+}
+
+void features(to_grid* g, WarmWS* w, const double* xPhys, float* x, cudaStream_t st) {
+    const Dims& d = g->d;
+    TOPO_CUDA(cudaMemsetAsync(w->fmax, 0, sizeof(unsigned), st));
+    kw_absmax<<<div_up(d.ndof, 256), 256, 0, st>>>(d.ndof, g->F, w->fmax);
+    TOPO_CHECK_LAUNCH();
+    const long long V = (long long)w->D * w->H * w->W;
+    kw_features<<<div_up(V, 256), 256, 0, st>>>(d, w->D, w->H, w->W, xPhys, g->F, g->fixed, w->fmax, x);
+    TOPO_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void warm_free(to_grid* g) {
+    WarmWS* w = (WarmWS*)g->warm;
+    if (!w) return;
+    if (w->hdots) cudaFreeHost(w->hdots);
+    if (w->e0) cudaEventDestroy(w->e0);
+    if (w->e1) cudaEventDestroy(w->e1);
+    delete w;
+    g->warm = nullptr;
+}
+
+// U <- argmin of the energy over span{U, U_h}; E(xPhys) in g->E (FP64).
+void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy) {
+    WarmWS* w = warm_ws(g);
+    const Dims& d = g->d;
+    cudaStream_t st = g->st;
+    TOPO_CUDA(cudaEventRecord(w->e0, st));
+    features(g, w, xPhys, w->x, st);
+    net_forward_on(g->net, w->x, 1, w->D, w->H, w->W, w->y, st);
+    kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->D, w->H, w->W, w->y, g->fixed, w->Uh);
+    TOPO_CHECK_LAUNCH();
+    launch_mask_copy(d.ndof, U, w->Up, g->fixed, st);
+    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr, st);
+    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Up, w->KUp, g->fixed, true, nullptr, nullptr, nullptr, st);
+    launch_dot(d.ndof, g->F, w->Up, w->dots + 0, g->partials, g->counter, st);
+    launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, g->partials, g->counter, st);
+    launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, g->partials, g->counter, st);
+    launch_dot(d.ndof, w->Up, w->KUh, w->dots + 3, g->partials, g->counter, st);
+    launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 4, g->partials, g->counter, st);
+    TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+    const double fp = w->hdots[0], fh = w->hdots[1], pp = w->hdots[2], ph = w->hdots[3], hh = w->hdots[4];
+    double a = 1.0, b = 0.0;  // keep U when the network direction adds nothing
+    const bool hok = hh > 0.0 && std::isfinite(hh) && std::isfinite(fh);
+    if (hok && !(pp > 0.0)) {  // no previous solution: the energy-optimal multiple of U_h
+        a = 0.0;
+        b = fh / hh;
+    } else if (hok && std::isfinite(pp) && std::isfinite(ph) && std::isfinite(fp)) {
+        const double det = pp * hh - ph * ph;
+        if (det > 1e-12 * pp * hh) {
+            a = (fp * hh - fh * ph) / det;
+            b = (pp * fh - ph * fp) / det;
+        }
+    }
+    if (!(a == 1.0 && b == 0.0)) {
+        kw_combine<<<div_up(d.ndof, 256), 256, 0, st>>>(d.ndof, a, w->Up, b, w->Uh, U);
+        TOPO_CHECK_LAUNCH();
+    }
+    TOPO_CUDA(cudaEventRecord(w->e1, st));
+    TOPO_CUDA(cudaEventSynchronize(w->e1));
+    float t = 0.f;
+    TOPO_CUDA(cudaEventElapsedTime(&t, w->e0, w->e1));
+    if (coef) {
+        coef[0] = a;
+        coef[1] = b;
+    }
+    if (ms) *ms = t;
+    if (energy) {  // potential energy 1/2 U^T K U - F^T U of U_prev and of the new start
+        energy[0] = 0.5 * pp - fp;
+        energy[1] = 0.5 * (a * a * pp + 2.0 * a * b * ph + b * b * hh) - (a * fp + b * fh);
+    }
+}
+
+}  // namespace topo
+
+using namespace topo;
+
+extern "C" {
+
+to_status to_set_warm_start(to_grid* g, to_net* net) {
+    if (!g) return api_fail(TO_EINVAL, "NULL handle");
+    if (net && g->d.dim != 3) return api_fail(TO_EINVAL, "the learned warm start works on 3D grids");
+    g->net = net;
+    return TO_OK;
+}
+
+to_status to_learned_features(to_grid* g, const double* xPhys, float* x, int32_t* dims) {
+    if (!g) return api_fail(TO_EINVAL, "NULL handle");
+    try {
+        WarmWS* w = warm_ws(g);
+        if (dims) {
+            dims[0] = w->D;
+            dims[1] = w->H;
+            dims[2] = w->W;
+        }
+        if (!x) return TO_OK;
+        if (!xPhys) return api_fail(TO_EINVAL, "NULL xPhys");
+        grid_sync_in(g);
+        features(g, w, xPhys, x, g->st);
+        grid_sync_out(g);
+    } catch (const topo::Error& e) {
+        return api_fail(e.code, e.what());
+    }
+    return TO_OK;
+}
+
+to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask) {
+    if (!g || !U || !t || !mask) return api_fail(TO_EINVAL, "NULL argument");
+    try {
+        WarmWS* w = warm_ws(g);
+        grid_sync_in(g);
+        const Dims& d = g->d;
+        launch_dot(d.ndof, U, nullptr, w->dots + 5, g->partials, g->counter, g->st);
+        const long long V = (long long)w->D * w->H * w->W;
+        kw_target<<<div_up(V, 256), 256, 0, g->st>>>(d, w->D, w->H, w->W, U, w->dots + 5, t, mask);
+        TOPO_CHECK_LAUNCH();
+        grid_sync_out(g);
+    } catch (const topo::Error& e) {
+        return api_fail(e.code, e.what());
+    }
+    return TO_OK;
+}
+
+}  // extern "C"

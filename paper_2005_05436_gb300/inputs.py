@@ -75,6 +75,45 @@ def cantilever_3d(nelx, nely, nelz):
     return F, fixed
 
 
+def cantilever_family(nelx, nely, nelz, seed):
+    """Seeded member of the 3D cantilever family used to generate training data
+    for the learned warm start: the x = 0 face clamped, and on the x = nelx face
+    either a line load (along y or z, sine or uniform profile, random unit
+    direction) or 1-3 unit point loads of random direction, plus a volume
+    fraction ~ U[0.1, 0.3]. Returns (F, fixed, volfrac)."""
+    rng = np.random.default_rng(seed)
+    _, _, _, ndof = counts(nelx, nely, nelz)
+    F = np.zeros(ndof)
+    fixed = np.zeros(ndof, np.uint8)
+    for iz in range(nelz + 1):
+        for iy in range(nely + 1):
+            n = node_id(iy, 0, iz, nely=nely, nelz=nelz)
+            fixed[3 * n:3 * n + 3] = 1
+
+    def unit():
+        v = rng.standard_normal(3)
+        return v / np.linalg.norm(v)
+
+    if rng.random() < 0.5:
+        d = unit()
+        sine = rng.random() < 0.5
+        if rng.random() < 0.5:  # along y at a random z
+            iz = int(rng.integers(0, nelz + 1))
+            for iy in range(nely + 1):
+                w = math.sin(math.pi * iy / nely) if sine else 1.0 / (nely + 1)
+                F[3 * node_id(iy, nelx, iz, nely=nely, nelz=nelz):][:3] += w * d
+        else:  # along z at a random y
+            iy = int(rng.integers(0, nely + 1))
+            for iz in range(nelz + 1):
+                w = math.sin(math.pi * iz / nelz) if sine else 1.0 / (nelz + 1)
+                F[3 * node_id(iy, nelx, iz, nely=nely, nelz=nelz):][:3] += w * d
+    else:
+        for _ in range(int(rng.integers(1, 4))):
+            iy, iz = int(rng.integers(0, nely + 1)), int(rng.integers(0, nelz + 1))
+            F[3 * node_id(iy, nelx, iz, nely=nely, nelz=nelz):][:3] += unit()
+    return F, fixed, float(rng.uniform(0.1, 0.3))
+
+
 def frame_reinforcement(nelx, nely):
     """Frame-reinforcement example of Sec. 3.5 (passive frame and opening).
 

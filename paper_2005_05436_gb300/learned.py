@@ -7,6 +7,7 @@ steps on CUDA float32 tensors laid out [N][D][H][W][C].
 from __future__ import annotations
 
 import ctypes as C
+import math
 
 import numpy as np
 import torch
@@ -96,3 +97,91 @@ class Net:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
         L.check(self.lib.to_net_adam(self.h, float(lr), float(beta1), float(beta2), float(eps), float(grad_scale)))
+
+
+# ------------------------------------------------------------- grid interface
+
+def features(grid, xPhys, out=None):
+    """Network input of a 3D Grid at xPhys (library kernel): [1, D, H, W, 4]."""
+    dims = (C.c_int32 * 3)()
+    L.check(grid.lib.to_learned_features(grid.h, None, None, dims))
+    D, H, W = dims
+    if out is None:
+        out = torch.empty((1, D, H, W, 4), dtype=torch.float32, device="cuda")
+    L.check(grid.lib.to_learned_features(grid.h, C.c_void_p(xPhys.data_ptr()), _fp(out, "x", D * H * W * 4),
+                                         dims))
+    return out
+
+
+def target(grid, U):
+    """Training target U / rms(U) on the padded node grid and its node mask."""
+    dims = (C.c_int32 * 3)()
+    L.check(grid.lib.to_learned_features(grid.h, None, None, dims))
+    D, H, W = dims
+    t = torch.empty((1, D, H, W, 3), dtype=torch.float32, device="cuda")
+    m = torch.empty((1, D, H, W), dtype=torch.uint8, device="cuda")
+    L.check(grid.lib.to_learned_target(grid.h, C.c_void_p(U.data_ptr()), _fp(t, "t"), _fp(m, "mask", None,
+                                                                                          torch.uint8)))
+    return t, m
+
+
+def attach(grid, net):
+    """Use net as the warm start of every to_step of grid (None detaches)."""
+    L.check(grid.lib.to_set_warm_start(grid.h, net.h if net is not None else None))
+
+
+def generate(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
+    """(features, target, mask) triples from runs of the method itself: for each
+    run a cantilever-family problem (inputs.cantilever_family) on one of the
+    given grid shapes is advanced by to_step (mixed precision + multigrid) and
+    every `every`-th design after `warmup` iterations is recorded. Returns a
+    dict shape -> list of (x, t, m) CUDA tensors."""
+    from . import TO_MIXED, TO_PC_GMG, default_params, inputs as I
+    from .topopt import Design, Grid
+    out = {}
+    for r in range(runs):
+        nelx, nely, nelz = shapes[r % len(shapes)]
+        F, fixed, vf = I.cantilever_family(nelx, nely, nelz, seed + r)
+        kw = dict(precision=TO_MIXED, precond=TO_PC_GMG, volfrac=vf, rmin=math.sqrt(3.0), beta=2.0,
+                  beta_cnt=(1, 16.0, 10, 2.0, 1), cg_rtol=1e-8, cg_maxit=5000)
+        kw.update(params)
+        p = default_params(3, nelx, nely, nelz, **kw)
+        g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+        d = Design(g, torch.full((g.nel,), vf, dtype=torch.float64, device="cuda"))
+        for k in range(iters):
+            d.step()
+            if k >= warmup and (k - warmup) % every == 0:
+                x = features(g, d.xPhys)
+                t, m = target(g, d.U)
+                out.setdefault((nelx, nely, nelz), []).append((x, t, m))
+        g.close()
+    return out
+
+
+def train(net, data, epochs, lr=2e-3, batch=4, seed=0, log=None, lr_final=None):
+    """Adam on the masked MSE over mini-batches of equal-shape samples; the
+    learning rate decays geometrically from lr to lr_final (default lr)."""
+    rng = np.random.default_rng(seed)
+    groups = []
+    for shape, items in data.items():
+        for i in range(0, len(items), batch):
+            groups.append(items[i:i + batch])
+    hist = []
+    lr_final = lr if lr_final is None else lr_final
+    for ep in range(epochs):
+        lr_ep = lr * (lr_final / lr) ** (ep / max(1, epochs - 1))
+        tot, cnt = 0.0, 0
+        for gi in rng.permutation(len(groups)):
+            grp = groups[gi]
+            x = torch.cat([a for a, _, _ in grp])
+            t = torch.cat([b for _, b, _ in grp])
+            m = torch.cat([c for _, _, c in grp])
+            net.zero_grad()
+            loss = net.accumulate(x, t, m)
+            net.adam(lr_ep)
+            tot += loss * len(grp)
+            cnt += len(grp)
+        hist.append(tot / max(cnt, 1))
+        if log:
+            log(ep, hist[-1])
+    return hist
