@@ -420,6 +420,9 @@ to_status to_net_forward(to_net* net, const float* x, int32_t N, int32_t D, int3
  * out, may be NULL) receives L. */
 to_status to_net_accumulate(to_net* net, const float* x, const float* target, const uint8_t* mask, int32_t N,
                             int32_t D, int32_t H, int32_t W, double* loss);
+/* Adds the gradient for an output gradient gy[N][D][H][W][3] (dL/dy), using
+ * the activations of the last to_net_forward, which must have had this shape. */
+to_status to_net_backward(to_net* net, const float* gy, int32_t N, int32_t D, int32_t H, int32_t W);
 to_status to_net_get_grad(const to_net* net, float* grad);
 to_status to_net_zero_grad(to_net* net);
 /* One Adam step (bias-corrected) with gradient grad_scale * internal gradient;
@@ -443,6 +446,13 @@ to_status to_learned_features(to_grid* g, const double* xPhys, float* x, int32_t
 /* Training target for displacements U: t[D][H][W][3] = U / rms(U) on the
  * nodes, 0 in the padding; mask[D][H][W] = 1 on nodes. */
 to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask);
+/* Energy objective of one network output y[D][H][W][3] (the grid's padded node
+ * layout) for the design xPhys whose converged compliance is c_star:
+ * L = 1 - (F^T U_h)^2 / (U_h^T K U_h c_star), the relative energy-norm error
+ * of the best multiple of U_h (U_h = y on the free DOFs; K at the grid's
+ * current penal). loss (host out) = L, gy = dL/dy (FP32, same layout). */
+to_status to_learned_energy_grad(to_grid* g, const double* xPhys, const float* y, double c_star, float* gy,
+                                 double* loss);
 
 /* Struct sizes, for bindings that mirror these layouts. */
 size_t to_sizeof_net_cfg(void);

@@ -138,6 +138,8 @@ _SIGS = {
     "to_set_warm_start": (C.c_int, [P, P]),
     "to_learned_features": (C.c_int, [P, P, P, P]),
     "to_learned_target": (C.c_int, [P, P, P, P]),
+    "to_learned_energy_grad": (C.c_int, [P, P, P, C.c_double, P, C.POINTER(C.c_double)]),
+    "to_net_backward": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "to_sizeof_tile_info": (C.c_size_t, []),
     "to_sizeof_batch_info": (C.c_size_t, []),
 }

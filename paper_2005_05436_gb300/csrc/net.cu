@@ -755,6 +755,23 @@ to_status to_net_accumulate(to_net* n, const float* x, const float* target, cons
     TOPO_NET_END
 }
 
+to_status to_net_backward(to_net* n, const float* gy, int32_t N, int32_t D, int32_t H, int32_t W) {
+    if (!n || !gy) return api_fail(TO_EINVAL, "NULL argument");
+    TOPO_NET_BEGIN
+    check_shape(n, N, D, H, W);
+    TOPO_REQUIRE(n->shp.N == N && n->shp.D == D && n->shp.H == H && n->shp.W == W,
+                 "to_net_backward: the last forward pass had another shape");
+    const Shape s{N, D, H, W};
+    sync_in(n);
+    TOPO_CUDA(cudaMemcpyAsync(n->gy, gy, s.vox() * 3 * sizeof(float), cudaMemcpyDeviceToDevice, n->st));
+    if (n->cfg.bf16)
+        backward<bf16>(n, s);
+    else
+        backward<float>(n, s);
+    sync_out(n);
+    TOPO_NET_END
+}
+
 to_status to_net_get_grad(const to_net* n, float* g) {
     if (!n || !g) return api_fail(TO_EINVAL, "NULL argument");
     TOPO_NET_BEGIN

@@ -83,6 +83,22 @@ __global__ void kw_crop(Dims d, int D, int H, int W, const float* __restrict__ y
     for (int c = 0; c < 3; ++c) Uh[3 * n + c] = fixed[3 * n + c] ? 0.0 : (double)y[v * 3 + c];
 }
 
+// Output gradient of the energy objective on the padded grid: g = ga F + gb K U_h
+// at free DOFs of nodes, 0 elsewhere.
+__global__ void kw_energy_grad(Dims d, int D, int H, int W, const double* __restrict__ F,
+                               const double* __restrict__ KUh, const uint8_t* __restrict__ fixed, double ga,
+                               double gb, float* __restrict__ gy) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (long long)D * H * W) return;
+    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
+    const bool in = ix < d.nnx && iz < d.nnz && iy < d.nny;
+    const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
+    for (int c = 0; c < 3; ++c) {
+        const long long i = 3 * n + c;
+        gy[v * 3 + c] = (in && !fixed[i]) ? (float)(ga * F[i] + gb * KUh[i]) : 0.f;
+    }
+}
+
 __global__ void kw_combine(long long n, double a, const double* __restrict__ Up, double b,
                            const double* __restrict__ Uh, double* __restrict__ U) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -235,6 +251,41 @@ to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask
         kw_target<<<div_up(V, 256), 256, 0, g->st>>>(d, w->D, w->H, w->W, U, w->dots + 5, t, mask);
         TOPO_CHECK_LAUNCH();
         grid_sync_out(g);
+    } catch (const topo::Error& e) {
+        return api_fail(e.code, e.what());
+    }
+    return TO_OK;
+}
+
+to_status to_learned_energy_grad(to_grid* g, const double* xPhys, const float* y, double c_star, float* gy,
+                                 double* loss) {
+    if (!g || !xPhys || !y || !gy || !(c_star > 0.0)) return api_fail(TO_EINVAL, "NULL argument or c <= 0");
+    try {
+        WarmWS* w = warm_ws(g);
+        grid_sync_in(g);
+        const Dims& d = g->d;
+        cudaStream_t st = g->st;
+        launch_modulus<double>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, g->E, st);
+        kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->D, w->H, w->W, y, g->fixed, w->Uh);
+        TOPO_CHECK_LAUNCH();
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr, st);
+        launch_dot(d.ndof, g->F, w->Uh, w->dots + 6, g->partials, g->counter, st);
+        launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 7, g->partials, g->counter, st);
+        TOPO_CUDA(cudaMemcpyAsync(w->hdots + 6, w->dots + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TOPO_CUDA(cudaStreamSynchronize(st));
+        const double fh = w->hdots[6], hh = w->hdots[7];
+        double ga = 0.0, gb = 0.0, L = 1.0;
+        if (hh > 0.0 && std::isfinite(hh) && std::isfinite(fh)) {
+            // L = 1 - fh^2 / (hh c): the relative energy error of the best multiple of U_h
+            L = 1.0 - fh * fh / (hh * c_star);
+            ga = -2.0 * fh / (hh * c_star);
+            gb = 2.0 * fh * fh / (hh * hh * c_star);
+        }
+        const long long V = (long long)w->D * w->H * w->W;
+        kw_energy_grad<<<div_up(V, 256), 256, 0, st>>>(d, w->D, w->H, w->W, g->F, w->KUh, g->fixed, ga, gb, gy);
+        TOPO_CHECK_LAUNCH();
+        grid_sync_out(g);
+        if (loss) *loss = L;
     } catch (const topo::Error& e) {
         return api_fail(e.code, e.what());
     }

@@ -185,3 +185,68 @@ def train(net, data, epochs, lr=2e-3, batch=4, seed=0, log=None, lr_final=None):
         if log:
             log(ep, hist[-1])
     return hist
+
+
+def generate_energy(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
+    """Samples for the energy objective: for each run a cantilever-family
+    problem is advanced by to_step; recorded are the network input, the design
+    xPhys and its converged compliance, with the run's Grid (which holds F and
+    the supports) kept open for the training-time operator products."""
+    from . import TO_MIXED, TO_PC_GMG, default_params, inputs as I
+    from .topopt import Design, Grid
+    samples, grids = [], []
+    for r in range(runs):
+        nelx, nely, nelz = shapes[r % len(shapes)]
+        F, fixed, vf = I.cantilever_family(nelx, nely, nelz, seed + r)
+        kw = dict(precision=TO_MIXED, precond=TO_PC_GMG, volfrac=vf, rmin=math.sqrt(3.0), beta=2.0,
+                  beta_cnt=(1, 16.0, 10, 2.0, 1), cg_rtol=1e-8, cg_maxit=5000)
+        kw.update(params)
+        p = default_params(3, nelx, nely, nelz, **kw)
+        g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+        d = Design(g, torch.full((g.nel,), vf, dtype=torch.float64, device="cuda"))
+        for k in range(iters):
+            info = d.step()
+            if k >= warmup and (k - warmup) % every == 0:
+                samples.append((len(grids), features(g, d.xPhys), d.xPhys.clone(), float(info["c"]),
+                                float(d.st.penal)))
+        grids.append(g)
+    return samples, grids
+
+
+def train_energy(net, samples, grids, epochs, lr=1e-3, lr_final=None, batch=4, seed=0, log=None):
+    """Adam on the mean relative energy error of the network direction
+    (to_learned_energy_grad) over mini-batches of samples of one grid shape."""
+    rng = np.random.default_rng(seed)
+    by_shape = {}
+    for i, s in enumerate(samples):
+        by_shape.setdefault(tuple(s[1].shape), []).append(i)
+    groups = []
+    for idx in by_shape.values():
+        for k in range(0, len(idx), batch):
+            groups.append(idx[k:k + batch])
+    lr_final = lr if lr_final is None else lr_final
+    hist = []
+    for ep in range(epochs):
+        lr_ep = lr * (lr_final / lr) ** (ep / max(1, epochs - 1))
+        tot = 0.0
+        for gi in rng.permutation(len(groups)):
+            grp = groups[gi]
+            x = torch.cat([samples[i][1] for i in grp])
+            N, D, H, W, _ = x.shape
+            y = net.forward(x)
+            gy = torch.empty_like(y)
+            net.zero_grad()
+            for b, i in enumerate(grp):
+                gi_, _, xphys, c, penal = samples[i]
+                g = grids[gi_]
+                g.set_scalars(penal, g.params.beta, g.params.eta)
+                loss = C.c_double()
+                L.check(g.lib.to_learned_energy_grad(g.h, C.c_void_p(xphys.data_ptr()), C.c_void_p(y[b].data_ptr()),
+                                                     float(c), C.c_void_p(gy[b].data_ptr()), C.byref(loss)))
+                tot += loss.value
+            L.check(net.lib.to_net_backward(net.h, _fp(gy, "gy"), N, D, H, W))
+            net.adam(lr_ep, grad_scale=1.0 / len(grp))
+        hist.append(tot / len(samples))
+        if log:
+            log(ep, hist[-1])
+    return hist

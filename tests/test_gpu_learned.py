@@ -27,14 +27,28 @@ def _lib():
 
 @pytest.fixture(scope="module")
 def nets():
+    """A network trained on the energy objective (to_learned_energy_grad) with
+    samples from 12 runs of the method, and the same network untrained."""
     from paper_2005_05436_gb300 import learned as Lr
-    data = Lr.generate(SHAPES, runs=12, iters=12, seed=0, warmup=2)
+    samples, grids = Lr.generate_energy(SHAPES, runs=12, iters=12, seed=0, warmup=2)
     trained = Lr.Net(base=16, bf16=True)
     trained.set_params(Lr.he_init(16, seed=1))
-    hist = Lr.train(trained, data, epochs=30, lr=3e-3, lr_final=2e-4, batch=4)
+    hist = Lr.train_energy(trained, samples, grids, epochs=30, lr=2e-3, lr_final=1e-4, batch=4)
+    for g in grids:
+        g.close()
     raw = Lr.Net(base=16, bf16=True)
     raw.set_params(Lr.he_init(16, seed=1))
     return trained, raw, hist
+
+
+def test_mse_training_on_the_normalised_displacement():
+    """The alternative objective: mean squared error to U / rms(U)."""
+    from paper_2005_05436_gb300 import learned as Lr
+    data = Lr.generate(SHAPES, runs=4, iters=8, seed=0, warmup=2)
+    net = Lr.Net(base=8, bf16=True)
+    net.set_params(Lr.he_init(8, seed=2))
+    hist = Lr.train(net, data, epochs=20, lr=3e-3, lr_final=2e-4, batch=4)
+    assert hist[-1] < 0.9 * hist[0], hist
 
 
 def _problem(r, precision):
@@ -78,9 +92,9 @@ def _steps(g, d, modes, nets):
     return out
 
 
-def test_training_lowers_the_loss(nets):
+def test_training_lowers_the_energy_error(nets):
     _, _, hist = nets
-    assert hist[-1] < 0.75 * hist[0], hist
+    assert hist[-1] < 0.95 * hist[0], hist
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
