@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--mg-nu", type=int, default=1, help="GMG smoothing sweeps per level")
     ap.add_argument("--inner-rtol", type=float, default=1e-3, help="mixed path: inner FP32 solve tolerance")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="headline without the learned warm start (mixed precision + GMG only)")
+    ap.add_argument("--learn-epochs", type=int, default=30)
     ap.add_argument("--loop-mode", type=int, default=0, choices=[0, 1],
                     help="0: PCG loop as one conditional-WHILE graph launch; 1: host-driven loop "
                          "of the same kernels (lets profilers see every launch)")
@@ -153,6 +156,31 @@ def _make_design(args, w, precision, precond, ku_impl, stream):
     return g, d
 
 
+def _train_warm_start(args):
+    """The learned warm start: samples from runs of the method itself on small
+    cantilever-family grids, energy objective, BF16 network with 16 base channels."""
+    import torch
+
+    from paper_2005_05436_gb300 import learned as Lr
+    t0 = time.perf_counter()
+    shapes = [(16, 8, 8), (24, 12, 12), (32, 16, 16)]
+    samples, grids = Lr.generate_energy(shapes, runs=18, iters=12, seed=0, warmup=2)
+    net = Lr.Net(base=16, bf16=True)
+    net.set_params(Lr.he_init(16, seed=1))
+    hist = Lr.train_energy(net, samples, grids, epochs=args.learn_epochs, lr=2e-3, lr_final=1e-4, batch=4)
+    for g in grids:
+        g.close()
+    torch.cuda.synchronize()
+    info = {"network": "3-level 3D conv encoder-decoder, 16 base channels, BF16 activations/weights, "
+                       "FP32 accumulation", "params": net.n_params,
+            "training": f"{len(samples)} (xPhys, F, U) samples from 18 runs of the method on "
+                        f"16x8x8 / 24x12x12 / 32x16x16 cantilever-family problems, energy objective, "
+                        f"{args.learn_epochs} epochs",
+            "energy_loss_first_last": [round(hist[0], 4), round(hist[-1], 4)],
+            "train_seconds": round(time.perf_counter() - t0, 1)}
+    return net, info
+
+
 def _timed_steps(d, steps, flush, stream):
     """Design steps timed one by one with CUDA events on the stream; L2 flushed before each."""
     import torch
@@ -192,7 +220,13 @@ def run_ours(args):
     ku_impl = {"auto": 0, "cuda": 1, "tc": 2}[args.ku_impl]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    net, learned_info = None, None
+    if not args.no_learned and precision == TO_MIXED:
+        from paper_2005_05436_gb300 import learned as Lr
+        net, learned_info = _train_warm_start(args)
     g, d = _make_design(args, w, precision, precond, ku_impl, stream)
+    if net is not None:
+        Lr.attach(g, net)
     for _ in range(args.warmup):
         d.step()
     torch.cuda.synchronize()
@@ -278,8 +312,11 @@ def run_ours(args):
     # ---- the plain FP64 paths on the same design iterations (comparison, not timed above)
     compare = {}
     if not args.no_compare and precision != TO_FP64:
-        for name, pc in (("plain_fp64_gmg", TO_PC_GMG), ("plain_fp64_jacobi", TO_PC_JACOBI)):
-            g2, d2 = _make_design(args, w, TO_FP64, pc, 0, stream)
+        arms = [("plain_fp64_gmg", TO_FP64, TO_PC_GMG), ("plain_fp64_jacobi", TO_FP64, TO_PC_JACOBI)]
+        if net is not None:
+            arms.insert(0, ("mixed_gmg_without_learned", TO_MIXED, TO_PC_GMG))
+        for name, prec2, pc in arms:
+            g2, d2 = _make_design(args, w, prec2, pc, ku_impl if prec2 == TO_MIXED else 0, stream)
             for _ in range(args.warmup):
                 d2.step()
             infos2, ms2 = _timed_steps(d2, args.steps, flush, stream)
@@ -307,11 +344,14 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if precision == TO_FP64 else "f32 inner PCG + GMG, f64 residual/refinement/dots",
+        "dtype": "f64" if precision == TO_FP64 else (
+            "f32 inner PCG + GMG, f64 residual/refinement/dots"
+            + ("; learned warm start: bf16 network, f32 accumulation" if net is not None else "")),
         "data": "synthetic (paper's cantilever load and supports; no dataset)",
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
                    "mg_nu": args.mg_nu, "inner_rtol": args.inner_rtol,
+                   "learned_warm_start": learned_info,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches),
@@ -321,7 +361,9 @@ def run_ours(args):
                       "c": t["c"], "rel_res": t["rel_res"], "t_solve_ms": round(t["t_solve_ms"], 2),
                       "t_setup_ms": round(t["t_setup_ms"], 2), "t_krylov_ms": round(t["t_krylov_ms"], 2),
                       "t_resid_ms": round(t["t_resid_ms"], 2),
-                      "t_other_ms": round(t["t_filter_ms"] + t["t_sens_ms"] + t["t_oc_ms"], 2)}
+                      "t_other_ms": round(t["t_filter_ms"] + t["t_sens_ms"] + t["t_oc_ms"], 2),
+                      "t_warm_ms": round(t["t_warm_ms"], 2), "warm_err": round(t["warm_err"], 4),
+                      "warm_err_prev": round(t["warm_err_prev"], 4)}
                      for t, m in zip(timed, step_ms)],
         "final": {"c": last["c"], "V": last["V"], "eta": last["eta"]},
         "paper_context": "top3D125 + MGCG, 96x48x48 rmin 2sqrt(3): 14.20 s/it (0.0704 it/s), "

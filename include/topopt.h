@@ -434,17 +434,20 @@ void to_net_destroy(to_net* net);
  * every to_step then starts its state solve from the minimiser of the
  * potential energy 1/2 U^T K U - F^T U over span{U, U_net}, U the previous
  * solution and U_net the network's output on the step's xPhys (a 2 x 2
- * Rayleigh-Ritz step with FP64 operator products; U is kept when the network
- * adds nothing). The solve still runs to cg_rtol. */
-to_status to_set_warm_start(to_grid* g, to_net* net);
-/* Network input of the grid at xPhys: x[D][H][W][4] on the node grid padded
- * to multiples of 4 (D = nnx, H = nnz, W = nny rounded up): the mean density
- * of the elements around each node (-1 at nodes with a Dirichlet DOF) and
- * F / max|F|; zero in the padding.
+ * Rayleigh-Ritz step with operator products in the handle's precision; U is
+ * kept when the network adds nothing). The solve still runs to cg_rtol.
+ * stride (1 or 2): the network works on the node grid coarsened by stride
+ * (coarse node I on fine node stride*I; loads restricted by full weighting,
+ * the output prolongated trilinearly); fixed at the first use of the grid. */
+to_status to_set_warm_start(to_grid* g, to_net* net, int32_t stride);
+/* Network input of the grid at xPhys: x[D][H][W][4] on the (coarsened) node
+ * grid padded to multiples of 4 (D, H, W along x, z, y): the mean density of
+ * the elements around each node (-1 at nodes with a Dirichlet DOF) and the
+ * restricted load / max|F|; zero in the padding.
  * dims (host out [3], may be NULL) = D, H, W; x = NULL only queries dims. */
 to_status to_learned_features(to_grid* g, const double* xPhys, float* x, int32_t* dims);
-/* Training target for displacements U: t[D][H][W][3] = U / rms(U) on the
- * nodes, 0 in the padding; mask[D][H][W] = 1 on nodes. */
+/* Training target for displacements U: t[D][H][W][3] = U / rms(U) at the
+ * (coarse) nodes, 0 in the padding; mask[D][H][W] = 1 on nodes. */
 to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask);
 /* Energy objective of one network output y[D][H][W][3] (the grid's padded node
  * layout) for the design xPhys whose converged compliance is c_star:

@@ -135,7 +135,7 @@ _SIGS = {
     "to_net_zero_grad": (C.c_int, [P]),
     "to_net_adam": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
     "to_net_destroy": (None, [P]),
-    "to_set_warm_start": (C.c_int, [P, P]),
+    "to_set_warm_start": (C.c_int, [P, P, C.c_int32]),
     "to_learned_features": (C.c_int, [P, P, P, P]),
     "to_learned_target": (C.c_int, [P, P, P, P]),
     "to_learned_energy_grad": (C.c_int, [P, P, P, C.c_double, P, C.POINTER(C.c_double)]),

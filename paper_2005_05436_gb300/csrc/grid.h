@@ -80,6 +80,7 @@ struct to_grid {
     topo::Solver* solver = nullptr;
     to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned
     void* warm = nullptr;      // its workspace (warm.cu)
+    int warm_stride = 1;       // the network's node-grid coarsening (1 or 2)
 };
 
 namespace topo {

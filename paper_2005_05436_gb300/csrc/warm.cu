@@ -15,8 +15,18 @@ void net_forward_on(to_net* n, const float* x, int N, int D, int H, int W, float
 
 namespace {
 
+// The network works on the node grid coarsened by S (1 or 2): coarse node
+// (I, J, K) sits on fine node (S I, S J, S K) (the last coarse node of an odd
+// axis lies one node past the grid). Load-like fields are restricted by full
+// weighting (the transpose of the trilinear prolongation, which conserves the
+// total load); the network output is prolongated trilinearly to the fine nodes.
+struct CGrid {
+    int S, Nx, Ny, Nz, D, H, W;  // coarse node counts and the padded tensor dims
+};
+
 struct WarmWS {
     int D = 0, H = 0, W = 0;
+    CGrid cg{};
     float *x = nullptr, *y = nullptr;
     double *Uh = nullptr, *KUh = nullptr, *Up = nullptr, *KUp = nullptr, *dots = nullptr, *hdots = nullptr;
     unsigned* fmax = nullptr;
@@ -30,18 +40,42 @@ __global__ void kw_absmax(long long n, const double* __restrict__ F, unsigned* o
     if (i < n) atomicMax(out, __float_as_uint((float)fabs(F[i])));  // non-negative floats order as integers
 }
 
-// Network input on the padded node grid [D = nnx][H = nnz][W = nny] (the node
-// numbering's order): the mean physical density of the elements around the node
-// (-1 at nodes with a Dirichlet DOF, so that supports are visible to the
-// network) and the load scaled by 1 / max |F|; zero in the padding.
-__global__ void kw_features(Dims d, int D, int H, int W, const double* __restrict__ xPhys,
-                            const double* __restrict__ F, const uint8_t* __restrict__ fixed,
-                            const unsigned* __restrict__ fmax, float* __restrict__ x) {
+__host__ __device__ inline int coarse_n(int nn, int S) { return S == 1 ? nn : (nn - 1 + 1) / 2 + 1; }
+
+// sum_{o} w(o) f(S I + o) along three axes (w = 1 at o = 0, 1/2 at o = +-1 for S = 2).
+template <typename Fn>
+__device__ __forceinline__ void restrict3(const Dims& d, const CGrid& c, int I, int J, int K, Fn&& add) {
+    const int r = c.S == 2 ? 1 : 0;
+    for (int ox = -r; ox <= r; ++ox)
+        for (int oz = -r; oz <= r; ++oz)
+            for (int oy = -r; oy <= r; ++oy) {
+                const int ix = c.S * I + ox, iz = c.S * K + oz, iy = c.S * J + oy;
+                if (ix < 0 || ix >= d.nnx || iz < 0 || iz >= d.nnz || iy < 0 || iy >= d.nny) continue;
+                const double w = (ox ? 0.5 : 1.0) * (oz ? 0.5 : 1.0) * (oy ? 0.5 : 1.0);
+                add(iy + (long long)d.nny * (iz + (long long)d.nnz * ix), w);
+            }
+}
+
+__device__ __forceinline__ void decode_v(const CGrid& c, long long v, int& I, int& K, int& J) {
+    J = (int)(v % c.W);
+    K = (int)((v / c.W) % c.H);
+    I = (int)(v / ((long long)c.W * c.H));
+}
+
+// Network input on the padded coarse node grid [D][H][W] (x, z, y: the node
+// numbering's order): the mean physical density of the elements around the
+// node (-1 at nodes with a Dirichlet DOF, so that supports are visible to the
+// network) and the restricted load scaled by 1 / max |F|; zero in the padding.
+__global__ void kw_features(Dims d, CGrid c, const double* __restrict__ xPhys, const double* __restrict__ F,
+                            const uint8_t* __restrict__ fixed, const unsigned* __restrict__ fmax,
+                            float* __restrict__ x) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= (long long)D * H * W) return;
-    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
+    if (v >= (long long)c.D * c.H * c.W) return;
+    int I, K, J;
+    decode_v(c, v, I, K, J);
     float f[4] = {0.f, 0.f, 0.f, 0.f};
-    if (ix < d.nnx && iz < d.nnz && iy < d.nny) {
+    if (I < c.Nx && K < c.Nz && J < c.Ny) {
+        const int ix = min(c.S * I, d.nnx - 1), iz = min(c.S * K, d.nnz - 1), iy = min(c.S * J, d.nny - 1);
         double s = 0.0;
         int cnt = 0;
         for (int o = 0; o < 8; ++o) {
@@ -51,52 +85,79 @@ __global__ void kw_features(Dims d, int D, int H, int W, const double* __restric
             ++cnt;
         }
         const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
-        const float fm = __uint_as_float(*fmax);
-        const float sc = fm > 0.f ? 1.f / fm : 0.f;
         const bool sup = fixed[3 * n] || fixed[3 * n + 1] || fixed[3 * n + 2];
         f[0] = sup ? -1.f : (cnt ? (float)(s / cnt) : 0.f);
-        for (int c = 0; c < 3; ++c) f[1 + c] = (float)F[3 * n + c] * sc;
+        const float fm = __uint_as_float(*fmax);
+        const double sc = fm > 0.f ? 1.0 / fm : 0.0;
+        double a[3] = {0.0, 0.0, 0.0};
+        restrict3(d, c, I, J, K, [&](long long m, double w) {
+            for (int q = 0; q < 3; ++q) a[q] += w * F[3 * m + q];
+        });
+        for (int q = 0; q < 3; ++q) f[1 + q] = (float)(a[q] * sc);
     }
-    for (int c = 0; c < 4; ++c) x[v * 4 + c] = f[c];
+    for (int q = 0; q < 4; ++q) x[v * 4 + q] = f[q];
 }
 
-// Training target: U / rms(U) on the padded node grid and the node mask.
-__global__ void kw_target(Dims d, int D, int H, int W, const double* __restrict__ U, const double* __restrict__ sumsq,
+// Training target: U / rms(U) at the coarse nodes (fine node S I, clamped) and
+// the coarse node mask.
+__global__ void kw_target(Dims d, CGrid c, const double* __restrict__ U, const double* __restrict__ sumsq,
                           float* __restrict__ t, uint8_t* __restrict__ mask) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= (long long)D * H * W) return;
-    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
-    const bool in = ix < d.nnx && iz < d.nnz && iy < d.nny;
+    if (v >= (long long)c.D * c.H * c.W) return;
+    int I, K, J;
+    decode_v(c, v, I, K, J);
+    const bool in = I < c.Nx && K < c.Nz && J < c.Ny;
     const double ss = *sumsq;
     const double inv = ss > 0.0 ? 1.0 / sqrt(ss / (double)d.ndof) : 0.0;
+    const int ix = min(c.S * I, d.nnx - 1), iz = min(c.S * K, d.nnz - 1), iy = min(c.S * J, d.nny - 1);
     const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
-    for (int c = 0; c < 3; ++c) t[v * 3 + c] = in ? (float)(U[3 * n + c] * inv) : 0.f;
+    for (int q = 0; q < 3; ++q) t[v * 3 + q] = in ? (float)(U[3 * n + q] * inv) : 0.f;
     mask[v] = in ? 1 : 0;
 }
 
-__global__ void kw_crop(Dims d, int D, int H, int W, const float* __restrict__ y, const uint8_t* __restrict__ fixed,
+// U_h at the fine nodes: trilinear prolongation of the coarse output; 0 at
+// Dirichlet DOFs.
+__global__ void kw_crop(Dims d, CGrid c, const float* __restrict__ y, const uint8_t* __restrict__ fixed,
                         double* __restrict__ Uh) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.nnodes) return;
     const int iy = (int)(n % d.nny), iz = (int)((n / d.nny) % d.nnz), ix = (int)(n / ((long long)d.nny * d.nnz));
-    const long long v = ((long long)ix * H + iz) * W + iy;
-    for (int c = 0; c < 3; ++c) Uh[3 * n + c] = fixed[3 * n + c] ? 0.0 : (double)y[v * 3 + c];
+    double a[3] = {0.0, 0.0, 0.0};
+    const int I0 = ix / c.S, K0 = iz / c.S, J0 = iy / c.S;
+    const int nI = (c.S == 2 && (ix & 1)) ? 2 : 1, nK = (c.S == 2 && (iz & 1)) ? 2 : 1,
+              nJ = (c.S == 2 && (iy & 1)) ? 2 : 1;
+    const double w = 1.0 / (nI * nK * nJ);
+    for (int p = 0; p < nI; ++p)
+        for (int q = 0; q < nK; ++q)
+            for (int r = 0; r < nJ; ++r) {
+                const long long v = ((long long)(I0 + p) * c.H + (K0 + q)) * c.W + (J0 + r);
+                for (int k = 0; k < 3; ++k) a[k] += w * (double)y[v * 3 + k];
+            }
+    for (int k = 0; k < 3; ++k) Uh[3 * n + k] = fixed[3 * n + k] ? 0.0 : a[k];
 }
 
-// Output gradient of the energy objective on the padded grid: g = ga F + gb K U_h
-// at free DOFs of nodes, 0 elsewhere.
-__global__ void kw_energy_grad(Dims d, int D, int H, int W, const double* __restrict__ F,
-                               const double* __restrict__ KUh, const uint8_t* __restrict__ fixed, double ga,
-                               double gb, float* __restrict__ gy) {
+// Output gradient of the energy objective: g = ga F + gb K U_h on the free fine
+// DOFs, taken to the coarse grid by the transpose of the prolongation.
+__global__ void kw_energy_grad(Dims d, CGrid c, const double* __restrict__ F, const double* __restrict__ KUh,
+                               const uint8_t* __restrict__ fixed, double ga, double gb, float* __restrict__ gy) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= (long long)D * H * W) return;
-    const int iy = (int)(v % W), iz = (int)((v / W) % H), ix = (int)(v / ((long long)W * H));
-    const bool in = ix < d.nnx && iz < d.nnz && iy < d.nny;
-    const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
-    for (int c = 0; c < 3; ++c) {
-        const long long i = 3 * n + c;
-        gy[v * 3 + c] = (in && !fixed[i]) ? (float)(ga * F[i] + gb * KUh[i]) : 0.f;
+    if (v >= (long long)c.D * c.H * c.W) return;
+    int I, K, J;
+    decode_v(c, v, I, K, J);
+    double a[3] = {0.0, 0.0, 0.0};
+    if (I < c.Nx && K < c.Nz && J < c.Ny) {
+        restrict3(d, c, I, J, K, [&](long long m, double w) {
+            // the prolongation weight of fine node m from this coarse node is w / (its stencil size)
+            const int ix = (int)(m / ((long long)d.nny * d.nnz)), iz = (int)((m / d.nny) % d.nnz), iy = (int)(m % d.nny);
+            const int cnt = ((c.S == 2 && (ix & 1)) ? 2 : 1) * ((c.S == 2 && (iz & 1)) ? 2 : 1) *
+                            ((c.S == 2 && (iy & 1)) ? 2 : 1);
+            const double pw = 1.0 / cnt;
+            for (int q = 0; q < 3; ++q)
+                if (!fixed[3 * m + q]) a[q] += pw * (ga * F[3 * m + q] + gb * KUh[3 * m + q]);
+            (void)w;
+        });
     }
+    for (int q = 0; q < 3; ++q) gy[v * 3 + q] = (float)a[q];
 }
 
 __global__ void kw_combine(long long n, double a, const double* __restrict__ Up, double b,
@@ -114,13 +175,18 @@ T* walloc(to_grid* g, long long count) {
 }
 
 WarmWS* warm_ws(to_grid* g) {
-    if (g->warm) return (WarmWS*)g->warm;
+    if (g->warm && ((WarmWS*)g->warm)->cg.S == g->warm_stride) return (WarmWS*)g->warm;
+    TOPO_REQUIRE(!g->warm, "the warm-start coarsening cannot change after first use");
     TOPO_REQUIRE(g->d.dim == 3, "the learned warm start works on 3D grids");
     WarmWS* w = new WarmWS();
     g->warm = w;
-    w->D = pad4(g->d.nnx);
-    w->H = pad4(g->d.nnz);
-    w->W = pad4(g->d.nny);
+    w->cg.S = g->warm_stride;
+    w->cg.Nx = coarse_n(g->d.nnx, w->cg.S);
+    w->cg.Ny = coarse_n(g->d.nny, w->cg.S);
+    w->cg.Nz = coarse_n(g->d.nnz, w->cg.S);
+    w->D = w->cg.D = pad4(w->cg.Nx);
+    w->H = w->cg.H = pad4(w->cg.Nz);
+    w->W = w->cg.W = pad4(w->cg.Ny);
     const long long V = (long long)w->D * w->H * w->W;
     w->x = walloc<float>(g, V * 4);
     w->y = walloc<float>(g, V * 3);
@@ -139,7 +205,7 @@ void features(to_grid* g, WarmWS* w, const double* xPhys, float* x, cudaStream_t
     kw_absmax<<<div_up(d.ndof, 256), 256, 0, st>>>(d.ndof, g->F, w->fmax);
     TOPO_CHECK_LAUNCH();
     const long long V = (long long)w->D * w->H * w->W;
-    kw_features<<<div_up(V, 256), 256, 0, st>>>(d, w->D, w->H, w->W, xPhys, g->F, g->fixed, w->fmax, x);
+    kw_features<<<div_up(V, 256), 256, 0, st>>>(d, w->cg, xPhys, g->F, g->fixed, w->fmax, x);
     TOPO_CHECK_LAUNCH();
 }
 
@@ -163,11 +229,19 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     TOPO_CUDA(cudaEventRecord(w->e0, st));
     features(g, w, xPhys, w->x, st);
     net_forward_on(g->net, w->x, 1, w->D, w->H, w->W, w->y, st);
-    kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->D, w->H, w->W, w->y, g->fixed, w->Uh);
+    kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->cg, w->y, g->fixed, w->Uh);
     TOPO_CHECK_LAUNCH();
     launch_mask_copy(d.ndof, U, w->Up, g->fixed, st);
-    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr, st);
-    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Up, w->KUp, g->fixed, true, nullptr, nullptr, nullptr, st);
+    if (g->p.precision == TO_MIXED) {
+        // the products only choose a starting point: the FP32 operator is enough
+        apply_K_fp32(g, xPhys, w->Uh, w->KUh, 1);
+        apply_K_fp32(g, xPhys, w->Up, w->KUp, 1);
+    } else {
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr,
+                               st);
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Up, w->KUp, g->fixed, true, nullptr, nullptr, nullptr,
+                               st);
+    }
     launch_dot(d.ndof, g->F, w->Up, w->dots + 0, g->partials, g->counter, st);
     launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, g->partials, g->counter, st);
     launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, g->partials, g->counter, st);
@@ -213,10 +287,14 @@ using namespace topo;
 
 extern "C" {
 
-to_status to_set_warm_start(to_grid* g, to_net* net) {
+to_status to_set_warm_start(to_grid* g, to_net* net, int32_t stride) {
     if (!g) return api_fail(TO_EINVAL, "NULL handle");
     if (net && g->d.dim != 3) return api_fail(TO_EINVAL, "the learned warm start works on 3D grids");
+    if (stride != 1 && stride != 2) return api_fail(TO_EINVAL, "stride must be 1 or 2");
+    if (g->warm && ((WarmWS*)g->warm)->cg.S != stride)
+        return api_fail(TO_EINVAL, "the warm-start coarsening cannot change after first use");
     g->net = net;
+    g->warm_stride = stride;
     return TO_OK;
 }
 
@@ -248,7 +326,7 @@ to_status to_learned_target(to_grid* g, const double* U, float* t, uint8_t* mask
         const Dims& d = g->d;
         launch_dot(d.ndof, U, nullptr, w->dots + 5, g->partials, g->counter, g->st);
         const long long V = (long long)w->D * w->H * w->W;
-        kw_target<<<div_up(V, 256), 256, 0, g->st>>>(d, w->D, w->H, w->W, U, w->dots + 5, t, mask);
+        kw_target<<<div_up(V, 256), 256, 0, g->st>>>(d, w->cg, U, w->dots + 5, t, mask);
         TOPO_CHECK_LAUNCH();
         grid_sync_out(g);
     } catch (const topo::Error& e) {
@@ -266,7 +344,7 @@ to_status to_learned_energy_grad(to_grid* g, const double* xPhys, const float* y
         const Dims& d = g->d;
         cudaStream_t st = g->st;
         launch_modulus<double>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, g->E, st);
-        kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->D, w->H, w->W, y, g->fixed, w->Uh);
+        kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->cg, y, g->fixed, w->Uh);
         TOPO_CHECK_LAUNCH();
         launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr, st);
         launch_dot(d.ndof, g->F, w->Uh, w->dots + 6, g->partials, g->counter, st);
@@ -282,7 +360,7 @@ to_status to_learned_energy_grad(to_grid* g, const double* xPhys, const float* y
             gb = 2.0 * fh * fh / (hh * hh * c_star);
         }
         const long long V = (long long)w->D * w->H * w->W;
-        kw_energy_grad<<<div_up(V, 256), 256, 0, st>>>(d, w->D, w->H, w->W, g->F, w->KUh, g->fixed, ga, gb, gy);
+        kw_energy_grad<<<div_up(V, 256), 256, 0, st>>>(d, w->cg, g->F, w->KUh, g->fixed, ga, gb, gy);
         TOPO_CHECK_LAUNCH();
         grid_sync_out(g);
         if (loss) *loss = L;

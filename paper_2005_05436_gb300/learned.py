@@ -125,12 +125,13 @@ def target(grid, U):
     return t, m
 
 
-def attach(grid, net):
-    """Use net as the warm start of every to_step of grid (None detaches)."""
-    L.check(grid.lib.to_set_warm_start(grid.h, net.h if net is not None else None))
+def attach(grid, net, stride=2):
+    """Use net as the warm start of every to_step of grid (None detaches); the
+    network works on the node grid coarsened by stride."""
+    L.check(grid.lib.to_set_warm_start(grid.h, net.h if net is not None else None, int(stride)))
 
 
-def generate(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
+def generate(shapes, runs, iters, seed=0, every=1, warmup=2, stride=2, **params):
     """(features, target, mask) triples from runs of the method itself: for each
     run a cantilever-family problem (inputs.cantilever_family) on one of the
     given grid shapes is advanced by to_step (mixed precision + multigrid) and
@@ -147,6 +148,7 @@ def generate(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
         kw.update(params)
         p = default_params(3, nelx, nely, nelz, **kw)
         g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+        attach(g, None, stride)
         d = Design(g, torch.full((g.nel,), vf, dtype=torch.float64, device="cuda"))
         for k in range(iters):
             d.step()
@@ -187,7 +189,7 @@ def train(net, data, epochs, lr=2e-3, batch=4, seed=0, log=None, lr_final=None):
     return hist
 
 
-def generate_energy(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
+def generate_energy(shapes, runs, iters, seed=0, every=1, warmup=2, stride=2, **params):
     """Samples for the energy objective: for each run a cantilever-family
     problem is advanced by to_step; recorded are the network input, the design
     xPhys and its converged compliance, with the run's Grid (which holds F and
@@ -203,6 +205,7 @@ def generate_energy(shapes, runs, iters, seed=0, every=1, warmup=2, **params):
         kw.update(params)
         p = default_params(3, nelx, nely, nelz, **kw)
         g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+        attach(g, None, stride)
         d = Design(g, torch.full((g.nel,), vf, dtype=torch.float64, device="cuda"))
         for k in range(iters):
             info = d.step()
