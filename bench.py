@@ -39,6 +39,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # dense TF32 : BF16 tensor throughput (nominal 1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 CUDA-core
+# operator at 96x48x48 (ncu, cold cache), from
+# profiles/k_fine_op3_fp32_96x48x48_and_256x128x128.md; null for other kernels
+# and grids, and to be re-measured whenever that kernel changes
+TRAFFIC_FP32_96 = 4401152
 
 
 def parse_args():
@@ -238,8 +243,10 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = lib.to_kernel_launches()
+    torch.cuda.nvtx.range_push("timed")  # profilers can select the timed steps
     with ClockSampler(local) as clk:
         timed, step_ms = _timed_steps(d, args.steps, flush, stream)
+    torch.cuda.nvtx.range_pop()
     launches = lib.to_kernel_launches() - launches0
     total_ms = sum(step_ms)
     if world > 1:
@@ -275,9 +282,11 @@ def run_ours(args):
                     "hbm_equivalent": hbm_eq}
         else:
             achieved = flops / (us * 1e-6) / 1e12
+            traffic = TRAFFIC_FP32_96 if args.grid == "96x48x48" else None
             roof = {"kernel": "k_fine_op3<float> (CUDA cores), FP32 K u of the inner solve", "bound": "alu",
                     "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                    "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
+                    "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic, "traffic_unit": "bytes",
+                    "us_per_launch": round(us, 2),
                     "peak_source": "derived: FP32 FMA lanes 152 SM x 128 x 2 flop x 2.07 GHz",
                     "algorithmic_flops": "2 x 24 x 24 per element per launch", "hbm_equivalent": hbm_eq}
 

@@ -1,29 +1,31 @@
-"""Micro-benchmark of the matrix-free K u kernel through the C ABI.
+"""Micro-benchmarks through the C ABI (the targets of the ncu captures
+summarised under profiles/).
 
     python -m paper_2005_05436_gb300.kernel_bench --grid 256x128x128 --precision fp64 --reps 3
+    python -m paper_2005_05436_gb300.kernel_bench --what batch --count 256 --steps 3
+    python -m paper_2005_05436_gb300.kernel_bench --what net --shape 52x28x28 --reps 10
 
-Builds a cantilever grid with a seeded SIMP-like design and launches the
+ku: builds a cantilever grid with a seeded SIMP-like design and launches the
 operator kernel reps + 1 times (one warm-up) on the current stream; prints the
-average device time per launch and the achieved rate. Used as the target of
-the ncu captures summarised under profiles/.
+average device time per launch and the achieved rate.
+batch: the batched workload (256 uneven 2D instances, nelx ~ U{60..480},
+seed 20050543): autotunes the tile shapes, then times design iterations.
+net: forward pass and one training step (forward, backward, Adam) of the
+warm-start network on an [N][D][H][W] input.
 """
 import argparse
 import json
 import math
+import time
 
+import numpy as np
 import torch
 
-from . import TO_FP64, TO_MIXED, build as B, default_params, inputs as I
-from .topopt import Grid
+from . import TO_FP64, TO_MIXED, TO_PC_GMG, build as B, default_params, inputs as I
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--grid", default="256x128x128")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--reps", type=int, default=3)
-    a = ap.parse_args()
-    B.build()
+def bench_ku(a):
+    from .topopt import Grid
     nelx, nely, nelz = (int(v) for v in a.grid.split("x"))
     dim = 3 if nelz else 2
     F, fixed = I.cantilever_3d(nelx, nely, nelz) if dim == 3 else I.mbb_half_beam(nelx, nely)
@@ -35,9 +37,80 @@ def main():
     if prec == TO_FP64:
         rate = {"TFLOP/s": 2.0 * (24 if dim == 3 else 8) ** 2 * g.nel / (us * 1e-6) / 1e12}
     else:
-        rate = {"GB/s": 4.0 * (2 * g.ndof + g.nel) / (us * 1e-6) / 1e9}
+        rate = {"GB/s": 4.0 * (2 * g.ndof + g.nel) / (us * 1e-6) / 1e9,
+                "TFLOP/s": 2.0 * (24 if dim == 3 else 8) ** 2 * g.nel / (us * 1e-6) / 1e12}
     print(json.dumps({"grid": a.grid, "precision": a.precision, "nel": g.nel, "ndof": g.ndof,
                       "us_per_launch": round(us, 3), **{k: round(v, 3) for k, v in rate.items()}}))
+
+
+def bench_batch(a):
+    from .topopt import Batch
+    insts = I.batched_instances(a.count, seed=20050543)
+    p = default_params(2, 8, 4, precision=TO_MIXED, precond=TO_PC_GMG, mg_nu=1, penal=3.0, beta=2.0,
+                       cg_rtol=1e-8, cg_maxit=100000, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, 1))
+    F = torch.from_numpy(np.concatenate([q.F for q in insts])).cuda()
+    fixed = torch.from_numpy(np.concatenate([q.fixed for q in insts])).cuda()
+    x0 = torch.from_numpy(np.concatenate([I.initial_design(q.nelx * q.nely, q.volfrac) for q in insts])).cuda()
+    b = Batch(p, [(q.nelx, q.nely, q.volfrac, q.rmin) for q in insts], F, fixed, x0)
+    tune = b.autotune(reps=5) if a.autotune else None
+    steps = []
+    for _ in range(a.steps):
+        info = b.step()
+        steps.append({k: info[k] for k in ("loop", "ms", "max_refinements", "max_inner_iters", "inner_passes",
+                                           "newton_passes", "oc_passes", "max_rel_res", "kernels")})
+    ms = [s["ms"] for s in steps[1:]] or [steps[0]["ms"]]
+    print(json.dumps({"instances": a.count, "elements": b.nel, "dofs": b.ndof, "tiles": tune and
+                      {"node": tune["node"], "elem": tune["elem"]},
+                      "design_iterations_per_s": round(1000.0 / (sum(ms) / len(ms)), 3),
+                      "elements_per_s": round(b.nel * 1000.0 / (sum(ms) / len(ms)), 1), "steps": steps}))
+
+
+def bench_net(a):
+    from .learned import Net, he_init
+    D, H, W = (int(v) for v in a.shape.split("x"))
+    net = Net(base=16, bf16=True)
+    net.set_params(he_init(16, seed=1))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((a.batch, D, H, W, 4), device="cuda", generator=g)
+    t = torch.randn((a.batch, D, H, W, 3), device="cuda", generator=g)
+    m = torch.ones((a.batch, D, H, W), dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net.forward(x)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.reps):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / a.reps
+    net.accumulate(x, t, m)
+    net.adam(1e-4)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.reps):
+        net.accumulate(x, t, m)
+        net.adam(1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    trn = e0.elapsed_time(e1) / a.reps
+    print(json.dumps({"shape": [a.batch, D, H, W], "params": net.n_params, "forward_ms": round(fwd, 3),
+                      "train_step_ms": round(trn, 3)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net"])
+    ap.add_argument("--grid", default="256x128x128")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--count", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--shape", default="52x28x28")
+    ap.add_argument("--batch", type=int, default=1)
+    a = ap.parse_args()
+    B.build()
+    {"ku": bench_ku, "batch": bench_batch, "net": bench_net}[a.what](a)
 
 
 if __name__ == "__main__":
