@@ -51,37 +51,68 @@ __global__ void kb_cond(BG* G, int which, int body, cudaGraphConditionalHandle h
     cudaGraphSetConditional(h, G->active[which] > 0 ? 1u : 0u);
 }
 
+// FP64 value v as an unevaluated float pair (hi + lo == v to about 48 bits).
+__device__ __forceinline__ float2 split_ff(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+// Filter inputs as float pairs, one FP64 operation per element (not per tap):
+// a[i] (forward), or a[i] * b[i] and b[i] (backward).
+__global__ void kb_split(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                         float2* __restrict__ o1, float2* __restrict__ o2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (b) {
+        o1[i] = split_ff(a[i] * b[i]);
+        o2[i] = split_ff(b[i]);
+    } else {
+        o1[i] = split_ff(a[i]);
+    }
+}
+
+// s += w * a in float-float: the product w_hi a_hi is split exactly (FMA), the
+// cross terms w_hi a_lo + w_lo a_hi are added in FP32 (w_lo a_lo is below the
+// pair's precision), and the sum is Knuth's TwoSum with the error carried in lo.
+__device__ __forceinline__ void ff_mac(float& hi, float& lo, float2 w, float2 a) {
+    const float p = __fmul_rn(w.x, a.x);
+    const float pe = fmaf(w.x, a.x, -p);
+    const float cross = fmaf(w.x, a.y, __fmul_rn(w.y, a.x));
+    const float s = hi + p;
+    const float bb = s - hi;
+    lo += ((hi - (s - bb)) + (p - bb)) + (pe + cross);
+    hi = s;
+}
+
 // Density filter (Eq. 2), 'N' padding by repeated reflection. Forward:
 // out = (A in) / Hs. Backward (chain rule of Eq. 7, A symmetric under 'N'):
 // out = A (dprj .* in) / Hs and out2 = dV A dprj / Hs with dV = 1 / (nEl f).
+// Inputs and weights arrive as float pairs (kb_split, host split of the taps)
+// and the taps accumulate in float-float arithmetic: FP64 accuracy without FP64
+// instructions in the loop of up to (2 ceil(rmin) - 1)^2 taps per element.
 template <bool BWD>
-__global__ void kb_filter(BK k, const int2* __restrict__ toff, const double* __restrict__ tw,
-                          const double* __restrict__ in, const double* __restrict__ dprj,
+__global__ void kb_filter(BK k, const int2* __restrict__ toff, const float2* __restrict__ tw,
+                          const float2* __restrict__ in, const float2* __restrict__ in2,
                           double* __restrict__ out, double* __restrict__ out2) {
     B_TILE(k)
     (void)S;
     const int ex = tx_, ey = ty_;
     if (ex >= I.nelx || ey >= I.nely) return;
     const long long b = I.el0;
-    double s = 0.0, s2 = 0.0;
+    float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;
     for (int j = 0; j < I.ntap; ++j) {
         const int2 o = toff[I.tap0 + j];
         int jx = ex + o.x, jy = ey + o.y;
         if (jx < 0 || jx >= I.nelx) jx = mirror_index(jx, I.nelx);
         if (jy < 0 || jy >= I.nely) jy = mirror_index(jy, I.nely);
         const long long m = b + jy + (long long)I.nely * jx;
-        const double w = tw[I.tap0 + j];
-        if (BWD) {
-            const double d = dprj[m];
-            s += w * (d * in[m]);
-            s2 += w * d;
-        } else {
-            s += w * in[m];
-        }
+        const float2 w = tw[I.tap0 + j];
+        ff_mac(sh, sl, w, in[m]);
+        if (BWD) ff_mac(qh, ql, w, in2[m]);
     }
     const long long e = b + ey + (long long)I.nely * ex;
-    out[e] = s / I.Hs;
-    if (BWD) out2[e] = I.dv * s2 / I.Hs;
+    out[e] = ((double)sh + (double)sl) / I.Hs;
+    if (BWD) out2[e] = I.dv * ((double)qh + (double)ql) / I.Hs;
 }
 
 // One pass of the eta search (Sec. 3.2) at the instance's current eta: sums of
@@ -276,8 +307,9 @@ __global__ void kb_inner_init(BK k, const float* __restrict__ dinv, const float*
             rr.add(r, r);
         }
     }
-    double v[2] = {rz.value(), rr.value()}, tot[2];
-    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[2] = {rz, rr};
+    double tot[2];
+    if (!seg_reduce_ff<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.rz = tot[0];
     S.irr0 = tot[1];
     S.inner_it = 0;
@@ -303,8 +335,9 @@ __global__ void kb_ku32(BK k, const KeP<float, 8> ke, const float* __restrict__ 
             pap.add(p32[i + c], y);
         }
     }
-    double v[1] = {pap.value()}, tot[1];
-    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[1] = {pap};
+    double tot[1];
+    if (!seg_reduce_ff<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     if (tot[0] > 0.0 && isfinite(tot[0])) {
         S.alpha = S.rz / tot[0];
     } else {  // breakdown: stop this inner solve, the FP64 test decides
@@ -335,8 +368,9 @@ __global__ void kb_inner_update(BK k, const float* __restrict__ dinv, float* __r
             rz.add(r, z);
         }
     }
-    double v[2] = {rr.value(), rz.value()}, tot[2];
-    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[2] = {rr, rz};
+    double tot[2];
+    if (!seg_reduce_ff<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.inner_it += 1;
     S.inner_total += 1;
     if (!(tot[0] > inner_rtol * inner_rtol * S.irr0) || S.inner_it >= maxit) {
@@ -381,8 +415,9 @@ __global__ void kb_mg_init(BK k, const float* __restrict__ r32, const float* __r
             rr.add(r, r);
         }
     }
-    double v[2] = {rz.value(), rr.value()}, tot[2];
-    if (!seg_reduce<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[2] = {rz, rr};
+    double tot[2];
+    if (!seg_reduce_ff<2>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.rz = tot[0];
     S.irr0 = tot[1];
     S.inner_it = 0;
@@ -407,8 +442,9 @@ __global__ void kb_mg_xr(BK k, float* __restrict__ x32, float* __restrict__ r32,
             rr.add(r, r);
         }
     }
-    double v[1] = {rr.value()}, tot[1];
-    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[1] = {rr};
+    double tot[1];
+    if (!seg_reduce_ff<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.inner_it += 1;
     S.inner_total += 1;
     if (!(tot[0] > inner_rtol * inner_rtol * S.irr0) || S.inner_it >= maxit) {
@@ -427,8 +463,9 @@ __global__ void kb_mg_rz(BK k, const float* __restrict__ r32, const float* __res
         rz.add(r32[i], z[i]);
         rz.add(r32[i + 1], z[i + 1]);
     }
-    double v[1] = {rz.value()}, tot[1];
-    if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
+    DotAcc<float> v[1] = {rz};
+    double tot[1];
+    if (!seg_reduce_ff<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.beta_cg = tot[0] / S.rz;
     S.rz = tot[0];
 }
@@ -789,7 +826,8 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
         const cudaGraphConditionalHandle h_oc = make_handle(st);
         KB_LAUNCH(kb_iter_begin, 1, 256, st, b->dG, b->dS, b->count, ft == 3 ? 1 : 0, h_eta);
         // RL.1: filter, eta, projection, change
-        KB_LAUNCH(kb_filter<false>, nb_e, te, st, ke, b->toff, b->tw, x, nullptr, b->xt, nullptr);
+        KB_LAUNCH(kb_split, div_up(b->nel, 256), 256, st, b->nel, x, nullptr, b->fs1, nullptr);
+        KB_LAUNCH(kb_filter<false>, nb_e, te, st, ke, b->toff, b->tw, b->fs1, nullptr, b->xt, nullptr);
         if (ft == 3) {
             b->k_static += captured_launches_reset();
             add_while(st, b->sb[0], h_eta, [&](cudaStream_t s) {
@@ -845,7 +883,8 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
         // RL.3: compliance, sensitivities, back-filter
         KB_LAUNCH(kb_compliance, nb_n, tn, st, kn, b->F, U);
         KB_LAUNCH(kb_sens, nb_e, te, st, ke, b->ke64, xPhys, U, b->dc, p.E0, p.Emin);
-        KB_LAUNCH(kb_filter<true>, nb_e, te, st, ke, b->toff, b->tw, b->dc, b->dprj, b->dcf, b->dV0);
+        KB_LAUNCH(kb_split, div_up(b->nel, 256), 256, st, b->nel, b->dc, b->dprj, b->fs1, b->fs2);
+        KB_LAUNCH(kb_filter<true>, nb_e, te, st, ke, b->toff, b->tw, b->fs1, b->fs2, b->dcf, b->dV0);
         // RL.4: OC with the lambda# bracket, continuation
         KB_LAUNCH(kb_oc_init, nb_e, te, st, ke, x, b->dcf, b->dV0, b->ocP);
         KB_LAUNCH(kb_cond, 1, 1, st, b->dG, (int)LOOP_OC, 0, h_oc);
@@ -936,7 +975,7 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
         TOPO_CUDA(cudaEventCreate(&b->ev1));
         // instance table and filter taps (Eq. 2: w = max(0, rmin - dist), window +-(ceil(rmin) - 1))
         std::vector<int2> toff;
-        std::vector<double> tw;
+        std::vector<float2> tw;
         b->hI.resize(count);
         long long el = 0, nd = 0;
         for (int i = 0; i < count; ++i) {
@@ -964,7 +1003,8 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
                     const double w = q.rmin - std::sqrt((double)(ox * ox + oy * oy));
                     if (w <= 0.0) continue;
                     toff.push_back(make_int2(ox, oy));
-                    tw.push_back(w);
+                    const float wh = (float)w;
+                    tw.push_back(make_float2(wh, (float)(w - (double)wh)));
                     hs += w;
                 }
             I.ntap = (int)toff.size() - I.tap0;
@@ -986,7 +1026,9 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
         b->dS = balloc<BS>(b, count);
         b->dG = balloc<BG>(b, 1);
         b->toff = balloc<int2>(b, toff.size());
-        b->tw = balloc<double>(b, tw.size());
+        b->tw = balloc<float2>(b, tw.size());
+        b->fs1 = balloc<float2>(b, el);
+        b->fs2 = balloc<float2>(b, el);
         b->ntiles = balloc<int4>(b, cap);
         b->etiles = balloc<int4>(b, cap);
         b->partials = balloc<double>(b, 2 * cap);
@@ -996,7 +1038,7 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
         for (float** a : {&b->dinv, &b->r32, &b->z32, &b->p32, &b->Ap32, &b->x32}) *a = balloc<float>(b, 2 * nd);
         for (double** a : {&b->r64, &b->p64, &b->Kp64}) *a = balloc<double>(b, 2 * nd);
         TOPO_CUDA(cudaMemcpyAsync(b->toff, toff.data(), toff.size() * sizeof(int2), cudaMemcpyHostToDevice, b->st));
-        TOPO_CUDA(cudaMemcpyAsync(b->tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, b->st));
+        TOPO_CUDA(cudaMemcpyAsync(b->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, b->st));
         TOPO_CUDA(cudaMemsetAsync(b->counters, 0, count * sizeof(unsigned), b->st));
         std::vector<double> K;
         element_matrix(2, base->nu, K);
@@ -1042,6 +1084,7 @@ to_status to_batch_autotune(to_batch* b, int32_t reps, to_tile_info* info) {
     sync_in(b);
     cudaStream_t st = b->st;
     KB_LAUNCH(kb_fill, div_up(b->nel, 256), 256, st, b->nel, b->xt, 0.5);
+    KB_LAUNCH(kb_split, div_up(b->nel, 256), 256, st, b->nel, b->xt, nullptr, b->fs1, nullptr);
     KB_LAUNCH(kb_fill32, div_up(b->nel, 256), 256, st, b->nel, b->E32, 0.5f);
     KB_LAUNCH(kb_fill32, div_up(2 * b->nnode, 256), 256, st, 2 * b->nnode, b->p32, 1.0f);
     double node_us[N_CAND], elem_us[N_CAND];
@@ -1064,7 +1107,7 @@ to_status to_batch_autotune(to_batch* b, int32_t reps, to_tile_info* info) {
             node_us[c] = 1e3 * ms / reps;
             TOPO_CUDA(cudaEventRecord(b->ev0, st));
             for (int r = 0; r < reps; ++r)
-                KB_LAUNCH(kb_filter<false>, b->n_et, th, st, ke, b->toff, b->tw, b->xt, nullptr, b->dc, nullptr);
+                KB_LAUNCH(kb_filter<false>, b->n_et, th, st, ke, b->toff, b->tw, b->fs1, nullptr, b->dc, nullptr);
             TOPO_CUDA(cudaEventRecord(b->ev1, st));
             TOPO_CUDA(cudaEventSynchronize(b->ev1));
             TOPO_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));

@@ -109,6 +109,63 @@ __device__ bool seg_reduce(const BK& k, int t0, int nt, unsigned* counter, doubl
     return true;
 }
 
+// (hi, lo) += (bh, bl) in float-float arithmetic (Knuth's TwoSum, then a
+// renormalisation); symmetric in its two operands, so an xor butterfly leaves
+// the same pair in every lane.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+    const float s = hi + bh;
+    const float bb = s - hi;
+    const float e = ((hi - (s - bb)) + (bh - bb)) + (lo + bl);
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// seg_reduce for float-float per-thread sums (DotAcc<float>): the warp sums
+// stay in FP32 pairs, FP64 enters once per warp (FP64 is 1/64 of the FP32 rate
+// on this part, and these reductions run in every inner PCG pass).
+template <int NV>
+__device__ bool seg_reduce_ff(const BK& k, int t0, int nt, unsigned* counter, DotAcc<float> (&a)[NV],
+                              double (&tot)[NV]) {
+    __shared__ double sm[NV * 32];
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        float hi = a[q].hi, lo = a[q].lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            ff_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+        if (lane == 0) sm[q * 32 + wid] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = warp_sum(lane < nw ? sm[q * 32 + lane] : 0.0);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) k.partials[q * k.pstride + blockIdx.x] = v[q];
+            __threadfence();
+            const unsigned t = atomicAdd(counter, 1u);
+            am_last = (t == (unsigned)nt - 1u);
+        }
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        s[q] = 0.0;
+        for (int j = threadIdx.x; j < nt; j += blockDim.x) s[q] += __ldcg(&k.partials[q * k.pstride + t0 + j]);
+    }
+    block_sum_dyn<NV>(s, sm);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = s[q];
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
 // ---------------------------------------------------------- element maths
 
 // Relaxed Heaviside projection (Eq. 1), its x-derivative (Eq. 8) and its
@@ -284,7 +341,8 @@ struct to_batch {
     topo::bt::BS* dS = nullptr;
     topo::bt::BG* dG = nullptr;
     int2* toff = nullptr;
-    double* tw = nullptr;
+    float2* tw = nullptr;      // filter weights as float pairs
+    float2 *fs1 = nullptr, *fs2 = nullptr;  // filter inputs as float pairs
     int4* ntiles = nullptr;
     int4* etiles = nullptr;
     int n_nt = 0, n_et = 0;
