@@ -206,6 +206,7 @@ def run_ours(args):
 
     from paper_2005_05436_gb300 import TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI
     from paper_2005_05436_gb300 import build as B, load
+    from paper_2005_05436_gb300 import replicas as R
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,13 +249,9 @@ def run_ours(args):
         timed, step_ms = _timed_steps(d, args.steps, flush, stream)
     torch.cuda.nvtx.range_pop()
     launches = lib.to_kernel_launches() - launches0
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = R.max_over_ranks(sum(step_ms), world, device="cuda")  # the slowest replica
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = R.whole_job_rate(world * args.steps, total_ms / 1000.0)
 
     # ---- roofline of the dominant kernel (the fine-level matrix-free K u)
     us = g.time_apply_K(d.xPhys, precision, reps=30)
@@ -309,11 +306,7 @@ def run_ours(args):
             out_host.copy_(d.x, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             x_host.copy_(out_host)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = R.max_over_ranks(time.perf_counter() - t0, world, device="cuda")
         e2e = {"value": round(world * args.steps / e2e_s, 4), "unit": UNIT,
                "h2d_bytes_per_step": nel * 8, "d2h_bytes_per_step": nel * 8 + 8 * 21}
     g.close()

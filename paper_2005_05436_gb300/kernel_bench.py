@@ -44,8 +44,19 @@ def bench_ku(a):
 
 
 def bench_batch(a):
+    """Under torchrun each rank advances its share of the instances (balanced by
+    element count, no collective in the data path); rank 0 prints the whole-job
+    rate over the slowest rank's time."""
+    from . import replicas as R
     from .topopt import Batch
+    rank, local, world = R.env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
     insts = I.batched_instances(a.count, seed=20050543)
+    if world > 1:
+        insts = [insts[i] for i in R.shard([q.nelx * q.nely for q in insts], world)[rank]]
     p = default_params(2, 8, 4, precision=TO_MIXED, precond=TO_PC_GMG, mg_nu=1, penal=3.0, beta=2.0,
                        cg_rtol=1e-8, cg_maxit=100000, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, 1))
     F = torch.from_numpy(np.concatenate([q.F for q in insts])).cuda()
@@ -59,10 +70,13 @@ def bench_batch(a):
         steps.append({k: info[k] for k in ("loop", "ms", "max_refinements", "max_inner_iters", "inner_passes",
                                            "newton_passes", "oc_passes", "max_rel_res", "kernels")})
     ms = [s["ms"] for s in steps[1:]] or [steps[0]["ms"]]
-    print(json.dumps({"instances": a.count, "elements": b.nel, "dofs": b.ndof, "tiles": tune and
-                      {"node": tune["node"], "elem": tune["elem"]},
-                      "design_iterations_per_s": round(1000.0 / (sum(ms) / len(ms)), 3),
-                      "elements_per_s": round(b.nel * 1000.0 / (sum(ms) / len(ms)), 1), "steps": steps}))
+    t_max = R.max_over_ranks(sum(ms) / len(ms) / 1000.0, world, device="cuda")
+    nel_all = R.sum_over_ranks(b.nel, world, device="cuda")
+    if rank == 0:
+        print(json.dumps({"instances": a.count, "ranks": world, "elements": int(nel_all), "dofs_rank0": b.ndof,
+                          "tiles": tune and {"node": tune["node"], "elem": tune["elem"]},
+                          "design_iterations_per_s": round(1.0 / t_max, 3),
+                          "elements_per_s": round(R.whole_job_rate(nel_all, t_max), 1), "steps": steps}))
 
 
 def bench_net(a):
