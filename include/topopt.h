@@ -99,7 +99,9 @@ typedef struct to_params {
                                (default); 1 the same kernels launched from a host loop, polled
                                every 8 iterations (for profilers that do not follow
                                device-side graph iterations) */
-    int32_t _pad2;
+    int32_t mg_coarse_every;/* GMG: rebuild the coarsest dense inverse at every k-th set-up (1: every
+                               set-up); an older inverse keeps the V-cycle symmetric positive
+                               definite, so only the iteration count can change */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("precond", C.c_int32), ("mg_levels", C.c_int32),
                 ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
-                ("loop_mode", C.c_int32), ("_pad2", C.c_int32)]
+                ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

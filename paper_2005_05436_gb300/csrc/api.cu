@@ -145,6 +145,7 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->precond == TO_PC_JACOBI || p->precond == TO_PC_GMG, "precond");
     TOPO_REQUIRE(p->deadline_cycles > 0, "deadline_cycles must be > 0");
     TOPO_REQUIRE(p->inner_rtol > 0.0 && p->inner_rtol < 1.0, "inner_rtol must be in (0, 1)");
+    TOPO_REQUIRE(p->mg_coarse_every >= 1 && p->mg_coarse_every <= 1000, "mg_coarse_every must be in [1, 1000]");
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
     TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 2, "ku_impl must be 0, 1 or 2");
@@ -195,6 +196,7 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->inner_rtol = 1e-3;
     p->mg_omega = 1.0;
     p->mg_nu = 2;
+    p->mg_coarse_every = 1;
     return TO_OK;
 }
 

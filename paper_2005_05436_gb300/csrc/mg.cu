@@ -36,14 +36,19 @@ __global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, c
             if (MODE == 2) o = r[i] - a[c];
             if (fixed[i]) o = T(0);
             out[i] = o;
-            if (PCG) dot.add(u[i], o);
+            if (PCG) dot.add(MODE == 1 ? r[i] : u[i], o);
         }
     }
     if (PCG) {
         double v[1] = {dot.value()}, tot[1];
         if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
-            pcg->pAp = tot[0];
-            pcg->alpha = pcg->rz / tot[0];
+            if (MODE == 1) {  // last V-cycle sweep: rz = r.z, beta = rz / rz_old
+                pcg->beta = tot[0] / pcg->rz;
+                pcg->rz = tot[0];
+            } else {          // K p: alpha = rz / p.Ap
+                pcg->pAp = tot[0];
+                pcg->alpha = pcg->rz / tot[0];
+            }
         }
     }
 }
@@ -69,14 +74,19 @@ __global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, co
             if (MODE == 2) o = r[i] - a[c];
             if (fixed[i]) o = T(0);
             out[i] = o;
-            if (PCG) dot.add(u[i], o);
+            if (PCG) dot.add(MODE == 1 ? r[i] : u[i], o);
         }
     }
     if (PCG) {
         double v[1] = {dot.value()}, tot[1];
         if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
-            pcg->pAp = tot[0];
-            pcg->alpha = pcg->rz / tot[0];
+            if (MODE == 1) {  // last V-cycle sweep: rz = r.z, beta = rz / rz_old
+                pcg->beta = tot[0] / pcg->rz;
+                pcg->rz = tot[0];
+            } else {          // K p: alpha = rz / p.Ap
+                pcg->pAp = tot[0];
+                pcg->alpha = pcg->rz / tot[0];
+            }
         }
     }
 }
@@ -106,6 +116,8 @@ void launch_fine_op(const to_grid* g, int mode, const T* E, const T* u, const T*
     }
     if (mode == 0 && pcg)
         fine_op_dispatch<T, 0, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
+    else if (mode == 1 && pcg)
+        fine_op_dispatch<T, 1, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
     else if (mode == 0)
         fine_op_dispatch<T, 0, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
     else if (mode == 1)
@@ -155,19 +167,24 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __r
     const int ex = (int)(t0 / dc.nelz);
     for (int i = threadIdx.x; i < NN * NN * NN; i += blockDim.x)
         pw[i] = (T)pn_weight<DIM>(i / (NN * NN), (i / NN) % NN, i % NN);
+    // children beyond an odd fine grid (ceil coarsening) contribute nothing
+    const bool all_inside = 2 * ex + 1 < df.nelx && 2 * ey + 1 < df.nely && (DIM == 2 || 2 * ez + 1 < df.nelz);
     if (FROM_FINE) {
-        if (threadIdx.x == 0) any_fixed = 0;
+        if (threadIdx.x == 0) any_fixed = all_inside ? 0 : 1;  // partial coarse elements take the general path
         if (threadIdx.x < NN) {
             const int j = threadIdx.x;
             const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j)), ezf = DIM == 3 ? 2 * ez + lnz(j) : 0;
-            Ej[j] = Ef[eyf + (long long)df.nely * (ezf + (long long)df.nelz * exf)];
+            const bool in = exf < df.nelx && eyf < df.nely && ezf < df.nelz;
+            Ej[j] = in ? Ef[eyf + (long long)df.nely * (ezf + (long long)df.nelz * exf)] : T(0);
         }
         __syncthreads();
         // the 3^dim fine nodes of the coarse element
         for (int i = threadIdx.x; i < (DIM == 3 ? 27 : 9) * DIM; i += blockDim.x) {
             const int c = i % DIM, q = i / DIM;
             const int ox = DIM == 3 ? q / 9 : q / 3, oz = DIM == 3 ? (q / 3) % 3 : 0, oy = q % 3;
-            const long long nf = (2 * ey + oy) + (long long)df.nny * ((DIM == 3 ? 2 * ez + oz : 0) + (long long)df.nnz * (2 * ex + ox));
+            const int fy = 2 * ey + oy, fz = DIM == 3 ? 2 * ez + oz : 0, fx = 2 * ex + ox;
+            if (fy >= df.nny || fz >= df.nnz || fx >= df.nnx) continue;
+            const long long nf = fy + (long long)df.nny * (fz + (long long)df.nnz * fx);
             if (fixed_f[DIM * nf + c]) any_fixed = 1;
         }
         __syncthreads();
@@ -186,7 +203,9 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __r
         const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j)), ezf = DIM == 3 ? 2 * ez + lnz(j) : 0;
         const long long ef = eyf + (long long)df.nely * (ezf + (long long)df.nelz * exf);
         T v;
-        if (FROM_FINE) {
+        if (exf >= df.nelx || eyf >= df.nely || ezf >= df.nelz) {
+            v = T(0);
+        } else if (FROM_FINE) {
             const int a = row / DIM, c = row % DIM, b = col / DIM, k = col % DIM;
             const long long na = (eyf + 1 - lny(a)) + (long long)df.nny * ((ezf + lnz(a)) + (long long)df.nnz * (exf + lnx(a)));
             const long long nb = (eyf + 1 - lny(b)) + (long long)df.nny * ((ezf + lnz(b)) + (long long)df.nnz * (exf + lnx(b)));
@@ -805,11 +824,12 @@ MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
         mg->lev[0].d = d;
         for (;;) {
             const Dims& c = mg->lev.back().d;
-            const bool even = c.nelx % 2 == 0 && c.nely % 2 == 0 && (dim == 2 || c.nelz % 2 == 0);
-            if (!even || c.ndof <= COARSE_TARGET) break;
+            if (c.ndof <= COARSE_TARGET) break;
             if (max_levels > 0 && (int)mg->lev.size() >= max_levels) break;
+            if (c.nelx < 2 && c.nely < 2 && (dim == 2 || c.nelz < 2)) break;
+            // ceil(n / 2): an odd grid coarsens too, its last coarse element covering one fine layer
             MGLevel<T> L;
-            L.d = make_dims(dim, c.nelx / 2, c.nely / 2, dim == 3 ? c.nelz / 2 : 0);
+            L.d = make_dims(dim, (c.nelx + 1) / 2, (c.nely + 1) / 2, dim == 3 ? (c.nelz + 1) / 2 : 0);
             mg->lev.push_back(L);
         }
         mg->nlev = (int)mg->lev.size();
@@ -908,7 +928,8 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
             TOPO_CHECK_LAUNCH();
         }
     }
-    if (mg->nc > 0) {
+    const bool refactor = mg->setups++ % mg->coarse_every == 0;
+    if (mg->nc > 0 && refactor) {
         MGLevel<T>& L = mg->lev.back();
         k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.fixed, mg->A);
         TOPO_CHECK_LAUNCH();
@@ -942,10 +963,10 @@ void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
 
 template <typename T>
 static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T* u, const T* r, T* out,
-                     const int* skip, cudaStream_t st) {
+                     const int* skip, cudaStream_t st, PcgScalars* pcg = nullptr) {
     MGLevel<T>& L = mg->lev[l];
     if (l == 0) {
-        launch_fine_op<T>(g, mode, E, u, r, L.dinv, out, mg->omega, skip, nullptr, st);
+        launch_fine_op<T>(g, mode, E, u, r, L.dinv, out, mg->omega, skip, pcg, st);
         return;
     }
     const int nb = div_up(L.d.nnodes, 256);
@@ -969,7 +990,8 @@ static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T
 }
 
 template <typename T>
-static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, const int* skip, cudaStream_t st) {
+static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, const int* skip, cudaStream_t st,
+                       PcgScalars* fuse_rz = nullptr, bool* fused = nullptr) {
     MGLevel<T>& L = mg->lev[l];
     const bool coarsest = l == mg->nlev - 1;
     if (coarsest && mg->nc > 0) {
@@ -1003,15 +1025,20 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         TOPO_CHECK_LAUNCH();
     }
     for (int s = 0; s < nu; ++s) {
-        level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st);
+        // the last fine-level sweep also forms r.z and the PCG beta when asked to
+        const bool last = l == 0 && s == nu - 1 && fuse_rz;
+        level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st, last ? fuse_rz : nullptr);
+        if (last && fused) *fused = true;
         std::swap(cur, oth);
     }
     return cur;
 }
 
 template <typename T>
-T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st) {
-    return vcycle_level<T>(g, mg, 0, mg->E, r, skip, st);
+T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st, PcgScalars* fuse_rz,
+             bool* fused) {
+    if (fused) *fused = false;
+    return vcycle_level<T>(g, mg, 0, mg->E, r, skip, st, fuse_rz, fused);
 }
 
 template MG<double>* mg_create<double>(to_grid*, int, int, double);
@@ -1020,7 +1047,9 @@ template void mg_destroy<double>(MG<double>*);
 template void mg_destroy<float>(MG<float>*);
 template void mg_setup<double>(to_grid*, MG<double>*, const double*, cudaStream_t);
 template void mg_setup<float>(to_grid*, MG<float>*, const float*, cudaStream_t);
-template double* mg_vcycle<double>(to_grid*, MG<double>*, const double*, const int*, cudaStream_t);
-template float* mg_vcycle<float>(to_grid*, MG<float>*, const float*, const int*, cudaStream_t);
+template double* mg_vcycle<double>(to_grid*, MG<double>*, const double*, const int*, cudaStream_t, PcgScalars*,
+                                     bool*);
+template float* mg_vcycle<float>(to_grid*, MG<float>*, const float*, const int*, cudaStream_t, PcgScalars*,
+                                   bool*);
 
 }  // namespace topo

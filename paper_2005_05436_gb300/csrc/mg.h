@@ -44,6 +44,8 @@ struct MG {
     T* Cj = nullptr;        // P_j^T Ke P_j of the 2^dim children of a coarse element
     int* status = nullptr;  // device: nonzero if the coarse Cholesky met a non-positive pivot
     const T* E = nullptr;   // fine modulus of the current set-up
+    int coarse_every = 1;   // rebuild the coarsest inverse at every k-th set-up
+    long long setups = 0;
     std::vector<void*> allocs;
 };
 
@@ -58,7 +60,10 @@ void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st);
 // Enqueue one V-cycle z = M r on level 0; returns the buffer holding z. All
 // launches are skipped while *skip != 0 (skip may be nullptr).
 template <typename T>
-T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st);
+// fuse_rz (optional): the last fine-level sweep also computes r.z and the PCG
+// beta into it (*fused reports whether it could).
+T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st, PcgScalars* fuse_rz = nullptr,
+             bool* fused = nullptr);
 
 // Fine-level operator kernels (matrix-free), shared with the Krylov solvers:
 // mode 0: out = K u (masked); 1: out = u + omega dinv (r - K u); 2: out = r - K u.

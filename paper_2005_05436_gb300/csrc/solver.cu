@@ -209,7 +209,10 @@ static void pcg_alloc(to_grid* g, Solver* sv, Pcg<T>& P, bool gmg) {
     P.dinv_j = salloc<T>(sv, n);
     P.E = sizeof(T) == 8 ? (T*)g->E : salloc<T>(sv, g->d.nel);
     P.s = salloc<PcgScalars>(sv, 1);
-    if (gmg) P.mg = mg_create<T>(g, g->p.mg_levels, g->p.mg_nu, g->p.mg_omega);
+    if (gmg) {
+        P.mg = mg_create<T>(g, g->p.mg_levels, g->p.mg_nu, g->p.mg_omega);
+        P.mg->coarse_every = g->p.mg_coarse_every;
+    }
 }
 
 // The body of one PCG iteration, captured into the WHILE node's body graph.
@@ -221,15 +224,21 @@ static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond,
     k_gpcg_xr<T><<<kblocks(n), KNT, 0, st>>>(n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter);
     TOPO_CHECK_LAUNCH();
     if (P.mg) {
-        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st);
-        k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
-                                                               g->counter);
+        // the tensor-core operator has no fused r.z epilogue
+        const bool tc = sizeof(T) == 4 && g->use_tc;
+        bool fused = false;
+        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st, tc ? nullptr : P.s, &fused);
+        if (!fused) {
+            k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
+                                                                   g->counter);
+            TOPO_CHECK_LAUNCH();
+        }
     } else {
         P.z = P.zj;
         k_gpcg_rz<T, false, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, P.mg ? nullptr : P.dinv_j, nullptr,
                                                               P.s, g->partials, g->counter);
+        TOPO_CHECK_LAUNCH();
     }
-    TOPO_CHECK_LAUNCH();
     k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(n, P.z, P.p, P.s, cond, set_cond);
     TOPO_CHECK_LAUNCH();
 }
