@@ -39,11 +39,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # dense TF32 : BF16 tensor throughput (nominal 1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 CUDA-core
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32 Walsh-tile
 # operator at 96x48x48 (ncu, cold cache), from
-# profiles/k_fine_op3_fp32_96x48x48_and_256x128x128.md; null for other kernels
+# profiles/k_walsh3_fp32_96x48x48_and_256x128x128.md; null for other kernels
 # and grids, and to be re-measured whenever that kernel changes
-TRAFFIC_FP32_96 = 4401152
+TRAFFIC_FP32_96 = 4403200
+# flops of one element product in the Walsh basis (27 x 3 forward, 53 for the
+# E-scaled blocks, 22 x 3 inverse, 21 for the x / y / z corner sums)
+WALSH_FLOPS_PER_ELEMENT = 221
 
 
 def parse_args():
@@ -55,8 +58,9 @@ def parse_args():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="gmg", choices=["jacobi", "gmg"])
     ap.add_argument("--grid", default="96x48x48")
-    ap.add_argument("--ku-impl", default="auto", choices=["auto", "cuda", "tc"],
-                    help="FP32 fine operator of the mixed path: CUDA cores or tcgen05 tensor cores")
+    ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"],
+                    help="3D stiffness operator: Walsh-factored element tiles (auto), the node-centric "
+                         "dense-Ke gather, or tcgen05 tensor cores for the FP32 inner solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
@@ -226,7 +230,7 @@ def run_ours(args):
     w = workload(args.grid)
     precision = TO_MIXED if args.precision == "mixed" else TO_FP64
     precond = TO_PC_GMG if args.precond == "gmg" else TO_PC_JACOBI
-    ku_impl = {"auto": 0, "cuda": 1, "tc": 2}[args.ku_impl]
+    ku_impl = {"auto": 0, "node": 1, "tc": 2, "walsh": 3}[args.ku_impl]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     net, learned_info = None, None
@@ -260,35 +264,57 @@ def run_ours(args):
     us = g.time_apply_K(d.xPhys, precision, reps=30)
     nel, ndof = g.nel, g.ndof
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    node = args.ku_impl == "node"
+    esize = 8 if precision == TO_FP64 else 4
+    alg_bytes = esize * (2 * ndof + nel)  # u read, y written, E read; connectivity implicit
+    gbs = alg_bytes / (us * 1e-6) / 1e9
+    dense = {"flops_per_element": 2 * 24 * 24, "tflops": round(2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12, 3)}
     if precision == TO_FP64:
-        achieved = 2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12
-        roof = {"kernel": "k_apply_K3<double> / k_fine_op3<double> (node-centric FP64 K u)", "bound": "alu",
-                "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
-                "peak_source": "derived: FP64 FMA units 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
-    else:
-        flops = 2.0 * 24 * 24 * nel  # the element contraction, counted once (algorithmic)
-        gbs = 4.0 * (2 * ndof + nel) / (us * 1e-6) / 1e9
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        hbm_eq = {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
-                  "algorithmic_bytes": "4 (2 nDof + nEl) per launch (u read, y write, E read)"}
-        if args.ku_impl == "tc":
-            peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
-            achieved = flops / (us * 1e-6) / 1e12
-            roof = {"kernel": "k_fine_op3_tc (tcgen05 TF32, split operands), FP32 K u of the inner solve",
-                    "bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": None, "us_per_launch": round(us, 2),
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio (of measured)",
-                    "hbm_equivalent": hbm_eq}
+        if node:
+            achieved = 2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12
+            roof = {"kernel": "k_apply_K3<double> (node-centric dense-Ke gather, FP64)", "bound": "alu",
+                    "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
+                    "peak_source": "derived: FP64 FMA units 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
         else:
-            achieved = flops / (us * 1e-6) / 1e12
-            traffic = TRAFFIC_FP32_96 if args.grid == "96x48x48" else None
-            roof = {"kernel": "k_fine_op3<float> (CUDA cores), FP32 K u of the inner solve", "bound": "alu",
-                    "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                    "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic, "traffic_unit": "bytes",
-                    "us_per_launch": round(us, 2),
-                    "peak_source": "derived: FP32 FMA lanes 152 SM x 128 x 2 flop x 2.07 GHz",
-                    "algorithmic_flops": "2 x 24 x 24 per element per launch", "hbm_equivalent": hbm_eq}
+            achieved = WALSH_FLOPS_PER_ELEMENT * nel / (us * 1e-6) / 1e12
+            roof = {"kernel": "k_walsh3<double> (Walsh-factored element tiles, FP64)", "bound": "alu",
+                    "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "us_per_launch": round(us, 2),
+                    "peak_source": "derived: FP64 FMA units 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                    "algorithmic_flops": f"{WALSH_FLOPS_PER_ELEMENT} per element per launch (factored product)",
+                    "dense_ke_equivalent": dense,
+                    "hbm_view": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4)}}
+    elif args.ku_impl == "tc":
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
+        achieved = 2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12
+        roof = {"kernel": "k_fine_op3_tc (tcgen05 TF32, split operands), FP32 K u of the inner solve",
+                "bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "us_per_launch": round(us, 2),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio (of measured)",
+                "hbm_view": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4)}}
+    elif node:
+        achieved = 2.0 * 24 * 24 * nel / (us * 1e-6) / 1e12
+        roof = {"kernel": "k_fine_op3<float> (node-centric dense-Ke gather), FP32 K u of the inner solve",
+                "bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "us_per_launch": round(us, 2),
+                "peak_source": "derived: FP32 FMA lanes 152 SM x 128 x 2 flop x 2.07 GHz",
+                "hbm_view": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4)}}
+    else:
+        alu = WALSH_FLOPS_PER_ELEMENT * nel / (us * 1e-6) / 1e12
+        traffic = TRAFFIC_FP32_96 if args.grid == "96x48x48" else None
+        roof = {"kernel": "k_walsh3<float> (Walsh-factored element tiles), FP32 K u of the inner solve",
+                "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs / hbm, 4), "traffic": traffic, "traffic_unit": "bytes",
+                "us_per_launch": round(us, 2),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_bytes": "4 (2 nDof + nEl) per launch (u read, y written, E read)",
+                "alu_view": {"algorithmic_flops": f"{WALSH_FLOPS_PER_ELEMENT} per element per launch",
+                             "achieved_tflops": round(alu, 3), "peak_tflops": round(FP32_PEAK_TFLOPS, 2),
+                             "frac": round(alu / FP32_PEAK_TFLOPS, 4)},
+                "dense_ke_equivalent": dense}
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None

@@ -92,9 +92,11 @@ typedef struct to_params {
     double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3) */
     double mg_omega;        /* GMG l1-Jacobi smoother weight (1.0) */
     int32_t mg_nu;          /* GMG pre- and post-smoothing sweeps per level (2) */
-    int32_t ku_impl;        /* FP32 fine operator of TO_MIXED: 0 auto (the faster one, at
-                               present the CUDA-core kernel), 1 CUDA cores, 2 tensor cores
-                               (tcgen05 TF32 with split operands, 3D only) */
+    int32_t ku_impl;        /* 3D stiffness operator: 0 auto (= 3); 1 node-centric gather with the
+                               dense 24x24 Ke (CUDA cores, FP32 and FP64); 2 tensor cores for the
+                               FP32 fine operator of TO_MIXED (tcgen05 TF32 with split operands;
+                               FP64 products as 3); 3 element tiles with Ke factored in the Walsh
+                               basis of the element corners (CUDA cores, FP32 and FP64) */
     int32_t loop_mode;      /* PCG loop: 0 one CUDA-graph launch with a conditional WHILE node
                                (default); 1 the same kernels launched from a host loop, polled
                                every 8 iterations (for profilers that do not follow
@@ -269,10 +271,11 @@ to_status to_oc_update_noalloc(int64_t nel, double* x, const double* dc, const d
 
 /* The FP32 stiffness operator of the TO_MIXED inner solve, y = K(xPhys) u
  * (masked as to_apply_K with masked = 1), for checking it against the FP64
- * one: u is rounded to FP32, the product runs on CUDA cores (impl = 1) or
- * tensor cores (impl = 2, tcgen05 TF32 with split operands, 3D only) and y is
- * returned widened to FP64. Needs a handle created with TO_MIXED. u[nDof],
- * y[nDof] device FP64. */
+ * one: u is rounded to FP32, the product runs as the node-centric dense-Ke
+ * gather on CUDA cores (impl = 1), on tensor cores (impl = 2, tcgen05 TF32
+ * with split operands, 3D only) or as Walsh-factored element tiles on CUDA
+ * cores (impl = 3, 3D only) and y is returned widened to FP64. Needs a handle
+ * created with TO_MIXED. u[nDof], y[nDof] device FP64. */
 to_status to_apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int32_t impl);
 
 /* Instrumentation (no counterpart in the paper): number of kernels this library

@@ -148,7 +148,7 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->mg_coarse_every >= 1 && p->mg_coarse_every <= 1000, "mg_coarse_every must be in [1, 1000]");
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
-    TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 2, "ku_impl must be 0, 1 or 2");
+    TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 3, "ku_impl must be 0, 1, 2 or 3");
     TOPO_REQUIRE(!(p->ku_impl == 2 && p->dim != 3), "the tensor-core operator is 3D only");
     const long long nnodes = (long long)(p->nelx + 1) * (p->nely + 1) * (p->dim == 3 ? p->nelz + 1 : 1);
     TOPO_REQUIRE(nnodes * p->dim < (1LL << 31) - 1, "grid too large for 32-bit DOF indices");
@@ -244,6 +244,16 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
             g->ke2f.k[i] = (float)K[i];
         }
     }
+    if (D == 24) {
+        double dev = 0.0;
+        if (!walsh_constants(K.data(), g->wk, &dev))
+            throw std::runtime_error("element matrix is not block diagonal in the Walsh basis (deviation " +
+                                     std::to_string(dev) + ")");
+        const WalshK<double>& w = g->wk;
+        g->wkf = WalshK<float>{(float)w.amb, (float)w.b, (float)w.c, (float)w.d,
+                               (float)w.f, (float)w.g, (float)w.pmq, (float)w.q};
+    }
+    g->node_centric = p->ku_impl == 1;
     g->Ke_host = K;
     g->Ke_dev = dalloc<double>(g, K.size());
     TOPO_CUDA(cudaMemcpyAsync(g->Ke_dev, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
@@ -395,8 +405,8 @@ to_status to_apply_K(to_grid* g, const double* xPhys, const double* u, double* y
         launch_mask_copy(d.ndof, u, g->v[6], g->fixed, g->st);
         src = g->v[6];
     }
-    launch_apply_K<double>(d, g->ke3, g->ke2, g->E, src, y, g->fixed, masked != 0, nullptr, nullptr,
-                           nullptr, g->st);
+    launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, src, y, g->fixed, masked != 0,
+                           g->st);
     grid_sync_out(g);
     TOPO_API_END
 }

@@ -45,6 +45,8 @@ struct to_grid {
     topo::KeP<double, 8> ke2{};
     topo::KeP<float, 24> ke3f{};
     topo::KeP<float, 8> ke2f{};
+    topo::WalshK<double> wk{};   // Ke in the Walsh basis (3D, walsh.cuh)
+    topo::WalshK<float> wkf{};
     std::vector<double> Ke_host;
     double* Ke_dev = nullptr;
 
@@ -76,6 +78,7 @@ struct to_grid {
     float* ke_tc = nullptr;    // Ke packed as the tensor-core B operand (TO_MIXED, 3D)
     int* tc_err = nullptr;     // device error word of the tensor-core operator
     bool use_tc = false;       // the FP32 fine operator runs on tensor cores
+    bool node_centric = false; // 3D K u by the node-centric dense-Ke kernels (ku_impl 1)
 
     topo::Solver* solver = nullptr;
     to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned
@@ -91,6 +94,12 @@ template <>
 inline const KeP<double, 24>& grid_ke3<double>(const to_grid* g) { return g->ke3; }
 template <>
 inline const KeP<float, 24>& grid_ke3<float>(const to_grid* g) { return g->ke3f; }
+template <typename T>
+inline const WalshK<T>& grid_wk(const to_grid* g);
+template <>
+inline const WalshK<double>& grid_wk<double>(const to_grid* g) { return g->wk; }
+template <>
+inline const WalshK<float>& grid_wk<float>(const to_grid* g) { return g->wkf; }
 template <typename T>
 inline const KeP<T, 8>& grid_ke2(const to_grid* g);
 template <>

@@ -60,10 +60,12 @@ to_status to_time_apply_K(to_grid* g, const double* xPhys, int32_t precision, in
         float ms = 0.f;
         if (precision == TO_FP64) {
             launch_modulus<double>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, g->E, st);
-            launch_apply_K<double>(d, g->ke3, g->ke2, g->E, u, y, g->fixed, true, nullptr, nullptr, nullptr, st);
+            launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, u, y, g->fixed,
+                               true, st);
             TOPO_CUDA(cudaEventRecord(e0, st));
             for (int r = 0; r < reps; ++r)
-                launch_apply_K<double>(d, g->ke3, g->ke2, g->E, u, y, g->fixed, true, nullptr, nullptr, nullptr, st);
+                launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, u, y, g->fixed,
+                               true, st);
             TOPO_CUDA(cudaEventRecord(e1, st));
         } else {
             time_apply_K_mixed(g, xPhys, reps, e0, e1);

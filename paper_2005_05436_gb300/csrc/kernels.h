@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "walsh.cuh"
 
 namespace topo {
 
@@ -19,10 +20,24 @@ struct PcgScalars {
 // y = K(E) u over all nodes (node-centric gather). mask_out zeroes fixed rows.
 // If pcg != nullptr: y = K p with the PCG dot p.Ap fused; the last block sets
 // alpha = rz / pAp; the launch is a no-op once pcg->done != 0.
+// 3D: the Walsh-factored element tiles (kernels_walsh.cu) unless node_centric.
 template <typename T>
-void launch_apply_K(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2, const T* E,
-                    const T* u, T* y, const uint8_t* fixed, bool mask_out, PcgScalars* pcg,
-                    double* partials, unsigned* counter, cudaStream_t st);
+void launch_apply_K(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2, const WalshK<T>& wk,
+                    bool node_centric, const T* E, const T* u, T* y, const uint8_t* fixed, bool mask_out,
+                    cudaStream_t st);
+
+// 3D K u by Walsh-factored element tiles (kernels_walsh.cu), with the fused
+// epilogues of the fine multigrid operator: mode 0 out = K u; 1 out = u +
+// omega dinv (r - K u); 2 out = r - K u; fixed rows zeroed if mask_out. With
+// pcg (modes 0 and 1): the FP64 dot u.out (mode 0) or r.out (mode 1) over the
+// grid and, in the last block, alpha = rz / pAp (mode 0) or beta = rz_new / rz,
+// rz = rz_new (mode 1); partials needs one value per block (npartials).
+// Reads of u cover the node planes around out's: out must not alias u.
+template <typename T>
+void launch_walsh_op3(const Dims& d, const WalshK<T>& wk, int mode, const T* E, const T* u, const T* r,
+                      const T* dinv, T* out, const uint8_t* fixed, bool mask_out, T omega, const int* skip,
+                      PcgScalars* pcg, double* partials, long long npartials, unsigned* counter, int nsm,
+                      cudaStream_t st);
 
 // Jacobi inverse diagonal: dinv[i] = 1 / K_ii (0 at fixed DOFs).
 template <typename T>

@@ -2,8 +2,9 @@
 // strain energies / compliance sensitivities and the lower-triangle CSR
 // assembly K^(s) (Ferrari & Sigmund 2020, Eqs. 4-6 and 10-11).
 //
-// K u is evaluated node-centrically: the thread of node n gathers, for each of
-// the (up to) 2^dim elements around n, E_e times the Ke rows of n's local DOFs
+// 3D K u runs on the Walsh-factored element tiles of kernels_walsh.cu; the
+// node-centric kernels here (2D, and 3D with ku_impl 1) gather, for each of the
+// (up to) 2^dim elements around node n, E_e times the Ke rows of n's local DOFs
 // against the element's displacement vector u_e. Every output is written by
 // exactly one thread (no atomics, deterministic), and all Ke indices are
 // compile-time constants so Ke is read from the constant bank.
@@ -73,30 +74,28 @@ __global__ void __launch_bounds__(256) k_apply_K2(Dims d, const KeP<T, 8> ke, co
 }
 
 template <typename T>
-void launch_apply_K(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2, const T* E,
-                    const T* u, T* y, const uint8_t* fixed, bool mask_out, PcgScalars* pcg,
-                    double* partials, unsigned* counter, cudaStream_t st) {
+void launch_apply_K(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2, const WalshK<T>& wk,
+                    bool node_centric, const T* E, const T* u, T* y, const uint8_t* fixed, bool mask_out,
+                    cudaStream_t st) {
     const int nb = div_up(d.nnodes, 256);
-    if (d.dim == 3) {
-        if (pcg)
-            k_apply_K3<T, true><<<nb, 256, 0, st>>>(d, ke3, E, u, y, fixed, mask_out, pcg, partials, counter);
-        else
-            k_apply_K3<T, false><<<nb, 256, 0, st>>>(d, ke3, E, u, y, fixed, mask_out, nullptr, nullptr, nullptr);
-    } else {
-        if (pcg)
-            k_apply_K2<T, true><<<nb, 256, 0, st>>>(d, ke2, E, u, y, fixed, mask_out, pcg, partials, counter);
-        else
-            k_apply_K2<T, false><<<nb, 256, 0, st>>>(d, ke2, E, u, y, fixed, mask_out, nullptr, nullptr, nullptr);
+    if (d.dim == 3 && !node_centric) {
+        launch_walsh_op3<T>(d, wk, 0, E, u, nullptr, nullptr, y, fixed, mask_out, T(0), nullptr, nullptr,
+                            nullptr, 0, nullptr, 0, st);
+        return;
     }
+    if (d.dim == 3)
+        k_apply_K3<T, false><<<nb, 256, 0, st>>>(d, ke3, E, u, y, fixed, mask_out, nullptr, nullptr, nullptr);
+    else
+        k_apply_K2<T, false><<<nb, 256, 0, st>>>(d, ke2, E, u, y, fixed, mask_out, nullptr, nullptr, nullptr);
     TOPO_CHECK_LAUNCH();
 }
 
 template void launch_apply_K<double>(const Dims&, const KeP<double, 24>&, const KeP<double, 8>&,
-                                     const double*, const double*, double*, const uint8_t*, bool,
-                                     PcgScalars*, double*, unsigned*, cudaStream_t);
+                                     const WalshK<double>&, bool, const double*, const double*, double*,
+                                     const uint8_t*, bool, cudaStream_t);
 template void launch_apply_K<float>(const Dims&, const KeP<float, 24>&, const KeP<float, 8>&,
-                                    const float*, const float*, float*, const uint8_t*, bool,
-                                    PcgScalars*, double*, unsigned*, cudaStream_t);
+                                    const WalshK<float>&, bool, const float*, const float*, float*,
+                                    const uint8_t*, bool, cudaStream_t);
 
 // ------------------------------------------------------------- diagonal --
 

@@ -96,6 +96,11 @@ static void fine_op_dispatch(const to_grid* g, const T* E, const T* u, const T* 
                              T omega, const int* skip, PcgScalars* pcg, cudaStream_t st) {
     const Dims& d = g->d;
     const int nb = div_up(d.nnodes, 256);
+    if (d.dim == 3 && !g->node_centric) {
+        launch_walsh_op3<T>(d, grid_wk<T>(g), MODE, E, u, r, dinv, out, g->fixed, true, omega, skip, pcg,
+                            g->partials, g->npartials, g->counter, g->nsm, st);
+        return;
+    }
     if (d.dim == 3)
         k_fine_op3<T, MODE, PCG><<<nb, 256, 0, st>>>(d, grid_ke3<T>(g), E, u, r, dinv, out, g->fixed, omega,
                                                      skip, pcg, g->partials, g->counter);

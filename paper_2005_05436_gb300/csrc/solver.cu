@@ -449,7 +449,8 @@ void solver_free(to_grid* g) {
 static void true_residual(to_grid* g, Solver* sv, const double* b, const double* x, double* r64, float* r32) {
     const long long n = g->d.ndof;
     TOPO_CUDA(cudaEventRecord(sv->ev[0], g->st));
-    launch_apply_K<double>(g->d, g->ke3, g->ke2, g->E, x, sv->y64, g->fixed, true, nullptr, nullptr, nullptr, g->st);
+    launch_apply_K<double>(g->d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, x, sv->y64, g->fixed,
+                               true, g->st);
     k_refine_resid<<<kblocks(n), KNT, 0, g->st>>>(n, b, sv->y64, r64, r32, g->fixed, sv->res, g->partials,
                                                    g->counter);
     TOPO_CHECK_LAUNCH();
@@ -536,8 +537,8 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             TOPO_CUDA(cudaEventRecord(sv->ev[0], st));
             k_fcg_beta<<<kblocks(n), KNT, 0, st>>>(n, P.x, sv->fKp, sv->fs, g->partials, g->counter);
             k_fcg_dir<<<div_up(n, 256), 256, 0, st>>>(n, P.x, sv->fp, sv->fs);
-            launch_apply_K<double>(d, g->ke3, g->ke2, g->E, sv->fp, sv->fKp, g->fixed, true, nullptr, nullptr,
-                                   nullptr, st);
+            launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, sv->fp, sv->fKp, g->fixed,
+                               true, st);
             k_fcg_alpha<<<kblocks(n), KNT, 0, st>>>(n, sv->fp, r64, sv->fKp, sv->fs, g->partials, g->counter);
             k_fcg_update<<<kblocks(n), KNT, 0, st>>>(n, x64, r64, sv->fp, sv->fKp, P.b, sv->fs, sv->res,
                                                     g->partials, g->counter);
@@ -571,11 +572,13 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
     return status;
 }
 
-// y = K u with the FP32 operator of the mixed path (impl 1: CUDA cores, 2: tensor cores).
+// y = K u with the FP32 operator of the mixed path (impl 1: node-centric dense Ke, 2: tensor cores,
+// 3: Walsh-factored element tiles).
 void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int impl) {
     Solver* sv = g->solver;
     TOPO_REQUIRE(g->p.precision == TO_MIXED, "handle was created for TO_FP64");
-    TOPO_REQUIRE(impl == 1 || (impl == 2 && g->ke_tc), "impl must be 1, or 2 on a 3D grid");
+    TOPO_REQUIRE(impl == 1 || (impl == 2 && g->ke_tc) || (impl == 3 && g->d.dim == 3),
+                 "impl must be 1, or 2 or 3 on a 3D grid");
     const Dims& d = g->d;
     const long long n = d.ndof;
     cudaStream_t st = g->st;
@@ -583,15 +586,18 @@ void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, i
     launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, P.E, st);
     k_cast_mask<double, float><<<div_up(n, 256), 256, 0, st>>>(n, u, P.p, g->fixed);
     TOPO_CHECK_LAUNCH();
-    const bool saved = g->use_tc;
+    const bool saved = g->use_tc, saved_nc = g->node_centric;
     g->use_tc = impl == 2;
+    g->node_centric = impl == 1;
     try {
         launch_fine_op<float>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, 0.f, nullptr, nullptr, st);
     } catch (...) {
         g->use_tc = saved;
+        g->node_centric = saved_nc;
         throw;
     }
     g->use_tc = saved;
+    g->node_centric = saved_nc;
     k_cast_mask<float, double><<<div_up(n, 256), 256, 0, st>>>(n, P.Ap, y, nullptr);
     TOPO_CHECK_LAUNCH();
     if (g->tc_err) {

@@ -237,10 +237,10 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
         apply_K_fp32(g, xPhys, w->Uh, w->KUh, 1);
         apply_K_fp32(g, xPhys, w->Up, w->KUp, 1);
     } else {
-        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr,
-                               st);
-        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Up, w->KUp, g->fixed, true, nullptr, nullptr, nullptr,
-                               st);
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Uh, w->KUh, g->fixed,
+                               true, st);
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Up, w->KUp, g->fixed,
+                               true, st);
     }
     launch_dot(d.ndof, g->F, w->Up, w->dots + 0, g->partials, g->counter, st);
     launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, g->partials, g->counter, st);
@@ -346,7 +346,8 @@ to_status to_learned_energy_grad(to_grid* g, const double* xPhys, const float* y
         launch_modulus<double>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, g->E, st);
         kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->cg, y, g->fixed, w->Uh);
         TOPO_CHECK_LAUNCH();
-        launch_apply_K<double>(d, g->ke3, g->ke2, g->E, w->Uh, w->KUh, g->fixed, true, nullptr, nullptr, nullptr, st);
+        launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Uh, w->KUh, g->fixed,
+                               true, st);
         launch_dot(d.ndof, g->F, w->Uh, w->dots + 6, g->partials, g->counter, st);
         launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 7, g->partials, g->counter, st);
         TOPO_CUDA(cudaMemcpyAsync(w->hdots + 6, w->dots + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

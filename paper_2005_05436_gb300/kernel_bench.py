@@ -30,7 +30,8 @@ def bench_ku(a):
     dim = 3 if nelz else 2
     F, fixed = I.cantilever_3d(nelx, nely, nelz) if dim == 3 else I.mbb_half_beam(nelx, nely)
     prec = TO_FP64 if a.precision == "fp64" else TO_MIXED
-    p = default_params(dim, nelx, nely, nelz, precision=prec, rmin=math.sqrt(3.0))
+    p = default_params(dim, nelx, nely, nelz, precision=prec, rmin=math.sqrt(3.0),
+                       ku_impl={"auto": 0, "node": 1, "tc": 2, "walsh": 3}[a.ku_impl])
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
     x = torch.from_numpy(I.random_design(g.nel, 1, "binary").clip(1e-3, 1.0)).cuda()
     us = g.time_apply_K(x, prec, reps=a.reps)
@@ -39,7 +40,8 @@ def bench_ku(a):
     else:
         rate = {"GB/s": 4.0 * (2 * g.ndof + g.nel) / (us * 1e-6) / 1e9,
                 "TFLOP/s": 2.0 * (24 if dim == 3 else 8) ** 2 * g.nel / (us * 1e-6) / 1e12}
-    print(json.dumps({"grid": a.grid, "precision": a.precision, "nel": g.nel, "ndof": g.ndof,
+    print(json.dumps({"grid": a.grid, "precision": a.precision, "ku_impl": a.ku_impl, "nel": g.nel,
+                      "ndof": g.ndof,
                       "us_per_launch": round(us, 3), **{k: round(v, 3) for k, v in rate.items()}}))
 
 
@@ -116,6 +118,7 @@ def main():
     ap.add_argument("--what", default="ku", choices=["ku", "batch", "net"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--steps", type=int, default=3)

@@ -18,6 +18,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(60, 20, 0), (67, 23, 0), (1, 1, 0), (9, 1, 0), (24, 12, 12), (13, 7, 5), (1, 1, 1), (5, 1, 3)]
+# 3D grids spanning several element tiles of the Walsh operator (31 x 7 node columns in
+# FP32, 31 x 3 in FP64) with ragged ends in every direction
+TILE_SHAPES = [(40, 70, 17), (9, 31, 7), (3, 62, 2), (33, 1, 15)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,10 +34,12 @@ def _xphys(g, seed):
     return simp_field(g.nel, seed)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("ku_impl", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES + TILE_SHAPES)
 @pytest.mark.parametrize("masked", [0, 1])
-def test_apply_K_fp64(shape, masked):
-    g, F, fixed = make_grid(shape, penal=3.0)
+def test_apply_K_fp64(shape, masked, ku_impl):
+    """ku_impl 0: Walsh-factored element tiles (3D); 1: node-centric dense-Ke gather."""
+    g, F, fixed = make_grid(shape, penal=3.0, ku_impl=ku_impl)
     og = O.Grid(*shape)
     Ke = O.element_stiffness(og.dim)
     xp = _xphys(g, 1)

@@ -97,6 +97,39 @@ def test_ke_uniform_strain_energy(dim):
     assert abs(u @ Ke @ u - energy) < 1e-13 * max(1.0, abs(energy))
 
 
+@pytest.mark.parametrize("nu", [0.1, 0.3, 0.45])
+def test_h8_ke_reflection_symmetry_and_walsh_blocks(nu):
+    """An isotropic cube element is unchanged by the reflections x -> 1 - x (and
+    y, z), which permute the corners and flip the reflected displacement
+    component. Consequently Ke is block diagonal in the Walsh basis of the
+    corners: mode c of component i only couples to modes c' of components j with
+    c xor e_i = c' xor e_j (eight 3x3 blocks), and the constant modes are null."""
+    Ke = O.element_stiffness(3, nu)
+    X = O._local_node_coords(3).astype(int)
+    key = {tuple(p): a for a, p in enumerate(X)}
+    for axis in range(3):
+        P = np.zeros((24, 24))
+        for a, p in enumerate(X):
+            q = p.copy()
+            q[axis] = 1 - q[axis]
+            b = key[tuple(q)]
+            for i in range(3):
+                P[3 * b + i, 3 * a + i] = -1.0 if i == axis else 1.0
+        assert np.abs(P @ Ke @ P.T - Ke).max() < 1e-15
+    H = np.zeros((24, 24))
+    for c in range(8):
+        cv = np.array([c >> 2, (c >> 1) & 1, c & 1])
+        for a, p in enumerate(X):
+            for i in range(3):
+                H[3 * c + i, 3 * a + i] = (-1.0) ** int(cv @ p)
+    M = H @ Ke @ H.T / 64
+    np.testing.assert_allclose(H.T @ M @ H, Ke, atol=1e-15)
+    char = [(c ^ (4 >> i)) for c in range(8) for i in range(3)]
+    off = max(abs(M[r, s]) for r in range(24) for s in range(24) if char[r] != char[s])
+    assert off < 1e-15 * np.abs(M).max()
+    assert np.abs(M[:3, :]).max() < 1e-15 and np.abs(M[:, :3]).max() < 1e-15
+
+
 # --------------------------------------------------------------- assembly --
 
 @pytest.mark.parametrize("shape", [(4, 3, 0), (3, 2, 2)])
