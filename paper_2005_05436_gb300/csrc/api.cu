@@ -444,7 +444,7 @@ to_status to_sensitivity(to_grid* g, const double* xPhys, const double* U, doubl
     if (!g || !xPhys || !U || !dc) return fail(TO_EINVAL, "NULL argument");
     TOPO_API_BEGIN
     grid_sync_in(g);
-    launch_sensitivity(g->d, g->ke3, g->ke2, xPhys, U, g->passive, g->penal, g->p.E0, g->p.Emin, dc,
+    launch_sensitivity(g->d, g->ke3, g->ke2, g->wk, g->node_centric, xPhys, U, g->passive, g->penal, g->p.E0, g->p.Emin, dc,
                        &g->ds->esum, g->partials, g->counter, g->st);
     if (c_out) {
         launch_dot(g->d.ndof, g->F, U, &g->ds->c, g->partials, g->counter, g->st);
@@ -555,7 +555,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     const to_status sst = solve_state(g, g->F, s->U, &si);
     TOPO_CUDA(cudaEventRecord(g->ev_t[2], st));
     // RL.3 sensitivities and chain rule through projection and filter
-    launch_sensitivity(d, g->ke3, g->ke2, s->xPhys, s->U, g->passive, s->penal, p.E0, p.Emin, g->dc,
+    launch_sensitivity(d, g->ke3, g->ke2, g->wk, g->node_centric, s->xPhys, s->U, g->passive, s->penal, p.E0, p.Emin, g->dc,
                        &g->ds->esum, g->partials, g->counter, st);
     launch_dot(d.ndof, g->F, s->U, &g->ds->c, g->partials, g->counter, st);
     launch_dv(d.nel, g->passive, 1.0 / ((double)d.nel * p.volfrac), g->dV, st);

@@ -47,10 +47,11 @@ void launch_diag_inv(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2,
 // Element strain energies ce_e = u_e^T Ke u_e; dc_e = -p (E0-Emin) x^(p-1) ce_e on
 // active elements (0 on passive ones). Fused deterministic sum of E_e ce_e
 // written to *energy_sum.
+// 3D: the Walsh form of Ke (wk) unless node_centric.
 void launch_sensitivity(const Dims& d, const KeP<double, 24>& ke3, const KeP<double, 8>& ke2,
-                        const double* xphys, const double* U, const int8_t* passive,
-                        double penal, double E0, double Emin, double* dc, double* energy_sum,
-                        double* partials, unsigned* counter, cudaStream_t st);
+                        const WalshK<double>& wk, bool node_centric, const double* xphys, const double* U,
+                        const int8_t* passive, double penal, double E0, double Emin, double* dc,
+                        double* energy_sum, double* partials, unsigned* counter, cudaStream_t st);
 
 // CSR lower triangle K^(s): row counts, then fill (row_ptr from a scan).
 void launch_lower_row_counts(const Dims& d, int32_t* counts, cudaStream_t st);

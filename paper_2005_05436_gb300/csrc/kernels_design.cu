@@ -246,8 +246,11 @@ __global__ void __launch_bounds__(ONT) k_oc(long long n, double* __restrict__ x,
             for (int k = 0; k < OC_NC; ++k) v[k] = 0.0;
             for (long long i = i0; i < n; i += stride) {
                 if (passive && passive[i] != 0) continue;
+                // max(max(min(min(t, x + m), 1), x - m), 0) = max(min(t, hi), lo) exactly
+                const double xi = x[i], o = ocp[i];
+                const double hi = fmin(xi + move, 1.0), lo = fmax(xi - move, 0.0);
 #pragma unroll
-                for (int k = 0; k < OC_NC; ++k) v[k] += newx(i, inv[k]);
+                for (int k = 0; k < OC_NC; ++k) v[k] += fmax(fmin(o * inv[k], hi), lo);
             }
             if (!grid_totals<ONT, OC_NC>(v, partials, parity, bar, deadline, tot)) return;
             parity ^= 1;

@@ -186,12 +186,58 @@ __global__ void __launch_bounds__(256) k_sensitivity(Dims d, const KeP<double, D
     if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) *energy_sum = tot[0];
 }
 
+// 3D: ce_e = u_e^T Ke u_e = w^T M w with w the Walsh modes of u_e over the
+// corners and M the block-diagonal form of Ke (walsh.cuh): about 170 FP64
+// operations per element instead of the dense quadratic form's 324.
+__global__ void __launch_bounds__(256) k_sensitivity3_walsh(Dims d, const WalshK<double> wk,
+                                                            const double* __restrict__ xphys,
+                                                            const double* __restrict__ U,
+                                                            const int8_t* __restrict__ passive, double penal,
+                                                            double E0, double Emin, double* __restrict__ dc,
+                                                            double* energy_sum, double* partials,
+                                                            unsigned* counter) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double esum = 0.0;
+    if (e < d.nel) {
+        const int ey = (int)(e % d.nely);
+        const long long t = e / d.nely;
+        const int ez = (int)(t % d.nelz);
+        const int ex = (int)(t / d.nelz);
+        double u[3][8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {  // corner g = 4 gx + 2 gy + gz: node (ex + gx, ey + gy, ez + gz)
+            const long long m = (ey + ((g >> 1) & 1)) + (long long)d.nny * ((ez + (g & 1)) + (long long)d.nnz * (ex + (g >> 2)));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) u[c][g] = U[3 * m + c];
+        }
+        double W[3][8], Z[3][8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) walsh_fwd<double>(u[c], W[c]);
+        walsh_blocks<double>(wk, 1.0, W[0], W[1], W[2], Z[0], Z[1], Z[2]);
+        double ce = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 1; q < 8; ++q) ce = fma(W[c][q], Z[c][q], ce);
+        const double x = xphys[e];
+        const double xp1 = pow(x, penal - 1.0);
+        const double Ee = Emin + xp1 * x * (E0 - Emin);
+        esum = Ee * ce;
+        dc[e] = (passive && passive[e] != 0) ? 0.0 : -penal * (E0 - Emin) * xp1 * ce;
+    }
+    double v[1] = {esum}, tot[1];
+    if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) *energy_sum = tot[0];
+}
+
 void launch_sensitivity(const Dims& d, const KeP<double, 24>& ke3, const KeP<double, 8>& ke2,
-                        const double* xphys, const double* U, const int8_t* passive, double penal,
-                        double E0, double Emin, double* dc, double* energy_sum, double* partials,
-                        unsigned* counter, cudaStream_t st) {
+                        const WalshK<double>& wk, bool node_centric, const double* xphys, const double* U,
+                        const int8_t* passive, double penal, double E0, double Emin, double* dc,
+                        double* energy_sum, double* partials, unsigned* counter, cudaStream_t st) {
     const int nb = div_up(d.nel, 256);
-    if (d.dim == 3)
+    if (d.dim == 3 && !node_centric)
+        k_sensitivity3_walsh<<<nb, 256, 0, st>>>(d, wk, xphys, U, passive, penal, E0, Emin, dc, energy_sum,
+                                                 partials, counter);
+    else if (d.dim == 3)
         k_sensitivity<24><<<nb, 256, 0, st>>>(d, ke3, xphys, U, passive, penal, E0, Emin, dc,
                                               energy_sum, partials, counter);
     else

@@ -996,7 +996,7 @@ static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T
 
 template <typename T>
 static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, const int* skip, cudaStream_t st,
-                       PcgScalars* fuse_rz = nullptr, bool* fused = nullptr) {
+                       PcgScalars* fuse_rz = nullptr, bool* fused = nullptr, bool first_done = false) {
     MGLevel<T>& L = mg->lev[l];
     const bool coarsest = l == mg->nlev - 1;
     if (coarsest && mg->nc > 0) {
@@ -1004,8 +1004,10 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         TOPO_CHECK_LAUNCH();
         return L.z;
     }
-    k_jacobi_first<T><<<div_up(L.d.ndof, 256), 256, 0, st>>>(L.d.ndof, L.dinv, rhs, L.z, mg->omega, skip);
-    TOPO_CHECK_LAUNCH();
+    if (!first_done) {
+        k_jacobi_first<T><<<div_up(L.d.ndof, 256), 256, 0, st>>>(L.d.ndof, L.dinv, rhs, L.z, mg->omega, skip);
+        TOPO_CHECK_LAUNCH();
+    }
     T* cur = L.z;
     T* oth = L.t;
     const int nu = coarsest ? 4 * mg->nu : mg->nu;
@@ -1041,9 +1043,9 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
 
 template <typename T>
 T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st, PcgScalars* fuse_rz,
-             bool* fused) {
+             bool* fused, bool first_done) {
     if (fused) *fused = false;
-    return vcycle_level<T>(g, mg, 0, mg->E, r, skip, st, fuse_rz, fused);
+    return vcycle_level<T>(g, mg, 0, mg->E, r, skip, st, fuse_rz, fused, first_done);
 }
 
 template MG<double>* mg_create<double>(to_grid*, int, int, double);
@@ -1053,8 +1055,8 @@ template void mg_destroy<float>(MG<float>*);
 template void mg_setup<double>(to_grid*, MG<double>*, const double*, cudaStream_t);
 template void mg_setup<float>(to_grid*, MG<float>*, const float*, cudaStream_t);
 template double* mg_vcycle<double>(to_grid*, MG<double>*, const double*, const int*, cudaStream_t, PcgScalars*,
-                                     bool*);
+                                     bool*, bool);
 template float* mg_vcycle<float>(to_grid*, MG<float>*, const float*, const int*, cudaStream_t, PcgScalars*,
-                                   bool*);
+                                   bool*, bool);
 
 }  // namespace topo

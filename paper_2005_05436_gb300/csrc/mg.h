@@ -62,8 +62,10 @@ void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st);
 template <typename T>
 // fuse_rz (optional): the last fine-level sweep also computes r.z and the PCG
 // beta into it (*fused reports whether it could).
+// first_done: the caller has already formed level 0's first damped Jacobi
+// iterate lev[0].z = omega lev[0].dinv r.
 T* mg_vcycle(to_grid* g, MG<T>* mg, const T* r, const int* skip, cudaStream_t st, PcgScalars* fuse_rz = nullptr,
-             bool* fused = nullptr);
+             bool* fused = nullptr, bool first_done = false);
 
 // Fine-level operator kernels (matrix-free), shared with the Krylov solvers:
 // mode 0: out = K u (masked); 1: out = u + omega dinv (r - K u); 2: out = r - K u.

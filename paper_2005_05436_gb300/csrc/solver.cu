@@ -85,10 +85,13 @@ __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restric
 }
 
 // x += alpha p; r -= alpha Ap; rr; iteration count and the stopping tests.
+// With dinv0 (multigrid): also the V-cycle's first fine-level iterate
+// z0 = omega dinv0 r (the k_jacobi_first of level 0, fused).
 template <typename T>
 __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x, T* __restrict__ r,
                                                  const T* __restrict__ p, const T* __restrict__ Ap, PcgScalars* s,
-                                                 double* partials, unsigned* counter) {
+                                                 double* partials, unsigned* counter, const T* __restrict__ dinv0,
+                                                 T* __restrict__ z0, T omega) {
     if (s->done) return;
     const T alpha = (T)s->alpha;
     DotAcc<T> acc;
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * Ap[i];
         r[i] = ri;
+        if (dinv0) z0[i] = omega * dinv0[i] * ri;
         acc.add(ri, ri);
     }
     double v[1] = {acc.value()};
@@ -286,13 +290,16 @@ static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond,
     const long long n = g->d.ndof;
     const int* skip = &P.s->done;
     launch_fine_op<T>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, T(0), skip, P.s, st);
-    k_gpcg_xr<T><<<kblocks(n), KNT, 0, st>>>(n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter);
+    const MGLevel<T>* L0 = P.mg ? &P.mg->lev[0] : nullptr;
+    k_gpcg_xr<T><<<kblocks(n), KNT, 0, st>>>(n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter,
+                                             L0 ? L0->dinv : nullptr, L0 ? L0->z : nullptr,
+                                             P.mg ? P.mg->omega : T(0));
     TOPO_CHECK_LAUNCH();
     if (P.mg) {
         // the tensor-core operator has no fused r.z epilogue
         const bool tc = sizeof(T) == 4 && g->use_tc;
         bool fused = false;
-        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st, tc ? nullptr : P.s, &fused);
+        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st, tc ? nullptr : P.s, &fused, true);
         if (!fused) {
             k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
                                                                    g->counter);
