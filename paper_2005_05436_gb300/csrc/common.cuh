@@ -152,6 +152,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV*NT/3
     __syncthreads();
 }
 
+// This thread's share of sum_i p[i] (i = threadIdx.x + k NT), in eight
+// independent chains so that eight loads are in flight; the order is fixed by
+// n and NT, so the result is deterministic.
+template <int NT>
+__device__ __forceinline__ double partial_sum(const double* p, int n) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0, a7 = 0.0, t = 0.0;
+    int i = threadIdx.x;
+    for (; i + 7 * NT < n; i += 8 * NT) {
+        a0 += __ldcg(&p[i]);
+        a1 += __ldcg(&p[i + NT]);
+        a2 += __ldcg(&p[i + 2 * NT]);
+        a3 += __ldcg(&p[i + 3 * NT]);
+        a4 += __ldcg(&p[i + 4 * NT]);
+        a5 += __ldcg(&p[i + 5 * NT]);
+        a6 += __ldcg(&p[i + 6 * NT]);
+        a7 += __ldcg(&p[i + 7 * NT]);
+    }
+    for (; i < n; i += NT) t += __ldcg(&p[i]);
+    return (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) + t;
+}
+
 // Two-level deterministic reduction inside one launch: every block stores its
 // NV partials, the last block to arrive sums them in block order and returns
 // true with the totals in tot (thread 0 valid). partials: [NV * gridDim.x].
@@ -176,10 +197,7 @@ __device__ bool last_block_totals(double (&v)[NV], double* partials, unsigned* c
     __threadfence();
     double s[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        s[k] = 0.0;
-        for (int i = threadIdx.x; i < (int)nb; i += NT) s[k] += __ldcg(&partials[k * nb + i]);
-    }
+    for (int k = 0; k < NV; ++k) s[k] = partial_sum<NT>(partials + (size_t)k * nb, (int)nb);
     block_sum<NT, NV>(s, sm);
 #pragma unroll
     for (int k = 0; k < NV; ++k) tot[k] = s[k];

@@ -633,10 +633,11 @@ __global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const uint8_t*
 
 // Coarsest-level dense inverse, in the solve's precision T, in four kernels:
 //  1. blocked right-looking Cholesky A = L L^T by one CTA: the NB x NB diagonal
-//     block is factored by one warp in shared memory, the column panel below it
-//     is solved row by row and staged in shared memory, then the trailing lower
-//     triangle is updated from the staged panel (n/NB barrier phases instead of
-//     3 n). A pivot below 1e-6 of the original diagonal is floored there and
+//     block is factored in shared memory by the whole CTA (one thread per
+//     element, three barriers per column), the column panel below it is solved
+//     row by row (reciprocal pivots) and staged in shared memory, then the
+//     trailing lower triangle is updated from the staged panel in 4 x 4
+//     register tiles (n/NB panel phases instead of 3 n). A pivot below 1e-6 of the original diagonal is floored there and
 //     flagged, which keeps the factor that of an SPD matrix.
 //  2. inverses of the diagonal blocks of L (one CTA each);
 //  3. W = L^{-1} block column by block column (one CTA per block column);
@@ -652,66 +653,100 @@ __global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, in
     extern __shared__ __align__(16) unsigned char chol_smem[];
     T* Dg = (T*)chol_smem;  // NB x LD diagonal block
     T* Pn = Dg + NB * LD;   // up to n x LD panel
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    __shared__ T rdiag[NB];  // reciprocals of the factored diagonal
+    const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) *status = 0;
-    for (int k = tid; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
+    for (int k = tid; k < n; k += nt) diag0[k] = A[(long long)k * n + k];
     __syncthreads();
     for (int k0 = 0; k0 < n; k0 += NB) {
         const int kw = min(NB, n - k0), k1 = k0 + kw, m = n - k1;
-        for (int i = tid; i < kw * kw; i += blockDim.x) {
+        for (int i = tid; i < kw * kw; i += nt) {
             const int r = i / kw, c = i % kw;
             Dg[r * LD + c] = c <= r ? A[(long long)(k0 + r) * n + k0 + c] : T(0);
         }
         __syncthreads();
-        if (warp == 0) {
-            for (int j = 0; j < kw; ++j) {
-                if (lane == 0) {
-                    T p = Dg[j * LD + j];
-                    const T fl = T(1e-6) * diag0[k0 + j];
-                    if (!(p > fl)) {
-                        *status = 1;
-                        p = fl > T(0) ? fl : T(1);
-                    }
-                    Dg[j * LD + j] = sqrt(p);
+        // the diagonal block, one thread per element (r, c), column by column
+        for (int j = 0; j < kw; ++j) {
+            if (tid == 0) {
+                T p = Dg[j * LD + j];
+                const T fl = T(1e-6) * diag0[k0 + j];
+                if (!(p > fl)) {
+                    *status = 1;
+                    p = fl > T(0) ? fl : T(1);
                 }
-                __syncwarp();
-                if (lane > j && lane < kw) Dg[lane * LD + j] /= Dg[j * LD + j];
-                __syncwarp();
-                if (lane > j && lane < kw)
-                    for (int l = j + 1; l <= lane; ++l) Dg[lane * LD + l] -= Dg[lane * LD + j] * Dg[l * LD + j];
-                __syncwarp();
+                Dg[j * LD + j] = sqrt(p);
             }
+            __syncthreads();
+            if (tid > j && tid < kw) Dg[tid * LD + j] /= Dg[j * LD + j];
+            __syncthreads();
+            for (int q = tid; q < kw * kw; q += nt) {
+                const int r = q / kw, c = q % kw;
+                if (c > j && c <= r) Dg[r * LD + c] -= Dg[r * LD + j] * Dg[c * LD + j];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int i = tid; i < kw * kw; i += blockDim.x) {
+        for (int i = tid; i < kw * kw; i += nt) {
             const int r = i / kw, c = i % kw;
             if (c <= r) A[(long long)(k0 + r) * n + k0 + c] = Dg[r * LD + c];
         }
+        if (tid < kw) rdiag[tid] = T(1) / Dg[tid * LD + tid];
+        __syncthreads();
         // panel rows k1..n-1: x L_kk^T = a  (forward substitution per row)
-        for (int i = tid; i < m; i += blockDim.x) {
+        for (int i = tid; i < m; i += nt) {
             T x[NB];
             const long long row = (long long)(k1 + i) * n + k0;
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
                 if (j < kw) {
                     T s = A[row + j];
+#pragma unroll
                     for (int l = 0; l < j; ++l) s -= x[l] * Dg[j * LD + l];
-                    x[j] = s / Dg[j * LD + j];
+                    x[j] = s * rdiag[j];
                     Pn[i * LD + j] = x[j];
                     A[row + j] = x[j];
                 }
             }
         }
         __syncthreads();
-        // trailing update of the lower triangle from the staged panel
-        for (int i = warp; i < m; i += nw) {
-            const T* pi = Pn + i * LD;
-            for (int j = lane; j <= i; j += 32) {
-                const T* pj = Pn + j * LD;
-                T s = T(0);
-                for (int l = 0; l < kw; ++l) s += pi[l] * pj[l];
-                A[(long long)(k1 + i) * n + k1 + j] -= s;
+        // trailing update of the lower triangle from the staged panel, 4 x 4
+        // register tiles (ti >= tj) over the m x m trailing block
+        const int mt = (m + 3) / 4;
+        const int ntile = mt * (mt + 1) / 2;
+        for (int t = tid; t < ntile; t += nt) {
+            int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while (ti * (ti + 1) / 2 > t) --ti;
+            const int tj = t - ti * (ti + 1) / 2;
+            T acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+            int ri[4], ci[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ri[r] = min(4 * ti + r, m - 1);
+                ci[r] = min(4 * tj + r, m - 1);
             }
+            for (int l = 0; l < kw; ++l) {
+                T a[4], b[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    a[r] = Pn[ri[r] * LD + l];
+                    b[r] = Pn[ci[r] * LD + l];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int gi = 4 * ti + r, gj = 4 * tj + c;
+                    if (gi < m && gj <= gi) A[(long long)(k1 + gi) * n + k1 + gj] -= acc[r][c];
+                }
         }
         __syncthreads();
     }
