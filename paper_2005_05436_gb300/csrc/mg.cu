@@ -494,9 +494,12 @@ __global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restric
 
 // ------------------------------------------------------- transfer operators
 
+// With dinv_c: also the coarse level's first damped Jacobi iterate
+// z_c = omega dinv_c r_c (its k_jacobi_first, fused).
 template <typename T, int DIM>
 __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __restrict__ rc,
-                           const uint8_t* __restrict__ fixed_c, const int* skip) {
+                           const uint8_t* __restrict__ fixed_c, const int* skip, const T* __restrict__ dinv_c,
+                           T* __restrict__ z_c, T omega) {
     if (skip && *skip) return;
     const long long N = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (N >= dc.nnodes) return;
@@ -518,7 +521,11 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
                 for (int c = 0; c < DIM; ++c) acc[c] += w * rf[DIM * f + c];
             }
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) rc[DIM * N + c] = fixed_c[DIM * N + c] ? T(0) : acc[c];
+    for (int c = 0; c < DIM; ++c) {
+        const T v = fixed_c[DIM * N + c] ? T(0) : acc[c];
+        rc[DIM * N + c] = v;
+        if (dinv_c) z_c[DIM * N + c] = omega * dinv_c[DIM * N + c] * v;
+    }
 }
 
 // 3D restriction with nine threads per coarse node: thread (tx, ty) sums the
@@ -528,7 +535,8 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
 template <typename T>
 __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* __restrict__ rf,
                                                     T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
-                                                    const int* skip) {
+                                                    const int* skip, const T* __restrict__ dinv_c,
+                                                    T* __restrict__ z_c, T omega) {
     __shared__ T part[9][32];
     if (skip && *skip) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -559,7 +567,9 @@ __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* _
     __syncthreads();
     if (ty % 3 != 0 || N >= dc.nnodes) return;
     const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
-    rc[3 * N + c] = fixed_c[3 * N + c] ? T(0) : a;
+    const T v = fixed_c[3 * N + c] ? T(0) : a;
+    rc[3 * N + c] = v;
+    if (dinv_c) z_c[3 * N + c] = omega * dinv_c[3 * N + c] * v;
 }
 
 template <typename T, int DIM>
@@ -1054,12 +1064,17 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         level_op<T>(g, mg, l, 2, E, cur, rhs, L.w, skip, st);
         MGLevel<T>& C = mg->lev[l + 1];
         const int nbc = div_up(C.d.nnodes, 256), nbf = div_up(L.d.nnodes, 256);
+        // the coarse level's first Jacobi iterate is formed by the restriction
+        // unless that level is the dense coarsest
+        const bool jf = !(l + 1 == mg->nlev - 1 && mg->nc > 0);
+        const T* dc_inv = jf ? C.dinv : nullptr;
         if (L.d.dim == 3)
-            k_restrict3s<T><<<div_up(C.d.nnodes, 32), dim3(32, 9), 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
+            k_restrict3s<T><<<div_up(C.d.nnodes, 32), dim3(32, 9), 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip,
+                                                                            dc_inv, C.z, mg->omega);
         else
-            k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip);
+            k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip, dc_inv, C.z, mg->omega);
         TOPO_CHECK_LAUNCH();
-        T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st);
+        T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st, nullptr, nullptr, jf);
         if (L.d.dim == 3)
             k_prolong_add<T, 3><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
         else
