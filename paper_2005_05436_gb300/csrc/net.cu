@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -115,6 +116,203 @@ __global__ void __launch_bounds__(CT) kn_conv_fwd(const TI* __restrict__ x, cons
         if (co0 + j >= Cout) continue;
         const float o = relu ? fmaxf(acc[j], 0.f) : acc[j];
         y[v * Cout + co0 + j] = fromf<TO>(o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05, kind::f16) forward convolution for BF16 layers with
+// Cin, Cout in {16, 32, 64}: an implicit GEMM with M = 128 voxels per CTA,
+// N = Cout and K = 27 taps x Cin. For each tap the CTA stages the 128 shifted
+// input rows (Cin BF16 values, zero outside the volume) and the tap's weights
+// (packed once per weight update into the same layout) into shared memory with
+// 16-byte cp.async, NSTAGE taps in flight; one thread issues the Cin/16 MMAs
+// of the tap (BF16 A and B, FP32 accumulation in tensor memory) and commits
+// them to the buffer's mbarrier, whose completion frees the buffer for the tap
+// NSTAGE - 1 later.
+// Operands use the canonical no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, LBO = 128 B along K, SBO = 128 Cin / 8 B between 8-row groups.
+namespace tcc {
+constexpr int MT = 128;                      // voxels (rows) per CTA
+constexpr int NTH = 128;                     // threads: one per row
+constexpr long long WAIT_LIMIT = 1LL << 26;  // mbarrier polls before giving up
+constexpr int NSTAGE = 4;                    // tap buffers in flight
+
+__host__ __device__ constexpr int core_byte(int r, int k, int KG) {
+    return ((r >> 3) * KG + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+    return d;
+}
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+        if (done) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+}  // namespace tcc
+
+// Packed weights of one layer: per tap, Cout rows x Cin columns in the core layout.
+__global__ void kn_pack_w(const bf16* __restrict__ W, bf16* __restrict__ Bp, int cin, int cout) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = 27LL * cin * cout;
+    if (i >= n) return;
+    const int co = (int)(i % cout);
+    const long long r = i / cout;
+    const int ci = (int)(r % cin), t = (int)(r / cin);  // W[t][ci][co]
+    Bp[(long long)t * cin * cout + tcc::core_byte(co, ci, cin / 8) / 2] = W[i];
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(tcc::NTH) kn_conv_fwd_tc(const bf16* __restrict__ x, const bf16* __restrict__ Bp,
+                                                           const float* __restrict__ bias, bf16* __restrict__ y,
+                                                           Shape s, int relu, int* err) {
+    using namespace tcc;
+    constexpr int KG = CIN / 8;
+    constexpr int A_BYTES = MT * CIN * 2, B_BYTES = COUT * CIN * 2, S_BYTES = A_BYTES + B_BYTES;
+    constexpr int TCOLS = COUT < 32 ? 32 : COUT;
+    constexpr uint32_t IDESC = idesc_bf16(COUT);
+    extern __shared__ __align__(1024) unsigned char smc[];
+    uint64_t* bar = (uint64_t*)(smc + NSTAGE * S_BYTES);  // one per stage
+    __shared__ uint32_t tmem_base;
+    __shared__ int ok_s;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long V = s.vox();
+    const long long v = (long long)blockIdx.x * MT + tid;  // this thread's row
+    const bool vin = v < V;
+    int n_ = 0, d_ = 0, h_ = 0, w_ = 0;
+    if (vin) decode(s, v, n_, d_, h_, w_);
+    (void)n_;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < NSTAGE; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[b])));
+        ok_s = 1;
+    }
+    // one commit group per call (empty past the last tap)
+    auto stage = [&](int t) {
+        if (t < 27) {
+            const int buf = t % NSTAGE;
+            const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+            const int dd = d_ + dx, hh = h_ + dy, ww = w_ + dz;
+            const bool ok = vin && dd >= 0 && dd < s.D && hh >= 0 && hh < s.H && ww >= 0 && ww < s.W;
+            const bf16* src = ok ? x + (v + ((long long)dx * s.H + dy) * s.W + dz) * CIN : x;
+            unsigned char* A = smc + buf * S_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < KG; ++kc) cp_async16(A + core_byte(tid, 8 * kc, KG), ok ? src + 8 * kc : x, ok);
+            const unsigned char* bsrc = (const unsigned char*)(Bp + (long long)t * CIN * COUT);
+            unsigned char* B = A + A_BYTES;
+            for (int c = tid; c < B_BYTES / 16; c += NTH) cp_async16(B + 16 * c, bsrc + 16 * c, true);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+#pragma unroll
+    for (int t = 0; t < NSTAGE - 1; ++t) stage(t);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+    for (int t = 0; t < 27; ++t) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NSTAGE - 2) : "memory");  // tap t has landed
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int buf = t % NSTAGE;
+            const uint32_t a0 = smem_u32(smc + buf * S_BYTES), b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < CIN / 16; ++k) {
+                const uint64_t da = make_desc(a0 + 256 * k, 128, KG * 128);
+                const uint64_t db = make_desc(b0 + 256 * k, 128, KG * 128);
+                const uint32_t acc = (t > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&bar[buf]))
+                         : "memory");
+        }
+        // with tap t queued behind it, wait for tap t - 1 and reuse its buffer for tap t + NSTAGE - 1
+        const int tn = t + NSTAGE - 1;
+        if (tn < 27 && t >= 1 && ok &&
+            !mbar_wait(smem_u32(&bar[(t - 1) % NSTAGE]), (uint32_t)(((t - 1) / NSTAGE) & 1)))
+            ok = false;
+        stage(tn);
+    }
+    // the taps whose commits were not awaited in the loop, in order
+    for (int t = 27 - NSTAGE; t < 27; ++t)
+        if (ok && !mbar_wait(smem_u32(&bar[t % NSTAGE]), (uint32_t)((t / NSTAGE) & 1))) ok = false;
+    if (!ok) {
+        ok_s = 0;
+        if (err) atomicExch(err, (int)TO_ETIMEOUT);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float acc[COUT];
+    {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(taddr + 8 * c8));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[8 * c8 + i] = __uint_as_float(r[i]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
+    }
+    if (!vin || !ok_s) return;
+    bf16* yo = y + v * COUT;
+#pragma unroll
+    for (int c8 = 0; c8 < COUT / 8; ++c8) {
+        __nv_bfloat162 q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float a = acc[8 * c8 + 2 * i] + bias[8 * c8 + 2 * i];
+            float b = acc[8 * c8 + 2 * i + 1] + bias[8 * c8 + 2 * i + 1];
+            if (relu) {
+                a = fmaxf(a, 0.f);
+                b = fmaxf(b, 0.f);
+            }
+            q[i] = __floats2bfloat162_rn(a, b);
+        }
+        *reinterpret_cast<uint4*>(yo + 8 * c8) = *reinterpret_cast<const uint4*>(q);
     }
 }
 
@@ -375,6 +573,10 @@ struct to_net {
     double* partials = nullptr; // reduction scratch
     unsigned* counter = nullptr;
     double* hsums = nullptr;    // pinned
+    // tensor-core forward: weights packed per tap (BF16 layers with Cin, Cout in {16, 32, 64})
+    bf16* wpack = nullptr;
+    long long wver = 0, pver = -1;  // weight version and the version packed
+    int* tc_err = nullptr;          // device error word of the tensor-core kernels
 };
 
 namespace {
@@ -451,9 +653,66 @@ void ensure_ws(to_net* n, const Shape& s) {
     n->shp = s;
 }
 
+bool tc_layer(const to_net* n, int k) {
+    static const bool on = [] {
+        const char* e = std::getenv("TOPO_NET_TC");
+        return !(e && e[0] == '0');
+    }();
+    const NLayer& Lk = n->L[k];
+    auto ok = [](int c) { return c == 16 || c == 32 || c == 64; };
+    // 16-byte cp.async of the packed weights: the layer's offset must be a multiple of 8 BF16 values
+    return on && n->cfg.bf16 && ok(Lk.cin) && ok(Lk.cout) && Lk.woff % 8 == 0;
+}
+
+template <int CIN, int COUT>
+void launch_conv_tc(to_net* n, const NLayer& Lk, const void* x, void* y, const Shape& s, int relu) {
+    constexpr int smem = tcc::NSTAGE * (tcc::MT * CIN * 2 + COUT * CIN * 2) + 8 * tcc::NSTAGE;
+    static bool attr = false;
+    if (!attr) {
+        TOPO_CUDA(cudaFuncSetAttribute(kn_conv_fwd_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    const unsigned blocks = (unsigned)((s.vox() + tcc::MT - 1) / tcc::MT);
+    kn_conv_fwd_tc<CIN, COUT><<<blocks, tcc::NTH, smem, n->st>>>((const bf16*)x, n->wpack + Lk.woff,
+                                                                 n->theta + Lk.boff, (bf16*)y, s, relu, n->tc_err);
+    TOPO_CHECK_LAUNCH();
+}
+
+void conv_fwd_tc(to_net* n, int k, const void* x, void* y, const Shape& s, int relu) {
+    const NLayer& Lk = n->L[k];
+#define TOPO_CT(CI, CO)                                          \
+    if (Lk.cin == CI && Lk.cout == CO) {                          \
+        launch_conv_tc<CI, CO>(n, Lk, x, y, s, relu);            \
+        return;                                                  \
+    }
+    TOPO_CT(16, 16) TOPO_CT(16, 32) TOPO_CT(32, 16) TOPO_CT(32, 32) TOPO_CT(32, 64) TOPO_CT(64, 32)
+    TOPO_CT(64, 64) TOPO_CT(16, 64) TOPO_CT(64, 16)
+#undef TOPO_CT
+    throw Error(TO_EINVAL, "tensor-core convolution: unsupported channel counts");
+}
+
+// Pack the weights of the tensor-core layers after every weight update.
+void pack_weights(to_net* n) {
+    if (n->pver == n->wver) return;
+    for (int k = 0; k < (int)n->L.size(); ++k) {
+        if (!tc_layer(n, k)) continue;
+        const NLayer& Lk = n->L[k];
+        const long long cnt = 27LL * Lk.cin * Lk.cout;
+        kn_pack_w<<<nb(cnt), 256, 0, n->st>>>((const bf16*)n->wact + Lk.woff, n->wpack + Lk.woff, Lk.cin, Lk.cout);
+        TOPO_CHECK_LAUNCH();
+    }
+    n->pver = n->wver;
+}
+
 template <typename TI, typename TO>
 void conv_fwd(to_net* n, int k, const void* x, void* y, const Shape& s, int relu) {
     const NLayer& Lk = n->L[k];
+    if constexpr (sizeof(TI) == 2 && sizeof(TO) == 2) {
+        if (tc_layer(n, k)) {
+            conv_fwd_tc(n, k, x, y, s, relu);
+            return;
+        }
+    }
     const TI* W = (const TI*)n->wact + Lk.woff;
     const float* b = n->theta + Lk.boff;
     const int blocks = nb(s.vox(), CT);
@@ -519,6 +778,7 @@ template <typename T>
 void forward(to_net* n, const float* x, const Shape& s) {
     const int c = n->cfg.base;
     const Shape s1{s.N, s.D / 2, s.H / 2, s.W / 2}, s2{s.N, s.D / 4, s.H / 4, s.W / 4};
+    if (sizeof(T) == 2) pack_weights(n);
     kn_cast<T><<<nb(s.vox() * 4), 256, 0, n->st>>>(x, (T*)n->xa, s.vox() * 4);
     TOPO_CHECK_LAUNCH();
     conv_fwd<T, T>(n, 0, n->xa, n->a0, s, 1);
@@ -666,6 +926,9 @@ to_status to_net_create(const to_net_cfg* cfg, void* stream, to_net** out) {
         TOPO_CUDA(cudaMalloc(&w, off * (cfg->bf16 ? sizeof(bf16) : sizeof(float))));
         n->allocs.push_back(w);
         n->wact = w;
+        if (cfg->bf16) n->wpack = nalloc<bf16>(n->allocs, off);
+        n->tc_err = nalloc<int>(n->allocs, 1);
+        TOPO_CUDA(cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->st));
         n->sums = nalloc<double>(n->allocs, 2);
         n->partials = nalloc<double>(n->allocs, 2 * 4096);
         n->counter = nalloc<unsigned>(n->allocs, 1);
@@ -696,6 +959,7 @@ to_status to_net_set_params(to_net* n, const float* theta) {
     TOPO_CHECK_LAUNCH();
     for (float* p : {n->grad, n->m, n->v}) TOPO_CUDA(cudaMemsetAsync(p, 0, n->np * sizeof(float), n->st));
     n->step = 0;
+    n->wver += 1;
     sync_out(n);
     TOPO_NET_END
 }
@@ -792,6 +1056,7 @@ to_status to_net_adam(to_net* n, double lr, double beta1, double beta2, double e
         return api_fail(TO_EINVAL, "bad Adam arguments");
     TOPO_NET_BEGIN
     n->step += 1;
+    n->wver += 1;
     const double lr_t = lr * std::sqrt(1.0 - std::pow(beta2, (double)n->step)) / (1.0 - std::pow(beta1, (double)n->step));
     if (n->cfg.bf16)
         kn_adam<bf16><<<nb(n->np), 256, 0, n->st>>>(n->theta, (bf16*)n->wact, n->grad, n->m, n->v, n->np, (float)lr_t,
