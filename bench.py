@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--mg-nu", type=int, default=1, help="GMG smoothing sweeps per level")
     ap.add_argument("--inner-rtol", type=float, default=1e-3, help="mixed path: inner FP32 solve tolerance")
+    ap.add_argument("--oc-method", default="bisection", choices=["bisection", "primal_dual"],
+                    help="OC multiplier search: the paper's bisection or the primal-dual iteration of its Appendix A")
     ap.add_argument("--mg-coarse-every", type=int, default=1,
                     help="rebuild the coarsest multigrid inverse every k-th design iteration")
     ap.add_argument("--no-learned", action="store_true",
@@ -161,6 +163,7 @@ def _make_design(args, w, precision, precond, ku_impl, stream):
                        cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
                        ku_impl=ku_impl, loop_mode=args.loop_mode, mg_nu=args.mg_nu,
                        inner_rtol=args.inner_rtol, mg_coarse_every=args.mg_coarse_every,
+                       oc_method=0 if args.oc_method == "bisection" else 1,
                        penal_cnt=(1, 3.0, 25, 0.25),
                        beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
@@ -382,6 +385,7 @@ def run_ours(args):
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
                    "mg_nu": args.mg_nu, "inner_rtol": args.inner_rtol, "mg_coarse_every": args.mg_coarse_every,
+                   "oc_method": args.oc_method,
                    "learned_warm_start": learned_info,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

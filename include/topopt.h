@@ -51,6 +51,7 @@ typedef enum to_status {
 enum { TO_FP64 = 0, TO_MIXED = 1 };                        /* to_params.precision */
 enum { TO_PC_JACOBI = 0, TO_PC_GMG = 1 };                  /* to_params.precond */
 enum { TO_CNT_ADD = 0, TO_CNT_MUL = 1 };                   /* to_continuation.kind */
+enum { TO_OC_BISECTION = 0, TO_OC_PRIMAL_DUAL = 1 };      /* to_params.oc_method */
 
 /* Continuation parCont = {istart, maxPar, isteps, deltaPar} (Sec. 3): after the
  * OC update of iteration `loop` (1-based), if loop >= istart, par < maxpar and
@@ -104,6 +105,11 @@ typedef struct to_params {
     int32_t mg_coarse_every;/* GMG: rebuild the coarsest dense inverse at every k-th set-up (1: every
                                set-up); an older inverse keeps the V-cycle symmetric positive
                                definite, so only the iteration count can change */
+    int32_t oc_method;      /* OC multiplier search: TO_OC_BISECTION (Sec. 3, Eq. 17 bracket, oc_tol,
+                               oc_maxit) or TO_OC_PRIMAL_DUAL (Appendix A: closed-form dual map
+                               iterated from lambda# until two iterates of sqrt(lambda) differ by
+                               at most 1e-10; oc_maxit caps it). Both solve mean(x_new) = volfrac. */
+    int32_t _pad3;
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

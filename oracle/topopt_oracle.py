@@ -575,6 +575,46 @@ def oc_update(x, dc, dV0, active, move, volfrac, tol=1e-4, maxit=200):
     return xn, lmid, steps
 
 
+def oc_update_primal_dual(x, dc, dV0, active, move, volfrac, tol=1e-10, maxit=200):
+    """Explicit primal-dual form of the same OC step (Appendix A: the primal map
+    puts each active element at its move/box limit or at ocP / lm, the dual map
+    solves the volume equation for lm = sqrt(lambda) in closed form over the
+    resulting sets), started from the estimate lambda# of Eq. (17) and iterated
+    until two iterates of lm differ by at most tol (reading R21: elements at a
+    limit belong to that limit's set; passive elements keep their densities and
+    their volume). Returns (x_new, lm, iterations)."""
+    x = np.array(x, float)
+    act = np.asarray(active, bool)
+    xT = x[act]
+    up = np.minimum(xT + move, 1.0)
+    lo = np.maximum(xT - move, 0.0)
+    ocP = xT * np.sqrt(np.maximum(0.0, -dc[act] / dV0[act]))
+    n = x.size
+    fixed_volume = float(np.sum(x[~act]))
+    lm = np.mean(ocP) / volfrac
+    if not lm > 0.0:
+        return x, 0.0, 0
+    it = 0
+    while it < maxit:
+        t = ocP / lm
+        at_up = t >= up
+        at_lo = (t <= lo) & ~at_up
+        mid = ~(at_up | at_lo)
+        num = float(np.sum(ocP[mid]))
+        den = volfrac * n - float(np.sum(up[at_up])) - float(np.sum(lo[at_lo])) - fixed_volume
+        it += 1
+        if not (num > 0.0 and den > 0.0):
+            break
+        lm_new = num / den
+        converged = abs(lm_new - lm) <= tol
+        lm = lm_new
+        if converged:
+            break
+    xn = x.copy()
+    xn[act] = np.minimum(np.maximum(ocP / lm, lo), up)
+    return xn, lm, it
+
+
 def continuation(par, cnt, loop, kind="add"):
     """Continuation of Sec. 3 (parCont = {istart, maxPar, isteps, deltaPar});
     kind "add" (paper) or "mul" (doubling, clamped to maxPar) (reading R9)."""
@@ -611,6 +651,7 @@ class Params:
     beta_kind: str = "add"
     newton_tol: float = 1e-6
     oc_tol: float = 1e-4
+    oc_method: str = "bisection"  # or "primal_dual" (Appendix A)
     solver: str = "direct"
     cg_rtol: float = 1e-10
 
@@ -683,7 +724,10 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
     dc = filter_backward(g, dc, p.rmin, p.ftBC, dp)
     dV0 = filter_backward(g, dV, p.rmin, p.ftBC, dp)
     # RL.4 OC and continuation
-    s.x, lm, n_bis = oc_update(s.x, dc, dV0, act, p.move, p.volfrac, p.oc_tol)
+    if p.oc_method == "primal_dual":
+        s.x, lm, n_bis = oc_update_primal_dual(s.x, dc, dV0, act, p.move, p.volfrac)
+    else:
+        s.x, lm, n_bis = oc_update(s.x, dc, dV0, act, p.move, p.volfrac, p.oc_tol)
     s.penal = continuation(s.penal, p.penal_cnt, s.loop, p.penal_kind)
     s.beta = continuation(s.beta, p.beta_cnt, s.loop, p.beta_kind)
     info = dict(loop=s.loop, c=c, V=float(np.mean(xphys)), ch=ch, penal=s.penal,

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "TO_OK", 1: "TO_EINVAL", 2: "TO_ENOMEM", 3: "TO_ECUDA", 4: "T
 TO_FP64, TO_MIXED = 0, 1
 TO_PC_JACOBI, TO_PC_GMG = 0, 1
 TO_CNT_ADD, TO_CNT_MUL = 0, 1
+TO_OC_BISECTION, TO_OC_PRIMAL_DUAL = 0, 1
 
 
 class Continuation(C.Structure):
@@ -37,7 +38,8 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("precond", C.c_int32), ("mg_levels", C.c_int32),
                 ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
-                ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32)]
+                ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
+                ("_pad3", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -92,11 +92,12 @@ struct OcOut {
     int steps;
     int status;
 };
-// Cooperative OC update with 15 bisection candidates per pass.
+// Cooperative OC update: bisection with 15 candidates per pass (TO_OC_BISECTION)
+// or the explicit primal-dual iteration of Appendix A (TO_OC_PRIMAL_DUAL).
 void launch_oc(long long n, double* x, const double* dc, const double* dV0, const int8_t* passive,
                long long nact, double move, double volfrac, double tol, int maxit, long long deadline,
                double* ocp, double* partials, GridBarrier* bar, OcOut* out, int nblocks,
-               cudaStream_t st);
+               cudaStream_t st, int method = TO_OC_BISECTION);
 int oc_max_blocks();
 
 // Deterministic dot products / norms: out[0] = sum a*b (b == nullptr: sum a*a).

@@ -284,22 +284,99 @@ __global__ void __launch_bounds__(ONT) k_oc(long long n, double* __restrict__ x,
     }
 }
 
+// Explicit primal-dual OC (Appendix A): with the move/box limits lo, up and
+// ocP as above, lm = sqrt(lambda) is iterated in closed form,
+//   lm <- sum_M ocP / (n f - sum_U up - sum_L lo - passive volume),
+// where U = {ocP / lm >= up}, L = {ocP / lm <= lo} \ U and M the rest (the
+// primal map puts U at up, L at lo, M at ocP / lm), starting from lambda# and
+// stopping when two iterates differ by at most tol (reading R21). Three grid
+// sums per iteration; the final design is min(max(ocP / lm, lo), up).
+__global__ void __launch_bounds__(ONT) k_oc_pd(long long n, double* __restrict__ x, const double* __restrict__ dc,
+                                               const double* __restrict__ dV0, const int8_t* __restrict__ passive,
+                                               long long nact, double move, double volfrac, double tol,
+                                               int maxit, long long deadline, double* __restrict__ ocp,
+                                               double* partials, GridBarrier* bar, OcOut* out) {
+    const long long stride = (long long)gridDim.x * ONT;
+    const long long i0 = (long long)blockIdx.x * ONT + threadIdx.x;
+    int parity = 0;
+    double s2[2] = {0.0, 0.0}, t2[2];
+    for (long long i = i0; i < n; i += stride) {
+        const bool act = !passive || passive[i] == 0;
+        if (act) {
+            const double o = x[i] * sqrt(fmax(0.0, -dc[i] / dV0[i]));
+            ocp[i] = o;
+            s2[0] += o;
+        } else {
+            s2[1] += x[i];
+        }
+    }
+    if (!grid_totals<ONT, 2>(s2, partials, parity, bar, deadline, t2)) return;
+    parity ^= 1;
+    const double fixed_volume = t2[1];
+    double lm = (t2[0] / (double)nact) / volfrac;
+    int steps = 0, status = 0;
+    if (lm > 0.0) {
+        bool converged = false;
+        while (steps < maxit) {
+            double v[3] = {0.0, 0.0, 0.0}, tot[3];  // sum_U up, sum_L lo, sum_M ocP
+            for (long long i = i0; i < n; i += stride) {
+                if (passive && passive[i] != 0) continue;
+                const double xi = x[i], o = ocp[i];
+                const double up = fmin(xi + move, 1.0), lo = fmax(xi - move, 0.0);
+                const double t = o / lm;
+                if (t >= up)
+                    v[0] += up;
+                else if (t <= lo)
+                    v[1] += lo;
+                else
+                    v[2] += o;
+            }
+            if (!grid_totals<ONT, 3>(v, partials, parity, bar, deadline, tot)) return;
+            parity ^= 1;
+            ++steps;
+            const double num = tot[2], den = volfrac * (double)n - tot[0] - tot[1] - fixed_volume;
+            if (!(num > 0.0 && den > 0.0)) break;
+            const double lm_new = num / den;
+            converged = fabs(lm_new - lm) <= tol;
+            lm = lm_new;
+            if (converged) break;
+        }
+        if (!converged) status = (int)TO_ENOTCONV;
+        for (long long i = i0; i < n; i += stride) {
+            if (passive && passive[i] != 0) continue;
+            const double xi = x[i];
+            x[i] = fmin(fmax(ocp[i] / lm, fmax(xi - move, 0.0)), fmin(xi + move, 1.0));
+        }
+    } else {
+        lm = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out->lm = lm;
+        out->steps = steps;
+        out->status = status;
+    }
+}
+
 int oc_max_blocks() {
     int dev = 0, nsm = 0, per = 0;
     TOPO_CUDA(cudaGetDevice(&dev));
     TOPO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int per_pd = 0;
     TOPO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oc, ONT, 0));
+    TOPO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_pd, k_oc_pd, ONT, 0));
+    per = std::min(per, per_pd);
     return nsm * (per < 2 ? per : 2);
 }
 
 void launch_oc(long long n, double* x, const double* dc, const double* dV0, const int8_t* passive,
                long long nact, double move, double volfrac, double tol, int maxit, long long deadline,
                double* ocp, double* partials, GridBarrier* bar, OcOut* out, int nblocks,
-               cudaStream_t st) {
+               cudaStream_t st, int method) {
     TOPO_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
     void* args[] = {&n, &x, &dc, &dV0, &passive, &nact, &move, &volfrac, &tol, &maxit, &deadline,
                     &ocp, &partials, &bar, &out};
-    TOPO_CUDA(cudaLaunchCooperativeKernel((void*)k_oc, dim3(nblocks), dim3(ONT), args, 0, st));
+    TOPO_CUDA(cudaLaunchCooperativeKernel((void*)(method == TO_OC_PRIMAL_DUAL ? k_oc_pd : k_oc), dim3(nblocks),
+                                          dim3(ONT), args, 0, st));
     count_launches(1);
 }
 

@@ -45,6 +45,36 @@ def bench_ku(a):
                       "us_per_launch": round(us, 3), **{k: round(v, 3) for k, v in rate.items()}}))
 
 
+def bench_oc(a):
+    """OC update (to_oc_update) with the bisection (paper tolerance 1e-4) and the
+    explicit primal-dual iteration, on a seeded SIMP-like state of the grid; wall
+    time per call (each call reads lambda back, so it includes one synchronisation)."""
+    from . import TO_OC_BISECTION, TO_OC_PRIMAL_DUAL
+    from .topopt import Grid
+    nelx, nely, nelz = (int(v) for v in a.grid.split("x"))
+    dim = 3 if nelz else 2
+    F, fixed = I.cantilever_3d(nelx, nely, nelz) if dim == 3 else I.mbb_half_beam(nelx, nely)
+    out = {"grid": a.grid}
+    for name, m in (("bisection", TO_OC_BISECTION), ("primal_dual", TO_OC_PRIMAL_DUAL)):
+        p = default_params(dim, nelx, nely, nelz, volfrac=0.3, move=0.2, oc_method=m)
+        g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+        r = np.random.default_rng(1)
+        x0 = torch.from_numpy(np.clip(0.3 + 0.2 * r.standard_normal(g.nel), 0, 1)).cuda()
+        dc = torch.from_numpy(-np.abs(r.standard_normal(g.nel)) * 10 ** r.uniform(-4, 1, g.nel)).cuda()
+        dV0 = torch.full((g.nel,), 1.0 / (g.nel * 0.3), dtype=torch.float64, device="cuda")
+        x = x0.clone()
+        g.oc_update(x, dc, dV0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            x.copy_(x0)
+            lm = g.oc_update(x, dc, dV0)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_call": round((time.perf_counter() - t0) / a.reps * 1e3, 3), "lm": lm}
+        g.close()
+    print(json.dumps(out))
+
+
 def bench_batch(a):
     """Under torchrun each rank advances its share of the instances (balanced by
     element count, no collective in the data path); rank 0 prints the whole-job
@@ -115,7 +145,7 @@ def bench_net(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net"])
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"])
@@ -127,7 +157,7 @@ def main():
     ap.add_argument("--batch", type=int, default=1)
     a = ap.parse_args()
     B.build()
-    {"ku": bench_ku, "batch": bench_batch, "net": bench_net}[a.what](a)
+    {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc}[a.what](a)
 
 
 if __name__ == "__main__":

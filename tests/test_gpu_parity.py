@@ -192,7 +192,8 @@ def _run_parity(shape, n_iter, **kw):
                          beta_cnt=(p.beta_cnt.istart, p.beta_cnt.maxpar, p.beta_cnt.isteps,
                                    p.beta_cnt.delta),
                          penal_kind="add" if p.penal_cnt.kind == 0 else "mul",
-                         beta_kind="add" if p.beta_cnt.kind == 0 else "mul")
+                         beta_kind="add" if p.beta_cnt.kind == 0 else "mul",
+                         oc_method="primal_dual" if p.oc_method == 1 else "bisection")
     s = O.initial_state(op)
     Ke = O.element_stiffness(3 if shape[2] else 2)
     d = Design(g, to_cuda(I.initial_design(g.nel, p.volfrac)))
@@ -208,6 +209,50 @@ def _run_parity(shape, n_iter, **kw):
         assert abs(got["eta"] - ref["eta"]) <= 1e-9
         assert got["penal"] == ref["penal"] and got["beta"] == ref["beta"]
     return worst
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (24, 12, 12), (200, 100, 0)])
+@pytest.mark.parametrize("with_passive", [False, True])
+def test_oc_update_primal_dual(shape, with_passive):
+    """Appendix A's explicit primal-dual OC against the oracle's, and against the
+    GPU bisection run to 1e-15 (the same volume equation)."""
+    from paper_2005_05436_gb300 import TO_OC_PRIMAL_DUAL
+    n = int(np.prod([v for v in shape if v]))
+    rng = np.random.default_rng(12)
+    passive = None
+    act = np.ones(n, bool)
+    if with_passive:
+        passive = np.zeros(n, np.int8)
+        idx = rng.choice(n, n // 20, replace=False)
+        passive[idx[: n // 40]] = 1
+        passive[idx[n // 40:]] = -1
+        act = passive == 0
+    x = np.clip(0.4 + 0.3 * rng.standard_normal(n), 0.0, 1.0)
+    if with_passive:
+        x[passive == 1], x[passive == -1] = 1.0, 0.0
+    dc = -np.abs(rng.standard_normal(n)) * 10 ** rng.uniform(-6, 2, n)
+    dV0 = np.full(n, 1.0 / (n * 0.4)) * (1 + 0.1 * rng.random(n))
+    xr, lm_ref, it = O.oc_update_primal_dual(x, dc, dV0, act, 0.2, 0.4)
+    assert it <= 50
+    g, _, _ = make_grid(shape, volfrac=0.4, move=0.2, oc_method=TO_OC_PRIMAL_DUAL, passive=passive)
+    xt = to_cuda(x)
+    lm = g.oc_update(xt, to_cuda(dc), to_cuda(dV0))
+    assert abs(lm - lm_ref) <= 1e-12 * lm_ref, (lm, lm_ref)
+    assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-12
+    gb, _, _ = make_grid(shape, volfrac=0.4, move=0.2, oc_tol=1e-15, passive=passive)
+    xb = to_cuda(x)
+    lmb = gb.oc_update(xb, to_cuda(dc), to_cuda(dV0))
+    assert abs(lm - lmb) <= 1e-9 * lmb
+    assert np.abs(xt.cpu().numpy() - xb.cpu().numpy()).max() <= 1e-9
+
+
+@pytest.mark.parametrize("ft", [1, 3])
+def test_design_iterations_primal_dual_parity(ft):
+    from paper_2005_05436_gb300 import TO_OC_PRIMAL_DUAL
+    _run_parity((60, 20, 0), 12, volfrac=0.5, penal=3.0, rmin=2.4, beta=2.0, ft=ft, newton_tol=1e-14,
+                oc_method=TO_OC_PRIMAL_DUAL, cg_rtol=1e-12, cg_maxit=200000)
+    _run_parity((12, 6, 6), 8, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0, ft=ft, newton_tol=1e-14,
+                oc_method=TO_OC_PRIMAL_DUAL, cg_rtol=1e-12, cg_maxit=200000)
 
 
 def test_design_iterations_mbb_60x20_parity():

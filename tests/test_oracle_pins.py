@@ -473,6 +473,47 @@ def test_oc_volume_limits_and_lambda_bracket():
     assert abs(np.mean(ocP / lam_sharp) - 0.5) < 1e-15
 
 
+@pytest.mark.parametrize("seed,with_passive", [(0, False), (1, False), (2, True), (3, True)])
+def test_oc_primal_dual_equals_bisection(seed, with_passive):
+    """The explicit primal-dual OC (Appendix A) solves the volume equation the
+    bisection solves: same lm and design as a bisection run to 1e-15, the volume
+    met exactly, the move and box limits kept, and few iterations."""
+    r = np.random.default_rng(seed)
+    n = 500
+    x = np.clip(r.uniform(0.0, 1.0, n), 0.0, 1.0)
+    dc = -np.exp(r.normal(0.0, 2.0, n))          # compliance sensitivities are negative
+    dV0 = np.full(n, 1.0 / (n * 0.4)) * r.uniform(0.5, 1.5, n)
+    act = np.ones(n, bool)
+    if with_passive:
+        act[r.choice(n, 40, replace=False)] = False
+    xb, lmb, _ = O.oc_update(x, dc, dV0, act, 0.2, 0.4, tol=1e-15, maxit=400)
+    xp, lmp, it = O.oc_update_primal_dual(x, dc, dV0, act, 0.2, 0.4)
+    assert it <= 30
+    assert abs(lmp - lmb) <= 1e-9 * lmb
+    assert np.abs(xp - xb).max() <= 1e-9
+    assert abs(np.mean(xp) - 0.4) <= 1e-12
+    assert np.all(xp[act] >= np.maximum(x[act] - 0.2, 0.0) - 1e-15)
+    assert np.all(xp[act] <= np.minimum(x[act] + 0.2, 1.0) + 1e-15)
+    np.testing.assert_array_equal(xp[~act], x[~act])
+
+
+def test_oc_primal_dual_special_cases():
+    """No sensitivity: the design stays. Every element free of its limits: one
+    closed-form step gives x_e = ocP_e / lm with mean exactly the volume fraction."""
+    n = 64
+    x = np.full(n, 0.5)
+    xn, lm, it = O.oc_update_primal_dual(x, np.zeros(n), np.full(n, 1.0), np.ones(n, bool), 0.2, 0.5)
+    assert lm == 0.0 and it == 0
+    np.testing.assert_array_equal(xn, x)
+    r = np.random.default_rng(9)
+    dc = -r.uniform(0.9, 1.1, n)   # sensitivities close to each other: no element reaches a limit
+    xn, lm, it = O.oc_update_primal_dual(x, dc, np.full(n, 1.0), np.ones(n, bool), 0.2, 0.5)
+    ocP = x * np.sqrt(-dc)
+    np.testing.assert_allclose(xn, ocP / lm, rtol=1e-15)
+    assert abs(np.mean(xn) - 0.5) <= 1e-15
+    assert abs(lm - np.sum(ocP) / (0.5 * n)) <= 1e-15 * lm
+
+
 def test_oc_paper_mode_step_count():
     """Sec. 3.3: with the lambda# bracket ~14 bisection steps at tol 1e-4."""
     n = 1200
