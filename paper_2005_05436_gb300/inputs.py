@@ -114,9 +114,11 @@ def cantilever_family(nelx, nely, nelz, seed):
     return F, fixed, float(rng.uniform(0.1, 0.3))
 
 
-def frame_reinforcement(nelx, nely):
+def frame_reinforcement(nelx, nely, sign=-1.0):
     """Frame-reinforcement example of Sec. 3.5 (passive frame and opening).
 
+    sign = -1: the height-proportional horizontal load points left (the paper's
+    listing), +1: right (the second design of its figure).
     Returns (F, fixed, passive) with passive[e] = 1 (solid), -1 (void), 0.
     nelx and nely must be multiples of 50.
     """
@@ -128,7 +130,7 @@ def frame_reinforcement(nelx, nely):
         F[2 * node_id(0, ix, nely=nely) + 1] += -2.0 / (nelx + 1)
     # horizontal height-proportional load on the right column of nodes
     for iy in range(nely + 1):
-        F[2 * node_id(iy, nelx, nely=nely) + 0] += -iy / float(nely) ** 2
+        F[2 * node_id(iy, nelx, nely=nely) + 0] += sign * iy / float(nely) ** 2
     fixed[[0, 1, ndof - 1]] = 1
     passive = np.zeros(nel, np.int8)
     E = np.arange(nel).reshape(nelx, nely)  # E[ix, iy] = element number

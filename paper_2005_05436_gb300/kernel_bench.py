@@ -75,6 +75,40 @@ def bench_oc(a):
     print(json.dumps(out))
 
 
+def bench_frame(a):
+    """The frame-reinforcement workload of Sec. 3.5 at the paper's size
+    (nelx = nely = 900, volfrac 0.2, penal 3, rmin 8, ft 3, eta 0.5, beta 2, no
+    continuation): design iterations through to_step, timed with CUDA events
+    after two untimed ones; both load orientations."""
+    from . import TO_FP64, TO_MIXED, TO_PC_GMG
+    from .topopt import Design, Grid
+    nelx, nely = (int(v) for v in a.grid.split("x")[:2])
+    prec = TO_FP64 if a.precision == "fp64" else TO_MIXED
+    out = {"grid": f"{nelx}x{nely}", "precision": a.precision, "paper_s_per_iteration": 10.8}
+    for sign in (-1.0, 1.0):
+        F, fixed, pas = I.frame_reinforcement(nelx, nely, sign)
+        p = default_params(2, nelx, nely, 0, volfrac=0.2, penal=3.0, rmin=8.0, ft=3, eta=0.5, beta=2.0,
+                           precision=prec, precond=TO_PC_GMG, mg_nu=1, cg_rtol=1e-8, cg_maxit=50000,
+                           penal_cnt=(1, 3.0, 1000, 0.0), beta_cnt=(1, 2.0, 1000, 0.0))
+        g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(),
+                 torch.from_numpy(pas).cuda())
+        d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.2, pas)).cuda())
+        for _ in range(2):
+            d.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        infos = [d.step() for _ in range(a.steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        out["left" if sign < 0 else "right"] = {
+            "ms_per_iteration": round(ms, 2), "n_cg": [i["n_cg"] for i in infos],
+            "c": infos[-1]["c"], "V": infos[-1]["V"], "speedup_vs_paper": round(10.8e3 / ms, 1)}
+        g.close()
+    print(json.dumps(out))
+
+
 def bench_batch(a):
     """Under torchrun each rank advances its share of the instances (balanced by
     element count, no collective in the data path); rank 0 prints the whole-job
@@ -145,7 +179,7 @@ def bench_net(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc"])
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"])
@@ -157,7 +191,7 @@ def main():
     ap.add_argument("--batch", type=int, default=1)
     a = ap.parse_args()
     B.build()
-    {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc}[a.what](a)
+    {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc, "frame": bench_frame}[a.what](a)
 
 
 if __name__ == "__main__":

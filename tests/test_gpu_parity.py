@@ -272,6 +272,34 @@ def test_design_iterations_with_continuation_and_dirichlet_filter():
                 oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=200000)
 
 
+@pytest.mark.parametrize("sign", [-1.0, 1.0])
+def test_frame_reinforcement_parity(sign):
+    """The frame-reinforcement workload of Sec. 3.5 (passive solid frame and void
+    opening, distributed vertical and height-proportional horizontal loads, ft = 3,
+    no continuation), scaled to 100 x 100 with rmin 2: design iterations against
+    the oracle, passive densities kept exactly."""
+    from paper_2005_05436_gb300.topopt import Design
+    from paper_2005_05436_gb300 import TO_PC_GMG
+    F, fixed, pas = I.frame_reinforcement(100, 100, sign)
+    # the void opening (E = Emin) puts the FP64 PCG floor near 1e-11: multigrid PCG to 1e-10
+    g, _, _ = make_grid((100, 100, 0), F=F, fixed=fixed, passive=pas, volfrac=0.2, penal=3.0, rmin=2.0,
+                        ft=3, eta=0.5, beta=2.0, newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-10,
+                        cg_maxit=200000, precond=TO_PC_GMG, penal_cnt=(1, 3.0, 1000, 0.0),
+                        beta_cnt=(1, 2.0, 1000, 0.0))
+    op = O.Params.parity(nelx=100, nely=100, volfrac=0.2, penal=3.0, rmin=2.0, ft=3, eta=0.5, beta=2.0,
+                         penal_cnt=(1, 3.0, 1000, 0.0), beta_cnt=(1, 2.0, 1000, 0.0))
+    s = O.initial_state(op, pas)
+    Ke = O.element_stiffness(2)
+    d = Design(g, to_cuda(s.x.copy()))
+    for k in range(6):
+        ref = O.design_step(op, s, F, fixed, pas, Ke)
+        got = d.step()
+        assert rel(d.xPhys.cpu().numpy(), s.xphys) <= 1e-8, (k, rel(d.xPhys.cpu().numpy(), s.xphys))
+        assert abs(got["c"] - ref["c"]) <= 1e-8 * abs(ref["c"]), (k, got["c"], ref["c"])
+    x = d.x.cpu().numpy()
+    assert np.all(x[pas == 1] == 1.0) and np.all(x[pas == -1] == 0.0)
+
+
 def test_passive_elements_step():
     """Passive solid/void sets (frame reinforcement, scaled down)."""
     from paper_2005_05436_gb300.topopt import Design
