@@ -51,7 +51,7 @@ typedef enum to_status {
 enum { TO_FP64 = 0, TO_MIXED = 1 };                        /* to_params.precision */
 enum { TO_PC_JACOBI = 0, TO_PC_GMG = 1 };                  /* to_params.precond */
 enum { TO_CNT_ADD = 0, TO_CNT_MUL = 1 };                   /* to_continuation.kind */
-enum { TO_OC_BISECTION = 0, TO_OC_PRIMAL_DUAL = 1 };      /* to_params.oc_method */
+enum { TO_OC_BISECTION = 0, TO_OC_PRIMAL_DUAL = 1, TO_OC_PHYSICAL_VOLUME = 2 };  /* to_params.oc_method */
 
 /* Continuation parCont = {istart, maxPar, isteps, deltaPar} (Sec. 3): after the
  * OC update of iteration `loop` (1-based), if loop >= istart, par < maxpar and
@@ -108,7 +108,12 @@ typedef struct to_params {
     int32_t oc_method;      /* OC multiplier search: TO_OC_BISECTION (Sec. 3, Eq. 17 bracket, oc_tol,
                                oc_maxit) or TO_OC_PRIMAL_DUAL (Appendix A: closed-form dual map
                                iterated from lambda# until two iterates of sqrt(lambda) differ by
-                               at most 1e-10; oc_maxit caps it). Both solve mean(x_new) = volfrac. */
+                               at most 1e-10; oc_maxit caps it), both solving mean(x_new) = volfrac;
+                               or TO_OC_PHYSICAL_VOLUME (Sec. 3.2, the general variant for a fixed
+                               threshold: each bisection candidate is filtered, its passive
+                               elements set to 1 / 0 and, for ft > 1, projected with the current
+                               eta and beta, and the bisection solves mean of that field =
+                               volfrac; oc_tol, oc_maxit). */
     int32_t _pad3;
 } to_params;
 

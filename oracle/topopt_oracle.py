@@ -615,6 +615,57 @@ def oc_update_primal_dual(x, dc, dV0, active, move, volfrac, tol=1e-10, maxit=20
     return xn, lm, it
 
 
+def oc_update_filtered(g, x, dc, dV0, active, move, volfrac, rmin, bc, ft, eta, beta, passive=None,
+                       tol=1e-4, maxit=200):
+    """OC step whose volume test is taken on the physical field of each candidate
+    (Sec. 3.2, the general variant for a fixed threshold): every bisection
+    candidate x(lm) of Eq. (14) is filtered (Eq. 2), its passive elements are set
+    to 1 (solid) and 0 (void), and it is projected (Eq. 1, threshold eta fixed)
+    when ft > 1; lm moves up while the mean of that field exceeds volfrac. The
+    bracket starts from lambda# (Eq. 17) and grows while its upper end still gives
+    too much volume (reading R6). Returns (x_new, lm, bisection steps)."""
+    x = np.array(x, float)
+    act = np.asarray(active, bool)
+    pas = np.zeros(x.size, np.int8) if passive is None else np.asarray(passive, np.int8)
+    xT = x[act]
+    xU, xL = xT + move, xT - move
+    ocP = xT * np.sqrt(np.maximum(0.0, -dc[act] / dV0[act]))
+    l1, l2 = 0.0, np.mean(ocP) / volfrac
+
+    def update(lm):
+        xn = x.copy()
+        xn[act] = np.maximum(np.maximum(np.minimum(np.minimum(ocP / lm, xU), 1.0), xL), 0.0)
+        return xn
+
+    def physical_volume(xn):
+        xf = filter_forward(g, xn, rmin, bc)
+        xf[pas == 1] = 1.0
+        xf[pas == -1] = 0.0
+        if ft > 1:
+            xf = prj(xf, eta, beta)
+        return float(np.mean(xf))
+
+    if not l2 > 0.0:
+        return x, 0.0, 0
+    grow = 0
+    xn = update(l2)
+    while physical_volume(xn) > volfrac and grow < 60:
+        l1, l2 = l2, 2.0 * l2
+        xn = update(l2)
+        grow += 1
+    steps = 0
+    lmid = l2
+    while (l2 - l1) / (l1 + l2) > tol and steps < maxit:
+        lmid = 0.5 * (l1 + l2)
+        xn = update(lmid)
+        if physical_volume(xn) > volfrac:
+            l1 = lmid
+        else:
+            l2 = lmid
+        steps += 1
+    return xn, lmid, steps
+
+
 def continuation(par, cnt, loop, kind="add"):
     """Continuation of Sec. 3 (parCont = {istart, maxPar, isteps, deltaPar});
     kind "add" (paper) or "mul" (doubling, clamped to maxPar) (reading R9)."""
@@ -651,7 +702,7 @@ class Params:
     beta_kind: str = "add"
     newton_tol: float = 1e-6
     oc_tol: float = 1e-4
-    oc_method: str = "bisection"  # or "primal_dual" (Appendix A)
+    oc_method: str = "bisection"  # or "primal_dual" (Appendix A), "filtered" (Sec. 3.2, general variant)
     solver: str = "direct"
     cg_rtol: float = 1e-10
 
@@ -726,6 +777,9 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
     # RL.4 OC and continuation
     if p.oc_method == "primal_dual":
         s.x, lm, n_bis = oc_update_primal_dual(s.x, dc, dV0, act, p.move, p.volfrac)
+    elif p.oc_method == "filtered":
+        s.x, lm, n_bis = oc_update_filtered(g, s.x, dc, dV0, act, p.move, p.volfrac, p.rmin, p.ftBC, p.ft,
+                                            s.eta, s.beta, pas, p.oc_tol)
     else:
         s.x, lm, n_bis = oc_update(s.x, dc, dV0, act, p.move, p.volfrac, p.oc_tol)
     s.penal = continuation(s.penal, p.penal_cnt, s.loop, p.penal_kind)

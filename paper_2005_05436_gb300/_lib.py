@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "TO_OK", 1: "TO_EINVAL", 2: "TO_ENOMEM", 3: "TO_ECUDA", 4: "T
 TO_FP64, TO_MIXED = 0, 1
 TO_PC_JACOBI, TO_PC_GMG = 0, 1
 TO_CNT_ADD, TO_CNT_MUL = 0, 1
-TO_OC_BISECTION, TO_OC_PRIMAL_DUAL = 0, 1
+TO_OC_BISECTION, TO_OC_PRIMAL_DUAL, TO_OC_PHYSICAL_VOLUME = 0, 1, 2
 
 
 class Continuation(C.Structure):

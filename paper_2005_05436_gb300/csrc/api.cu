@@ -149,8 +149,9 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
     TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 3, "ku_impl must be 0, 1, 2 or 3");
-    TOPO_REQUIRE(p->oc_method == TO_OC_BISECTION || p->oc_method == TO_OC_PRIMAL_DUAL,
-                 "oc_method must be TO_OC_BISECTION or TO_OC_PRIMAL_DUAL");
+    TOPO_REQUIRE(p->oc_method == TO_OC_BISECTION || p->oc_method == TO_OC_PRIMAL_DUAL ||
+                     p->oc_method == TO_OC_PHYSICAL_VOLUME,
+                 "oc_method must be TO_OC_BISECTION, TO_OC_PRIMAL_DUAL or TO_OC_PHYSICAL_VOLUME");
     TOPO_REQUIRE(!(p->ku_impl == 2 && p->dim != 3), "the tensor-core operator is 3D only");
     const long long nnodes = (long long)(p->nelx + 1) * (p->nely + 1) * (p->dim == 3 ? p->nelz + 1 : 1);
     TOPO_REQUIRE(nnodes * p->dim < (1LL << 31) - 1, "grid too large for 32-bit DOF indices");
@@ -467,9 +468,16 @@ to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV
     if (!g || !x || !dc || !dV0) return fail(TO_EINVAL, "NULL argument");
     TOPO_API_BEGIN
     grid_sync_in(g);
-    launch_oc(g->d.nel, x, dc, dV0, g->passive, g->nact, g->p.move, g->p.volfrac, oc_tol_of(g->p),
-              g->p.oc_maxit, g->p.deadline_cycles, g->ocp, g->partials, g->bar, &g->ds->oo,
-              g->oc_blocks, g->st, g->p.oc_method);
+    if (g->p.oc_method == TO_OC_PHYSICAL_VOLUME) {
+        TOPO_CUDA(cudaMemsetAsync(g->bar, 0, sizeof(GridBarrier), g->st));
+        launch_oc_filtered(g->d, g->taps, (char)g->p.ftBC, g->Hs, g->Hs_const, x, dc, dV0, g->passive, g->nact,
+                           g->p.move, g->p.volfrac, g->p.ft, g->eta, nullptr, g->beta, g->p.oc_tol, g->p.oc_maxit, g->ocp,
+                           g->dV, g->dc, &g->ds->ocf, &g->hs->ocf, g->partials, g->counter, &g->ds->oo, g->st);
+    } else {
+        launch_oc(g->d.nel, x, dc, dV0, g->passive, g->nact, g->p.move, g->p.volfrac, oc_tol_of(g->p),
+                  g->p.oc_maxit, g->p.deadline_cycles, g->ocp, g->partials, g->bar, &g->ds->oo,
+                  g->oc_blocks, g->st, g->p.oc_method);
+    }
     TOPO_CUDA(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, g->st));
     TOPO_CUDA(cudaMemcpyAsync(&g->hbar, g->bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, g->st));
     TOPO_CUDA(cudaStreamSynchronize(g->st));
@@ -570,8 +578,16 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     launch_filter(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st);
     TOPO_CUDA(cudaEventRecord(g->ev_t[3], st));
     // RL.4 OC update
-    launch_oc(d.nel, s->x, g->dcf, g->dV0, g->passive, g->nact, p.move, p.volfrac, oc_tol_of(p), p.oc_maxit,
-              p.deadline_cycles, g->ocp, g->partials, g->bar, &g->ds->oo, g->oc_blocks, st, p.oc_method);
+    if (p.oc_method == TO_OC_PHYSICAL_VOLUME) {
+        // the physical field of each candidate, with the step's threshold and sharpness
+        launch_oc_filtered(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, s->x, g->dcf, g->dV0, g->passive, g->nact,
+                           p.move, p.volfrac, p.ft, s->eta, p.ft == 3 ? &g->ds->po.eta : nullptr, s->beta, p.oc_tol,
+                           p.oc_maxit, g->ocp, g->dV, g->dc,
+                           &g->ds->ocf, &g->hs->ocf, g->partials, g->counter, &g->ds->oo, st);
+    } else {
+        launch_oc(d.nel, s->x, g->dcf, g->dV0, g->passive, g->nact, p.move, p.volfrac, oc_tol_of(p), p.oc_maxit,
+                  p.deadline_cycles, g->ocp, g->partials, g->bar, &g->ds->oo, g->oc_blocks, st, p.oc_method);
+    }
     TOPO_CUDA(cudaEventRecord(g->ev_t[4], st));
     TOPO_CUDA(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     TOPO_CUDA(cudaMemcpyAsync(&g->hbar, g->bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, st));

@@ -17,6 +17,7 @@ struct DevScalars {
     long long nnz;
     PcgScalars pcg;
     double res[4];     // refinement norms
+    OcfState ocf;      // OC search on the physical field
 };
 
 struct Solver;  // solver.cu

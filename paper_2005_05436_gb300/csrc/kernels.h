@@ -92,6 +92,27 @@ struct OcOut {
     int steps;
     int status;
 };
+
+// Device state of the OC search with the volume taken on the physical field of
+// each candidate (launch_oc_filtered): bracket, the candidate's lm and phase
+// (0 growing the bracket, 1 bisecting, 2 done, 3 nothing to do).
+struct OcfState {
+    double l1, l2, lmid;
+    int phase, grows, steps, status;
+};
+
+// OC update whose bisection tests mean(prj(filter(x(lm)))) > volfrac (Sec. 3.2,
+// the general variant for a fixed threshold eta; projection only when ft > 1;
+// passive elements 1 / 0 after filtering; eta from eta_dev when non-null, e.g.
+// the eta* of the same design iteration). Each step is three launches
+// (candidate, forward filter, projected volume with the bracket update in the
+// last block); the host checks the phase every four steps. xc, xf: [nEl]
+// scratch; on return x holds the last candidate and out the last lm.
+void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+                        double* x, const double* dc, const double* dV0, const int8_t* passive, long long nact,
+                        double move, double volfrac, int ft, double eta, const double* eta_dev, double beta,
+                        double tol, int maxit, double* ocp, double* xc, double* xf, OcfState* sdev,
+                        OcfState* shost, double* partials, unsigned* counter, OcOut* out, cudaStream_t st);
 // Cooperative OC update: bisection with 15 candidates per pass (TO_OC_BISECTION)
 // or the explicit primal-dual iteration of Appendix A (TO_OC_PRIMAL_DUAL).
 void launch_oc(long long n, double* x, const double* dc, const double* dV0, const int8_t* passive,

@@ -357,6 +357,115 @@ __global__ void __launch_bounds__(ONT) k_oc_pd(long long n, double* __restrict__
     }
 }
 
+// ----------------------------------------------- OC on the physical field --
+
+__global__ void __launch_bounds__(256) k_ocf_prep(long long n, const double* __restrict__ x,
+                                                  const double* __restrict__ dc, const double* __restrict__ dV0,
+                                                  const int8_t* __restrict__ passive, long long nact, double volfrac,
+                                                  double* __restrict__ ocp, OcfState* s, double* partials,
+                                                  unsigned* counter) {
+    double v[1] = {0.0}, tot[1];
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        if (passive && passive[i] != 0) continue;
+        const double o = x[i] * sqrt(fmax(0.0, -dc[i] / dV0[i]));
+        ocp[i] = o;
+        v[0] += o;
+    }
+    if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        const double l2 = (tot[0] / (double)nact) / volfrac;
+        s->l1 = 0.0;
+        s->l2 = l2;
+        s->lmid = l2;
+        s->phase = l2 > 0.0 ? 0 : 3;
+        s->grows = s->steps = s->status = 0;
+    }
+}
+
+// Candidate x(lm) of Eq. 14 at lm = l2 (growing) or the bracket midpoint.
+__global__ void k_ocf_cand(long long n, const double* __restrict__ x, const double* __restrict__ ocp,
+                           const int8_t* __restrict__ passive, double move, OcfState* s, double* __restrict__ xc) {
+    const int phase = s->phase;
+    if (phase >= 2) return;
+    const double lm = phase == 0 ? s->l2 : 0.5 * (s->l1 + s->l2);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) s->lmid = lm;
+    if (i >= n) return;
+    const double xi = x[i];
+    xc[i] = (passive && passive[i] != 0) ? xi
+                                         : fmax(fmax(fmin(fmin(ocp[i] / lm, xi + move), 1.0), xi - move), 0.0);
+}
+
+// Volume of the projected, filtered candidate; the last block moves the bracket.
+__global__ void __launch_bounds__(256) k_ocf_vol(long long n, const double* __restrict__ xf, int ft, double eta0,
+                                                 const double* eta_dev, double beta, double volfrac, double tol,
+                                                 int maxit, OcfState* s, double* partials, unsigned* counter) {
+    if (s->phase >= 2) return;  // uniform
+    const double eta = eta_dev ? *eta_dev : eta0;
+    const double tb = tanh(beta * eta), den = tb + tanh(beta * (1.0 - eta));
+    double v[1] = {0.0}, tot[1];
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        v[0] += ft > 1 ? (tb + tanh(beta * (xf[i] - eta))) / den : xf[i];
+    if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        const bool over = tot[0] / (double)n > volfrac;
+        double l1 = s->l1, l2 = s->l2;
+        if (s->phase == 0) {
+            if (over && s->grows < 60) {
+                l1 = l2;
+                l2 = 2.0 * l2;
+                s->grows += 1;
+            } else {
+                s->phase = 1;
+            }
+        } else {
+            if (over)
+                l1 = s->lmid;
+            else
+                l2 = s->lmid;
+            s->steps += 1;
+        }
+        s->l1 = l1;
+        s->l2 = l2;
+        if (s->phase == 1 && !((l2 - l1) / (l1 + l2) > tol && s->steps < maxit)) {
+            s->status = (l2 - l1) / (l1 + l2) > tol ? (int)TO_ENOTCONV : 0;
+            s->phase = 2;
+        }
+    }
+}
+
+void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+                        double* x, const double* dc, const double* dV0, const int8_t* passive, long long nact,
+                        double move, double volfrac, int ft, double eta, const double* eta_dev, double beta,
+                        double tol, int maxit, double* ocp, double* xc, double* xf, OcfState* sdev,
+                        OcfState* shost, double* partials, unsigned* counter, OcOut* out, cudaStream_t st) {
+    const long long n = d.nel;
+    const int nbr = std::min(div_up(n, 256), 1024), nbe = div_up(n, 256);
+    k_ocf_prep<<<nbr, 256, 0, st>>>(n, x, dc, dV0, passive, nact, volfrac, ocp, sdev, partials, counter);
+    TOPO_CHECK_LAUNCH();
+    const int cap = maxit + 64;  // growing (at most 60) and bisection steps
+    for (int done = 0; done < cap;) {
+        for (int k = 0; k < 4; ++k, ++done) {
+            k_ocf_cand<<<nbe, 256, 0, st>>>(n, x, ocp, passive, move, sdev, xc);
+            TOPO_CHECK_LAUNCH();
+            launch_filter(d, taps, bc, Hs, Hs_const, xc, nullptr, xf, passive, xc, st);
+            k_ocf_vol<<<nbr, 256, 0, st>>>(n, xf, ft, eta, eta_dev, beta, volfrac, tol, maxit, sdev, partials,
+                                           counter);
+            TOPO_CHECK_LAUNCH();
+        }
+        TOPO_CUDA(cudaMemcpyAsync(shost, sdev, sizeof(OcfState), cudaMemcpyDeviceToHost, st));
+        TOPO_CUDA(cudaStreamSynchronize(st));
+        if (shost->phase >= 2) break;
+    }
+    OcOut o{0.0, 0, 0};
+    if (shost->phase == 2) {
+        TOPO_CUDA(cudaMemcpyAsync(x, xc, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        o = OcOut{shost->lmid, shost->steps, shost->status};
+    } else if (shost->phase < 2) {
+        o.status = (int)TO_ENOTCONV;
+    }
+    TOPO_CUDA(cudaMemcpyAsync(out, &o, sizeof(OcOut), cudaMemcpyHostToDevice, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+}
+
 int oc_max_blocks() {
     int dev = 0, nsm = 0, per = 0;
     TOPO_CUDA(cudaGetDevice(&dev));

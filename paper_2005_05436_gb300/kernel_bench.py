@@ -46,17 +46,20 @@ def bench_ku(a):
 
 
 def bench_oc(a):
-    """OC update (to_oc_update) with the bisection (paper tolerance 1e-4) and the
-    explicit primal-dual iteration, on a seeded SIMP-like state of the grid; wall
+    """OC update (to_oc_update) with the bisection (paper tolerance 1e-4), the
+    explicit primal-dual iteration and the bisection on the physical volume
+    (filter and fixed-threshold projection per candidate, ft = 2), on a seeded
+    SIMP-like state of the grid; wall
     time per call (each call reads lambda back, so it includes one synchronisation)."""
-    from . import TO_OC_BISECTION, TO_OC_PRIMAL_DUAL
+    from . import TO_OC_BISECTION, TO_OC_PHYSICAL_VOLUME, TO_OC_PRIMAL_DUAL
     from .topopt import Grid
     nelx, nely, nelz = (int(v) for v in a.grid.split("x"))
     dim = 3 if nelz else 2
     F, fixed = I.cantilever_3d(nelx, nely, nelz) if dim == 3 else I.mbb_half_beam(nelx, nely)
     out = {"grid": a.grid}
-    for name, m in (("bisection", TO_OC_BISECTION), ("primal_dual", TO_OC_PRIMAL_DUAL)):
-        p = default_params(dim, nelx, nely, nelz, volfrac=0.3, move=0.2, oc_method=m)
+    for name, m in (("bisection", TO_OC_BISECTION), ("primal_dual", TO_OC_PRIMAL_DUAL),
+                    ("physical_volume", TO_OC_PHYSICAL_VOLUME)):
+        p = default_params(dim, nelx, nely, nelz, volfrac=0.3, move=0.2, oc_method=m, ft=2, eta=0.5, beta=2.0)
         g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
         r = np.random.default_rng(1)
         x0 = torch.from_numpy(np.clip(0.3 + 0.2 * r.standard_normal(g.nel), 0, 1)).cuda()

@@ -193,7 +193,7 @@ def _run_parity(shape, n_iter, **kw):
                                    p.beta_cnt.delta),
                          penal_kind="add" if p.penal_cnt.kind == 0 else "mul",
                          beta_kind="add" if p.beta_cnt.kind == 0 else "mul",
-                         oc_method="primal_dual" if p.oc_method == 1 else "bisection")
+                         oc_method={0: "bisection", 1: "primal_dual", 2: "filtered"}[p.oc_method])
     s = O.initial_state(op)
     Ke = O.element_stiffness(3 if shape[2] else 2)
     d = Design(g, to_cuda(I.initial_design(g.nel, p.volfrac)))
@@ -253,6 +253,49 @@ def test_design_iterations_primal_dual_parity(ft):
                 oc_method=TO_OC_PRIMAL_DUAL, cg_rtol=1e-12, cg_maxit=200000)
     _run_parity((12, 6, 6), 8, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0, ft=ft, newton_tol=1e-14,
                 oc_method=TO_OC_PRIMAL_DUAL, cg_rtol=1e-12, cg_maxit=200000)
+
+
+@pytest.mark.parametrize("shape", [(60, 20, 0), (12, 6, 6)])
+@pytest.mark.parametrize("with_passive", [False, True])
+def test_oc_update_physical_volume(shape, with_passive):
+    """The general OC variant of Sec. 3.2 (volume of the filtered, projected
+    candidate, fixed threshold) against the oracle at a 1e-15 bracket."""
+    from paper_2005_05436_gb300 import TO_OC_PHYSICAL_VOLUME
+    n = int(np.prod([v for v in shape if v]))
+    rng = np.random.default_rng(13)
+    passive = None
+    act = np.ones(n, bool)
+    if with_passive:
+        passive = np.zeros(n, np.int8)
+        idx = rng.choice(n, n // 10, replace=False)
+        passive[idx[: n // 20]] = 1
+        passive[idx[n // 20:]] = -1
+        act = passive == 0
+    x = np.clip(0.35 + 0.25 * rng.standard_normal(n), 0.0, 1.0)
+    if with_passive:
+        x[passive == 1], x[passive == -1] = 1.0, 0.0
+    dc = -np.abs(rng.standard_normal(n)) * 10 ** rng.uniform(-4, 1, n)
+    dV0 = np.full(n, 1.0 / (n * 0.35)) * (1 + 0.1 * rng.random(n))
+    og = O.Grid(*shape)
+    xr, lm_ref, steps = O.oc_update_filtered(og, x, dc, dV0, act, 0.2, 0.35, 2.0, "N", 2, 0.4, 4.0, passive,
+                                             tol=1e-15)
+    g, _, _ = make_grid(shape, volfrac=0.35, move=0.2, rmin=2.0, ft=2, oc_tol=1e-15,
+                        oc_method=TO_OC_PHYSICAL_VOLUME, passive=passive)
+    g.set_scalars(3.0, 4.0, 0.4)
+    xt = to_cuda(x)
+    lm = g.oc_update(xt, to_cuda(dc), to_cuda(dV0))
+    assert abs(lm - lm_ref) <= 1e-13 * lm_ref, (lm, lm_ref)
+    assert np.abs(xt.cpu().numpy() - xr).max() <= 1e-12
+
+
+@pytest.mark.parametrize("ft", [2, 3])
+def test_design_iterations_physical_volume_parity(ft):
+    from paper_2005_05436_gb300 import TO_OC_PHYSICAL_VOLUME
+    _run_parity((60, 20, 0), 10, volfrac=0.5, penal=3.0, rmin=2.4, beta=4.0, eta=0.4, ft=ft, newton_tol=1e-14,
+                oc_tol=1e-15, oc_method=TO_OC_PHYSICAL_VOLUME, cg_rtol=1e-12, cg_maxit=200000)
+    _run_parity((12, 6, 6), 6, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=4.0, eta=0.4, ft=ft,
+                newton_tol=1e-14, oc_tol=1e-15, oc_method=TO_OC_PHYSICAL_VOLUME, cg_rtol=1e-12,
+                cg_maxit=200000)
 
 
 def test_design_iterations_mbb_60x20_parity():
