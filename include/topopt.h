@@ -114,7 +114,12 @@ typedef struct to_params {
                                elements set to 1 / 0 and, for ft > 1, projected with the current
                                eta and beta, and the bisection solves mean of that field =
                                volfrac; oc_tol, oc_maxit). */
-    int32_t _pad3;
+    int32_t pae_q0;         /* periodic Anderson extrapolation of the OC iteration (Sec. 3.6) from
+                               loop pae_q0 on; 0: off */
+    int32_t pae_q;          /* extrapolate when (loop - pae_q0 + 1) is a multiple of pae_q (4) */
+    int32_t pae_m;          /* history columns m_r, 1..4 (4) */
+    double pae_alpha;       /* damping of the other steps, x += alpha r (0.9) */
+    double pae_zeta;        /* damping of the extrapolated step (1) */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */
@@ -165,6 +170,8 @@ typedef struct to_iter_info {
     double warm_a, warm_b;  /* its starting point: warm_a U_prev + warm_b U_net */
     double warm_err_prev;   /* energy-norm error of U_prev relative to that of U = 0: ||U_prev - U||_K^2 / ||U||_K^2 */
     double warm_err;        /* the same for the warm start actually used (<= warm_err_prev) */
+    int32_t pae;            /* Anderson extrapolation of this step: 0 off, 1 damped step, 2 extrapolated */
+    int32_t _pad2;
 } to_iter_info;
 
 /* Thread-local message of the last failing call ("" if none). */

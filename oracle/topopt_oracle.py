@@ -666,6 +666,63 @@ def oc_update_filtered(g, x, dc, dV0, active, move, volfrac, rmin, bc, ft, eta, 
     return xn, lmid, steps
 
 
+def solve_small(G, b, rel=1e-14):
+    """Gaussian elimination with partial pivoting for the m x m normal equations
+    of the extrapolation (m <= 8); None when a pivot falls below rel times the
+    largest diagonal entry (the extrapolation step is then skipped)."""
+    G = np.array(G, float)
+    b = np.array(b, float)
+    m = b.size
+    scale = max(float(np.max(np.abs(np.diag(G)))) if m else 0.0, 1e-300)
+    for k in range(m):
+        piv = k + int(np.argmax(np.abs(G[k:, k])))
+        if not abs(G[piv, k]) > rel * scale:
+            return None
+        if piv != k:
+            G[[k, piv]] = G[[piv, k]]
+            b[[k, piv]] = b[[piv, k]]
+        for i in range(k + 1, m):
+            f = G[i, k] / G[k, k]
+            G[i, k:] -= f * G[k, k:]
+            b[i] -= f * b[k]
+    y = np.zeros(m)
+    for i in range(m - 1, -1, -1):
+        y[i] = (b[i] - G[i, i + 1:] @ y[i + 1:]) / G[i, i]
+    return y
+
+
+def pae_update(h, x, r, it, m, q, alpha, zeta):
+    """Periodic Anderson extrapolation of the OC fixed-point iteration (Sec. 3.6):
+    r = U(x) - x is the OC step's residual on the active elements and it the step
+    counted from q0. The differences of x and r between consecutive steps go to
+    cyclic slots (slot (it - 1) mod m, the last m of them kept); when (it + 1) is
+    a multiple of q (reading R23) gamma minimises ||r - R gamma|| (normal
+    equations) and x + zeta r - (X + zeta R) gamma is taken, otherwise the damped
+    step x + alpha r; the result is clipped to [0, 1]. h holds the slots and the
+    previous x and r. Returns (x_new, kind) with kind 1 damped, 2 extrapolated."""
+    if it == 0 or "X" not in h:
+        h["X"] = np.zeros((m, x.size))
+        h["R"] = np.zeros((m, x.size))
+        h["filled"] = 0
+    if it >= 1:
+        k = (it - 1) % m
+        h["X"][k] = x - h["xold"]
+        h["R"][k] = r - h["rold"]
+        h["filled"] = min(h["filled"] + 1, m)
+    kind, xn = 1, None
+    if it >= 1 and (it + 1) % q == 0:
+        f = h["filled"]
+        Rm, Xm = h["R"][:f].T, h["X"][:f].T
+        gamma = solve_small(Rm.T @ Rm, Rm.T @ r)
+        if gamma is not None:
+            xn = x + zeta * r - (Xm + zeta * Rm) @ gamma
+            kind = 2
+    if xn is None:
+        xn = x + alpha * r
+    h["xold"], h["rold"] = x.copy(), r.copy()
+    return np.clip(xn, 0.0, 1.0), kind
+
+
 def continuation(par, cnt, loop, kind="add"):
     """Continuation of Sec. 3 (parCont = {istart, maxPar, isteps, deltaPar});
     kind "add" (paper) or "mul" (doubling, clamped to maxPar) (reading R9)."""
@@ -703,6 +760,11 @@ class Params:
     newton_tol: float = 1e-6
     oc_tol: float = 1e-4
     oc_method: str = "bisection"  # or "primal_dual" (Appendix A), "filtered" (Sec. 3.2, general variant)
+    pae_q0: int = 0               # first loop of the periodic Anderson extrapolation (0: off)
+    pae_q: int = 4
+    pae_m: int = 4
+    pae_alpha: float = 0.9
+    pae_zeta: float = 1.0
     solver: str = "direct"
     cg_rtol: float = 1e-10
 
@@ -725,6 +787,7 @@ class State:
     beta: float
     loop: int = 0
     history: list = field(default_factory=list)
+    pae: dict = field(default_factory=dict)
 
 
 def initial_state(p: Params, passive=None):
@@ -775,6 +838,7 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
     dc = filter_backward(g, dc, p.rmin, p.ftBC, dp)
     dV0 = filter_backward(g, dV, p.rmin, p.ftBC, dp)
     # RL.4 OC and continuation
+    x_prev = s.x.copy()
     if p.oc_method == "primal_dual":
         s.x, lm, n_bis = oc_update_primal_dual(s.x, dc, dV0, act, p.move, p.volfrac)
     elif p.oc_method == "filtered":
@@ -782,11 +846,16 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
                                             s.eta, s.beta, pas, p.oc_tol)
     else:
         s.x, lm, n_bis = oc_update(s.x, dc, dV0, act, p.move, p.volfrac, p.oc_tol)
+    pae_kind = 0
+    if p.pae_q0 > 0 and s.loop >= p.pae_q0:
+        xa, pae_kind = pae_update(s.pae, x_prev[act], s.x[act] - x_prev[act], s.loop - p.pae_q0, p.pae_m,
+                                  p.pae_q, p.pae_alpha, p.pae_zeta)
+        s.x[act] = xa
     s.penal = continuation(s.penal, p.penal_cnt, s.loop, p.penal_kind)
     s.beta = continuation(s.beta, p.beta_cnt, s.loop, p.beta_kind)
     info = dict(loop=s.loop, c=c, V=float(np.mean(xphys)), ch=ch, penal=s.penal,
                 beta=s.beta, eta=s.eta, lm=lm, n_newton=n_newton, n_bisect=n_bis,
-                n_cg=n_cg)
+                n_cg=n_cg, pae=pae_kind)
     s.history.append(info)
     return info
 

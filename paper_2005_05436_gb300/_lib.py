@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("deadline_cycles", C.c_int64), ("inner_rtol", C.c_double),
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
-                ("_pad3", C.c_int32)]
+                ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
+                ("pae_zeta", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -62,7 +63,7 @@ class IterInfo(C.Structure):
                 ("rel_res", C.c_double), ("t_filter_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_warm_ms", C.c_double), ("warm_a", C.c_double), ("warm_b", C.c_double),
-                ("warm_err_prev", C.c_double), ("warm_err", C.c_double)]
+                ("warm_err_prev", C.c_double), ("warm_err", C.c_double), ("pae", C.c_int32), ("_pad2", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -149,6 +149,10 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
     TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 3, "ku_impl must be 0, 1, 2 or 3");
+    TOPO_REQUIRE(p->pae_q0 >= 0 && p->pae_q >= 1 && p->pae_m >= 1 && p->pae_m <= 4 && p->pae_alpha > 0.0 &&
+                     p->pae_alpha <= 1.0 && p->pae_zeta >= 0.0 && p->pae_zeta <= 1.0,
+                 "Anderson extrapolation: pae_q0 >= 0, pae_q >= 1, pae_m in 1..4, pae_alpha in (0, 1], "
+                 "pae_zeta in [0, 1]");
     TOPO_REQUIRE(p->oc_method == TO_OC_BISECTION || p->oc_method == TO_OC_PRIMAL_DUAL ||
                      p->oc_method == TO_OC_PHYSICAL_VOLUME,
                  "oc_method must be TO_OC_BISECTION, TO_OC_PRIMAL_DUAL or TO_OC_PHYSICAL_VOLUME");
@@ -201,6 +205,11 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->mg_nu = 2;
     p->mg_coarse_every = 1;
     p->oc_method = TO_OC_BISECTION;
+    p->pae_q0 = 0;
+    p->pae_q = 4;
+    p->pae_m = 4;
+    p->pae_alpha = 0.9;
+    p->pae_zeta = 1.0;
     return TO_OK;
 }
 
@@ -378,6 +387,7 @@ void to_destroy(to_grid* g) {
     if (g->st) cudaStreamSynchronize(g->st);
     solver_free(g);
     warm_free(g);
+    pae_free(g);
     for (void* p : g->allocs) cudaFree(p);
     if (g->hs) cudaFreeHost(g->hs);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
@@ -578,6 +588,8 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     launch_filter(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st);
     TOPO_CUDA(cudaEventRecord(g->ev_t[3], st));
     // RL.4 OC update
+    const bool pae_on = p.pae_q0 > 0 && s->loop >= p.pae_q0;
+    if (pae_on) pae_before_oc(g, s->x, st);
     if (p.oc_method == TO_OC_PHYSICAL_VOLUME) {
         // the physical field of each candidate, with the step's threshold and sharpness
         launch_oc_filtered(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, s->x, g->dcf, g->dV0, g->passive, g->nact,
@@ -588,6 +600,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
         launch_oc(d.nel, s->x, g->dcf, g->dV0, g->passive, g->nact, p.move, p.volfrac, oc_tol_of(p), p.oc_maxit,
                   p.deadline_cycles, g->ocp, g->partials, g->bar, &g->ds->oo, g->oc_blocks, st, p.oc_method);
     }
+    const int pae_kind = pae_on ? pae_after_oc(g, s->x, s->loop - p.pae_q0, st) : 0;
     TOPO_CUDA(cudaEventRecord(g->ev_t[4], st));
     TOPO_CUDA(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     TOPO_CUDA(cudaMemcpyAsync(&g->hbar, g->bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, st));
@@ -610,6 +623,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
         it.n_newton = h.po.newton;
     }
     it.lm = h.oo.lm;
+    it.pae = pae_kind == 2 ? (h.pae_ok ? 2 : 1) : pae_kind;
     it.n_bisect = h.oo.steps;
     float ms[4];
     for (int i = 0; i < 4; ++i) TOPO_CUDA(cudaEventElapsedTime(&ms[i], g->ev_t[i], g->ev_t[i + 1]));

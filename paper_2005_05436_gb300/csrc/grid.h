@@ -18,6 +18,8 @@ struct DevScalars {
     PcgScalars pcg;
     double res[4];     // refinement norms
     OcfState ocf;      // OC search on the physical field
+    int pae_ok;        // the Anderson least-squares system was regular
+    int pad_;
 };
 
 struct Solver;  // solver.cu
@@ -85,6 +87,7 @@ struct to_grid {
     to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned
     void* warm = nullptr;      // its workspace (warm.cu)
     int warm_stride = 1;       // the network's node-grid coarsening (1 or 2)
+    void* pae = nullptr;       // Anderson extrapolation history (pae.cu)
 };
 
 namespace topo {
@@ -110,6 +113,13 @@ inline const KeP<float, 8>& grid_ke2<float>(const to_grid* g) { return g->ke2f; 
 
 void grid_sync_in(to_grid* g);
 void warm_free(to_grid* g);
+// Periodic Anderson extrapolation (pae.cu): keep x before the OC step, then
+// replace the OC output by the damped or extrapolated step (it = loop - q0);
+// returns 1 (damped) or 2 (extrapolation attempted; DevScalars::pae_ok says
+// whether it was taken). pae_free releases the history.
+void pae_before_oc(to_grid* g, const double* x, cudaStream_t st);
+int pae_after_oc(to_grid* g, double* x, int it, cudaStream_t st);
+void pae_free(to_grid* g);
 void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy);
 void grid_sync_out(to_grid* g);
 void solver_init(to_grid* g);

@@ -112,6 +112,40 @@ def bench_frame(a):
     print(json.dumps(out))
 
 
+def bench_pae(a):
+    """The convergence study of Sec. 3.6 (Table 2) on the half MBB beam (300 x 100,
+    f = 0.5, rmin = 8.75, penal 3, no continuation): T1 density filter (ft 1), T2
+    filter + volume-preserving projection (ft 3, beta 2); each without and with
+    periodic Anderson extrapolation (q0 = 20, q = 4, m_r = 4, alpha 0.9, zeta 1),
+    run until ||xPhys_k - xPhys_k-1|| / sqrt(m) < 1e-6 or 2500 design iterations
+    (FP64 + GMG state solves to 1e-8)."""
+    from . import TO_FP64, TO_PC_GMG
+    from .topopt import Design, Grid
+    nelx, nely = (int(v) for v in a.grid.split("x")[:2])
+    F, fixed = I.mbb_half_beam(nelx, nely)
+    out = {"grid": f"{nelx}x{nely}", "paper_iterations": {"T1": 2500, "T1-PAE": 828, "T2": 2500, "T2-PAE": 352}}
+    for case, ft in (("T1", 1), ("T2", 3)):
+        for pae in (False, True):
+            p = default_params(2, nelx, nely, 0, volfrac=0.5, penal=3.0, rmin=8.75, ft=ft, eta=0.5, beta=2.0,
+                               precision=TO_FP64, precond=TO_PC_GMG, mg_nu=1, cg_rtol=1e-8, cg_maxit=50000,
+                               penal_cnt=(1, 3.0, 1000000, 0.0), beta_cnt=(1, 2.0, 1000000, 0.0),
+                               pae_q0=20 if pae else 0, pae_q=4, pae_m=4, pae_alpha=0.9, pae_zeta=1.0)
+            g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+            d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.5)).cuda())
+            t0 = time.perf_counter()
+            info = None
+            while True:
+                info = d.step()
+                if info["ch"] < 1e-6 or info["loop"] >= a.steps:
+                    break
+            dt = time.perf_counter() - t0
+            out[case + ("-PAE" if pae else "")] = {"iterations": info["loop"], "c": round(info["c"], 2),
+                                                   "ch": info["ch"], "s": round(dt, 2),
+                                                   "ms_per_iteration": round(1e3 * dt / info["loop"], 2)}
+            g.close()
+    print(json.dumps(out))
+
+
 def bench_batch(a):
     """Under torchrun each rank advances its share of the instances (balanced by
     element count, no collective in the data path); rank 0 prints the whole-job
@@ -182,7 +216,7 @@ def bench_net(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame"])
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"])
@@ -194,7 +228,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1)
     a = ap.parse_args()
     B.build()
-    {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc, "frame": bench_frame}[a.what](a)
+    {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc, "frame": bench_frame,
+     "pae": bench_pae}[a.what](a)
 
 
 if __name__ == "__main__":

@@ -193,7 +193,9 @@ def _run_parity(shape, n_iter, **kw):
                                    p.beta_cnt.delta),
                          penal_kind="add" if p.penal_cnt.kind == 0 else "mul",
                          beta_kind="add" if p.beta_cnt.kind == 0 else "mul",
-                         oc_method={0: "bisection", 1: "primal_dual", 2: "filtered"}[p.oc_method])
+                         oc_method={0: "bisection", 1: "primal_dual", 2: "filtered"}[p.oc_method],
+                         pae_q0=p.pae_q0, pae_q=p.pae_q, pae_m=p.pae_m, pae_alpha=p.pae_alpha,
+                         pae_zeta=p.pae_zeta)
     s = O.initial_state(op)
     Ke = O.element_stiffness(3 if shape[2] else 2)
     d = Design(g, to_cuda(I.initial_design(g.nel, p.volfrac)))
@@ -208,6 +210,7 @@ def _run_parity(shape, n_iter, **kw):
         assert abs(got["c"] - ref["c"]) <= 1e-8 * abs(ref["c"]), (k, got["c"], ref["c"])
         assert abs(got["eta"] - ref["eta"]) <= 1e-9
         assert got["penal"] == ref["penal"] and got["beta"] == ref["beta"]
+        assert got["pae"] == ref["pae"], (k, got["pae"], ref["pae"])
     return worst
 
 
@@ -296,6 +299,18 @@ def test_design_iterations_physical_volume_parity(ft):
     _run_parity((12, 6, 6), 6, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=4.0, eta=0.4, ft=ft,
                 newton_tol=1e-14, oc_tol=1e-15, oc_method=TO_OC_PHYSICAL_VOLUME, cg_rtol=1e-12,
                 cg_maxit=200000)
+
+
+def test_design_iterations_anderson_extrapolation_parity():
+    """Periodic Anderson extrapolation of the OC iteration (Sec. 3.6): damped steps
+    and, every q = 4th step from q0, the least-squares extrapolation over m_r = 4
+    history columns, against the oracle over the design iterations (ft 1, 2D;
+    ft 3, 3D), including which steps were extrapolated."""
+    _run_parity((60, 20, 0), 18, volfrac=0.5, penal=3.0, rmin=2.4, ft=1, newton_tol=1e-14, oc_tol=1e-15,
+                cg_rtol=1e-12, cg_maxit=200000, pae_q0=3, pae_q=4, pae_m=4, pae_alpha=0.9, pae_zeta=1.0)
+    _run_parity((12, 6, 6), 12, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0, ft=3, newton_tol=1e-14,
+                oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=200000, pae_q0=2, pae_q=4, pae_m=3, pae_alpha=0.9,
+                pae_zeta=1.0)
 
 
 def test_design_iterations_mbb_60x20_parity():

@@ -544,6 +544,41 @@ def test_oc_filtered_reduces_to_bisection_and_meets_physical_volume():
     np.testing.assert_array_equal(xn[~act], x[~act])
 
 
+def test_pae_extrapolation_reaches_the_fixed_point_of_an_affine_map():
+    """On an affine contraction U(x) = A x + c the extrapolation step is a
+    GMRES-like minimal-residual step: with as many history columns as
+    dimensions it lands on the fixed point (I - A)^-1 c exactly (up to
+    rounding); the damped steps are x + alpha r."""
+    r = np.random.default_rng(5)
+    n = 3
+    A = 0.3 * r.standard_normal((n, n)) / n
+    c = 0.2 + 0.1 * r.random(n)
+    xstar = np.linalg.solve(np.eye(n) - A, c)
+    assert np.all((xstar > 0) & (xstar < 1))
+    h = {}
+    x = np.full(n, 0.5)
+    for it in range(4):  # q = 4, m = 3: steps 0..2 damped, step 3 extrapolated
+        res = A @ x + c - x
+        xn, kind = O.pae_update(h, x, res, it, 3, 4, 0.9, 1.0)
+        if it < 3:
+            assert kind == 1
+            np.testing.assert_allclose(xn, np.clip(x + 0.9 * res, 0, 1), rtol=0, atol=1e-15)
+        else:
+            assert kind == 2
+            np.testing.assert_allclose(xn, xstar, rtol=0, atol=1e-12)
+        x = xn
+
+
+def test_solve_small_matches_numpy_and_flags_singular():
+    r = np.random.default_rng(6)
+    B = r.standard_normal((4, 4))
+    G = B.T @ B + 0.1 * np.eye(4)
+    b = r.standard_normal(4)
+    np.testing.assert_allclose(O.solve_small(G, b), np.linalg.solve(G, b), rtol=1e-12)
+    S = np.outer([1.0, 2.0, 3.0], [1.0, 2.0, 3.0])
+    assert O.solve_small(S, np.ones(3)) is None
+
+
 def test_oc_paper_mode_step_count():
     """Sec. 3.3: with the lambda# bracket ~14 bisection steps at tol 1e-4."""
     n = 1200
