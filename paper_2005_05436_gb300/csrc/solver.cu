@@ -249,6 +249,8 @@ struct Solver {
     PcgScalars* hpcg = nullptr;  // pinned mirror
     std::vector<void*> allocs;
     cudaEvent_t ev[3] = {};      // phase timers
+    cudaEvent_t ev_setup[2] = {};  // solver_setup's own timers
+    bool setup_done = false;       // solver_setup ran for the coming solve
     double t_setup = 0, t_krylov = 0, t_resid = 0;
 };
 
@@ -347,18 +349,22 @@ static void build_loop_graph(to_grid* g, Pcg<T>& P) {
 
 // Set up the preconditioner from P.E (when `setup`), r = b - K x (or r = b for
 // x = 0), and run the loop.
+// The preconditioner for the current modulus P.E: multigrid hierarchy or Jacobi diagonal.
+template <typename T>
+static void precond_setup(to_grid* g, Pcg<T>& P, cudaStream_t st) {
+    if (P.mg)
+        mg_setup<T>(g, P.mg, P.E, st);
+    else
+        launch_diag_inv<T>(g->d, grid_ke3<T>(g), grid_ke2<T>(g), P.E, g->fixed, P.dinv_j, st);
+}
+
 template <typename T>
 static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int maxit, bool x0_zero, bool setup) {
     const Dims& d = g->d;
     const long long n = d.ndof;
     cudaStream_t st = g->st;
     TOPO_CUDA(cudaEventRecord(sv->ev[0], st));
-    if (setup) {
-        if (P.mg)
-            mg_setup<T>(g, P.mg, P.E, st);
-        else
-            launch_diag_inv<T>(d, grid_ke3<T>(g), grid_ke2<T>(g), P.E, g->fixed, P.dinv_j, st);
-    }
+    if (setup) precond_setup<T>(g, P, st);
     if (!P.loop) {
         build_loop_graph<T>(g, P);
         P.body_kernels = captured_launches_reset();
@@ -428,6 +434,7 @@ void solver_init(to_grid* g) {
         s->y64 = salloc<double>(s, g->d.ndof);
         s->res = salloc<double>(s, 4);
         for (int i = 0; i < 3; ++i) TOPO_CUDA(cudaEventCreate(&s->ev[i]));
+        for (int i = 0; i < 2; ++i) TOPO_CUDA(cudaEventCreate(&s->ev_setup[i]));
         TOPO_CUDA(cudaMallocHost(&s->hres, 4 * sizeof(double)));
         TOPO_CUDA(cudaMallocHost(&s->hpcg, sizeof(PcgScalars)));
     } catch (...) {
@@ -446,6 +453,8 @@ void solver_free(to_grid* g) {
     for (void* p : s->allocs) cudaFree(p);
     for (int i = 0; i < 3; ++i)
         if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    for (int i = 0; i < 2; ++i)
+        if (s->ev_setup[i]) cudaEventDestroy(s->ev_setup[i]);
     if (s->hres) cudaFreeHost(s->hres);
     if (s->hpcg) cudaFreeHost(s->hpcg);
     delete s;
@@ -467,6 +476,24 @@ static void true_residual(to_grid* g, Solver* sv, const double* b, const double*
     sv->t_resid += elapsed_ms(sv->ev[0], sv->ev[1]);
 }
 
+// Preconditioner set-up for the modulus in g->E, enqueued on the grid stream
+// ahead of the next solve_state (which then skips it), so that independent work
+// on another stream (the learned warm start) can overlap it.
+void solver_setup(to_grid* g) {
+    Solver* sv = g->solver;
+    cudaStream_t st = g->st;
+    TOPO_CUDA(cudaEventRecord(sv->ev_setup[0], st));
+    if (g->p.precision == TO_FP64) {
+        precond_setup<double>(g, sv->p64, st);
+    } else {
+        k_cast_mask<double, float><<<div_up(g->d.nel, 256), 256, 0, st>>>(g->d.nel, g->E, sv->p32.E, nullptr);
+        TOPO_CHECK_LAUNCH();
+        precond_setup<float>(g, sv->p32, st);
+    }
+    TOPO_CUDA(cudaEventRecord(sv->ev_setup[1], st));
+    sv->setup_done = true;
+}
+
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info) {
     Solver* sv = g->solver;
     const Dims& d = g->d;
@@ -476,6 +503,8 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
     int iters = 0, refinements = 0;
     double rel = 0.0;
     sv->t_setup = sv->t_krylov = sv->t_resid = 0.0;
+    const bool pre = sv->setup_done;  // the preconditioner is already set up for this modulus
+    sv->setup_done = false;
     if (g->p.precision == TO_FP64) {
         Pcg<double>& P = sv->p64;
         TOPO_CUDA(cudaMemcpyAsync(P.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -484,7 +513,8 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         // The recursive CG residual can drift below the true one; the true FP64
         // residual decides, and the PCG restarts from the current x if needed.
         for (int restart = 0;; ++restart) {
-            const PcgScalars h = run_pcg<double>(g, sv, P, g->p.cg_rtol, g->p.cg_maxit - iters, false, restart == 0);
+            const PcgScalars h =
+                run_pcg<double>(g, sv, P, g->p.cg_rtol, g->p.cg_maxit - iters, false, restart == 0 && !pre);
             iters += h.iters;
             true_residual(g, sv, P.b, P.x, P.r, nullptr);
             rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
@@ -504,11 +534,13 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         Pcg<float>& P = sv->p32;
         double* x64 = sv->p64.x;
         double* r64 = sv->p64.r;
-        k_cast_mask<double, float><<<div_up(d.nel, 256), 256, 0, st>>>(d.nel, g->E, P.E, nullptr);
+        if (!pre) {
+            k_cast_mask<double, float><<<div_up(d.nel, 256), 256, 0, st>>>(d.nel, g->E, P.E, nullptr);
+            count_launches(1);
+        }
         k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, x64, g->fixed);
         TOPO_CHECK_LAUNCH();
-        count_launches(1);
-        bool prepared = false;
+        bool prepared = pre;
         const int max_ref = 60;
         true_residual(g, sv, b, x64, r64, P.b);
         rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
@@ -567,6 +599,7 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             if (herr) status = TO_ETIMEOUT;
         }
     }
+    if (pre) sv->t_setup += elapsed_ms(sv->ev_setup[0], sv->ev_setup[1]);  // the stream has drained
     if (info) {
         info->iters = iters;
         info->refinements = refinements;

@@ -1,13 +1,16 @@
 // The learned warm start inside the design iteration (no counterpart in the
 // paper): node features -> network -> displacement direction U_h, and the
 // starting point of the state solve is the minimiser of the potential energy
-// 1/2 U^T K U - F^T U over span{U_prev, U_h} (a 2 x 2 Rayleigh-Ritz step with
-// FP64 operator products). Its energy never exceeds that of U_prev, and the
-// solve that follows runs to the same tolerance, so the solution does not
-// depend on the network; only the iteration count can.
+// 1/2 U^T K U - F^T U over span{U_prev, U_h} (a 2 x 2 Rayleigh-Ritz step; its
+// operator products in FP32 for the mixed solve, FP64 otherwise). Its energy
+// never exceeds that of U_prev, and the solve that follows runs to the same
+// tolerance, so the solution does not depend on the network; only the
+// iteration count can. It runs on a stream of its own while the grid stream
+// sets up the preconditioner.
 #include <cmath>
 
 #include "grid.h"
+#include "mg.h"
 
 namespace topo {
 
@@ -31,6 +34,12 @@ struct WarmWS {
     double *Uh = nullptr, *KUh = nullptr, *Up = nullptr, *KUp = nullptr, *dots = nullptr, *hdots = nullptr;
     unsigned* fmax = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // the warm start runs on its own stream, beside the preconditioner set-up
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, ready = nullptr, join = nullptr;
+    float *E32 = nullptr, *u32 = nullptr, *y32 = nullptr;  // FP32 operator products (mixed path)
+    double* partials = nullptr;                            // reduction scratch of its own
+    unsigned* counter = nullptr;
 };
 
 inline int pad4(int n) { return (n + 3) / 4 * 4; }
@@ -166,6 +175,17 @@ __global__ void kw_combine(long long n, double a, const double* __restrict__ Up,
     if (i < n) U[i] = a * Up[i] + b * Uh[i];
 }
 
+__global__ void kw_to_f32(long long n, const double* __restrict__ a, const uint8_t* __restrict__ fixed,
+                          float* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (fixed && fixed[i]) ? 0.f : (float)a[i];
+}
+
+__global__ void kw_to_f64(long long n, const float* __restrict__ a, double* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)a[i];
+}
+
 template <typename T>
 T* walloc(to_grid* g, long long count) {
     void* p = nullptr;
@@ -196,7 +216,29 @@ WarmWS* warm_ws(to_grid* g) {
     TOPO_CUDA(cudaMallocHost(&w->hdots, 8 * sizeof(double)));
     TOPO_CUDA(cudaEventCreate(&w->e0));
     TOPO_CUDA(cudaEventCreate(&w->e1));
+    TOPO_CUDA(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&w->fork, &w->ready, &w->join})
+        TOPO_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    if (g->p.precision == TO_MIXED) {
+        w->E32 = walloc<float>(g, g->d.nel);
+        w->u32 = walloc<float>(g, g->d.ndof);
+        w->y32 = walloc<float>(g, g->d.ndof);
+    }
+    w->partials = walloc<double>(g, g->npartials);
+    w->counter = walloc<unsigned>(g, 16);
+    TOPO_CUDA(cudaMemsetAsync(w->counter, 0, 16 * sizeof(unsigned), g->st));
+    TOPO_CUDA(cudaStreamSynchronize(g->st));
     return w;
+}
+
+// KU = K U with the grid's FP32 operator (the one of the mixed solve) and the FP32 modulus in w->E32.
+void product32(to_grid* g, WarmWS* w, const double* U, double* KU, cudaStream_t st) {
+    const long long n = g->d.ndof;
+    kw_to_f32<<<div_up(n, 256), 256, 0, st>>>(n, U, g->fixed, w->u32);
+    TOPO_CHECK_LAUNCH();
+    launch_fine_op<float>(g, 0, w->E32, w->u32, nullptr, nullptr, w->y32, 0.f, nullptr, nullptr, st);
+    kw_to_f64<<<div_up(n, 256), 256, 0, st>>>(n, w->y32, KU);
+    TOPO_CHECK_LAUNCH();
 }
 
 void features(to_grid* g, WarmWS* w, const double* xPhys, float* x, cudaStream_t st) {
@@ -217,6 +259,12 @@ void warm_free(to_grid* g) {
     if (w->hdots) cudaFreeHost(w->hdots);
     if (w->e0) cudaEventDestroy(w->e0);
     if (w->e1) cudaEventDestroy(w->e1);
+    for (cudaEvent_t e : {w->fork, w->ready, w->join})
+        if (e) cudaEventDestroy(e);
+    if (w->aux) {
+        cudaStreamSynchronize(w->aux);
+        cudaStreamDestroy(w->aux);
+    }
     delete w;
     g->warm = nullptr;
 }
@@ -225,30 +273,38 @@ void warm_free(to_grid* g) {
 void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy) {
     WarmWS* w = warm_ws(g);
     const Dims& d = g->d;
-    cudaStream_t st = g->st;
-    TOPO_CUDA(cudaEventRecord(w->e0, st));
-    features(g, w, xPhys, w->x, st);
-    net_forward_on(g->net, w->x, 1, w->D, w->H, w->W, w->y, st);
-    kw_crop<<<div_up(d.nnodes, 256), 256, 0, st>>>(d, w->cg, w->y, g->fixed, w->Uh);
+    cudaStream_t st = g->st, ax = w->aux;
+    // xPhys, E and U are ready in the grid stream's order; the warm start forks
+    // onto its own stream, and the preconditioner set-up for this design runs on
+    // the grid stream meanwhile (the two share no buffer that either writes).
+    TOPO_CUDA(cudaEventRecord(w->fork, st));
+    TOPO_CUDA(cudaStreamWaitEvent(ax, w->fork, 0));
+    TOPO_CUDA(cudaEventRecord(w->e0, ax));
+    features(g, w, xPhys, w->x, ax);
+    net_forward_on(g->net, w->x, 1, w->D, w->H, w->W, w->y, ax);
+    kw_crop<<<div_up(d.nnodes, 256), 256, 0, ax>>>(d, w->cg, w->y, g->fixed, w->Uh);
     TOPO_CHECK_LAUNCH();
-    launch_mask_copy(d.ndof, U, w->Up, g->fixed, st);
+    launch_mask_copy(d.ndof, U, w->Up, g->fixed, ax);
     if (g->p.precision == TO_MIXED) {
         // the products only choose a starting point: the FP32 operator is enough
-        apply_K_fp32(g, xPhys, w->Uh, w->KUh, 1);
-        apply_K_fp32(g, xPhys, w->Up, w->KUp, 1);
+        launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, w->E32, ax);
+        product32(g, w, w->Uh, w->KUh, ax);
+        product32(g, w, w->Up, w->KUp, ax);
     } else {
         launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Uh, w->KUh, g->fixed,
-                               true, st);
+                               true, ax);
         launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Up, w->KUp, g->fixed,
-                               true, st);
+                               true, ax);
     }
-    launch_dot(d.ndof, g->F, w->Up, w->dots + 0, g->partials, g->counter, st);
-    launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, g->partials, g->counter, st);
-    launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, g->partials, g->counter, st);
-    launch_dot(d.ndof, w->Up, w->KUh, w->dots + 3, g->partials, g->counter, st);
-    launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 4, g->partials, g->counter, st);
-    TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TOPO_CUDA(cudaStreamSynchronize(st));
+    launch_dot(d.ndof, g->F, w->Up, w->dots + 0, w->partials, w->counter, ax);
+    launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, w->partials, w->counter, ax);
+    launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, w->partials, w->counter, ax);
+    launch_dot(d.ndof, w->Up, w->KUh, w->dots + 3, w->partials, w->counter, ax);
+    launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 4, w->partials, w->counter, ax);
+    TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 5 * sizeof(double), cudaMemcpyDeviceToHost, ax));
+    TOPO_CUDA(cudaEventRecord(w->ready, ax));
+    solver_setup(g);
+    TOPO_CUDA(cudaEventSynchronize(w->ready));
     const double fp = w->hdots[0], fh = w->hdots[1], pp = w->hdots[2], ph = w->hdots[3], hh = w->hdots[4];
     double a = 1.0, b = 0.0;  // keep U when the network direction adds nothing
     const bool hok = hh > 0.0 && std::isfinite(hh) && std::isfinite(fh);
@@ -263,10 +319,12 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
         }
     }
     if (!(a == 1.0 && b == 0.0)) {
-        kw_combine<<<div_up(d.ndof, 256), 256, 0, st>>>(d.ndof, a, w->Up, b, w->Uh, U);
+        kw_combine<<<div_up(d.ndof, 256), 256, 0, ax>>>(d.ndof, a, w->Up, b, w->Uh, U);
         TOPO_CHECK_LAUNCH();
     }
-    TOPO_CUDA(cudaEventRecord(w->e1, st));
+    TOPO_CUDA(cudaEventRecord(w->e1, ax));
+    TOPO_CUDA(cudaEventRecord(w->join, ax));
+    TOPO_CUDA(cudaStreamWaitEvent(st, w->join, 0));
     TOPO_CUDA(cudaEventSynchronize(w->e1));
     float t = 0.f;
     TOPO_CUDA(cudaEventElapsedTime(&t, w->e0, w->e1));
