@@ -206,7 +206,7 @@ __global__ void kb_modulus(long long n, const double* __restrict__ xPhys, const 
                            double* __restrict__ E64, float* __restrict__ E32) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double e = Emin + pow(xPhys[i], G->penal) * (E0 - Emin);
+    const double e = Emin + powp(xPhys[i], G->penal) * (E0 - Emin);
     E64[i] = e;
     E32[i] = (float)e;
 }
@@ -579,7 +579,7 @@ __global__ void kb_sens(BK k, const KeP<double, 8> ke, const double* __restrict_
     }
     const double p = k.G->penal;
     const long long e = I.el0 + ey + (long long)I.nely * ex;
-    dc[e] = -p * (E0 - Emin) * pow(xPhys[e], p - 1.0) * ce;
+    dc[e] = -p * (E0 - Emin) * powp(xPhys[e], p - 1.0) * ce;
 }
 
 // ocP = x sqrt(max(0, -dc / dV0)); bracket [0, mean(ocP) / f] (Eq. 17).

@@ -95,6 +95,20 @@ __host__ __device__ inline int mirror_index(int j, int n) {
 
 // ------------------------------------------------------------ reductions --
 
+// x^p for the penalisation exponent: small integer exponents (the usual
+// p = 3 and its p - 1 = 2) by repeated multiplication, since the FP64 pow is a
+// long instruction sequence at the FP64 rate; other exponents by pow.
+__device__ __forceinline__ double powp(double x, double p) {
+    if (p == 1.0) return x;
+    if (p == 2.0) return x * x;
+    if (p == 3.0) return x * x * x;
+    if (p == 4.0) {
+        const double x2 = x * x;
+        return x2 * x2;
+    }
+    return pow(x, p);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -12,7 +12,7 @@ template <typename T>
 __global__ void k_modulus(long long n, const double* __restrict__ x, double penal, double E0,
                           double Emin, T* __restrict__ E) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) E[i] = (T)(Emin + pow(x[i], penal) * (E0 - Emin));
+    if (i < n) E[i] = (T)(Emin + powp(x[i], penal) * (E0 - Emin));
 }
 
 template <typename T>
@@ -242,18 +242,70 @@ __global__ void __launch_bounds__(ONT) k_oc(long long n, double* __restrict__ x,
                 }
             }
             double v[OC_NC], tot[OC_NC];
+            // FP32 screen of the 15 volumes. Per element the FP32 term differs from
+            // the FP64 one by at most 4.01 u hi <= 4.01 u (u = 2^-24: rounding of
+            // ocP, 1/lmid, their product, and of hi; clamping is 1-Lipschitz),
+            // plus 2e-15 for subnormal ocP while 1/lmid <= 1e30; a thread's FP32
+            // sum of at most M terms adds (M - 1) u of its value. A decision on
+            // the path the walk takes is certain when the screened volume is
+            // farther than that bound from volfrac; otherwise the pass is redone
+            // in FP64, so the lambda sequence is the FP64 bisection's.
+            bool certain = true;
 #pragma unroll
-            for (int k = 0; k < OC_NC; ++k) v[k] = 0.0;
-            for (long long i = i0; i < n; i += stride) {
-                if (passive && passive[i] != 0) continue;
-                // max(max(min(min(t, x + m), 1), x - m), 0) = max(min(t, hi), lo) exactly
-                const double xi = x[i], o = ocp[i];
-                const double hi = fmin(xi + move, 1.0), lo = fmax(xi - move, 0.0);
+            for (int k = 0; k < OC_NC; ++k) certain = certain && c[k] >= 1e-30 && c[k] <= 1e30;
+            if (certain) {
+                float inv32[OC_NC], vf[OC_NC];
 #pragma unroll
-                for (int k = 0; k < OC_NC; ++k) v[k] += fmax(fmin(o * inv[k], hi), lo);
+                for (int k = 0; k < OC_NC; ++k) {
+                    inv32[k] = (float)inv[k];
+                    vf[k] = 0.f;
+                }
+                for (long long i = i0; i < n; i += stride) {
+                    if (passive && passive[i] != 0) continue;
+                    const double xi = x[i];
+                    const float o = (float)ocp[i], hi = (float)fmin(xi + move, 1.0), lo = (float)fmax(xi - move, 0.0);
+#pragma unroll
+                    for (int k = 0; k < OC_NC; ++k) vf[k] += fmaxf(fminf(o * inv32[k], hi), lo);
+                }
+#pragma unroll
+                for (int k = 0; k < OC_NC; ++k) v[k] = (double)vf[k];
+                if (!grid_totals<ONT, OC_NC>(v, partials, parity, bar, deadline, tot)) return;
+                parity ^= 1;
+                const double u = 0x1p-24, M = (double)((n + stride - 1) / stride);
+                double a1 = l1, a2 = l2;
+                int kk = 0, sk = steps;
+                for (int lev = 0; lev < OC_DEPTH; ++lev) {
+                    if (!((a2 - a1) / (a1 + a2) > tol && sk < maxit)) break;
+                    const double bound = (double)nact * (4.01 * u + 2e-15) + 1.01 * (M - 1.0) * u * fabs(tot[kk]);
+                    const double vol = (tot[kk] + pas_sum) / nd;
+                    if (!(fabs(vol - volfrac) > 1.25 * bound / nd + 1e-13 * (fabs(vol) + volfrac))) {
+                        certain = false;
+                        break;
+                    }
+                    if (vol > volfrac) {
+                        a1 = c[kk];
+                        kk = 2 * kk + 2;
+                    } else {
+                        a2 = c[kk];
+                        kk = 2 * kk + 1;
+                    }
+                    ++sk;
+                }
             }
-            if (!grid_totals<ONT, OC_NC>(v, partials, parity, bar, deadline, tot)) return;
-            parity ^= 1;
+            if (!certain) {
+#pragma unroll
+                for (int k = 0; k < OC_NC; ++k) v[k] = 0.0;
+                for (long long i = i0; i < n; i += stride) {
+                    if (passive && passive[i] != 0) continue;
+                    // max(max(min(min(t, x + m), 1), x - m), 0) = max(min(t, hi), lo) exactly
+                    const double xi = x[i], o = ocp[i];
+                    const double hi = fmin(xi + move, 1.0), lo = fmax(xi - move, 0.0);
+#pragma unroll
+                    for (int k = 0; k < OC_NC; ++k) v[k] += fmax(fmin(o * inv[k], hi), lo);
+                }
+                if (!grid_totals<ONT, OC_NC>(v, partials, parity, bar, deadline, tot)) return;
+                parity ^= 1;
+            }
             int k = 0;
             for (int lev = 0; lev < OC_DEPTH; ++lev) {
                 if (!((l2 - l1) / (l1 + l2) > tol && steps < maxit)) break;

@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(256) k_sensitivity(Dims d, const KeP<double, D
             ce += 2.0 * r * ue[i];
         }
         const double x = xphys[e];
-        const double Ee = Emin + pow(x, penal) * (E0 - Emin);
+        const double Ee = Emin + powp(x, penal) * (E0 - Emin);
         esum = Ee * ce;
-        dc[e] = (passive && passive[e] != 0) ? 0.0 : -penal * (E0 - Emin) * pow(x, penal - 1.0) * ce;
+        dc[e] = (passive && passive[e] != 0) ? 0.0 : -penal * (E0 - Emin) * powp(x, penal - 1.0) * ce;
     }
     double v[1] = {esum}, tot[1];
     if (last_block_totals<256, 1>(v, partials, counter, tot) && threadIdx.x == 0) *energy_sum = tot[0];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_sensitivity3_walsh(Dims d, const WalshK
 #pragma unroll
             for (int q = 1; q < 8; ++q) ce = fma(W[c][q], Z[c][q], ce);
         const double x = xphys[e];
-        const double xp1 = pow(x, penal - 1.0);
+        const double xp1 = powp(x, penal - 1.0);
         const double Ee = Emin + xp1 * x * (E0 - Emin);
         esum = Ee * ce;
         dc[e] = (passive && passive[e] != 0) ? 0.0 : -penal * (E0 - Emin) * xp1 * ce;

@@ -942,8 +942,21 @@ MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
 template <typename T>
 void mg_destroy(MG<T>* mg) {
     if (!mg) return;
+    if (mg->side) {
+        cudaStreamSynchronize(mg->side);
+        cudaStreamDestroy(mg->side);
+    }
+    if (mg->fork) cudaEventDestroy(mg->fork);
+    if (mg->ready) cudaEventDestroy(mg->ready);
     for (void* p : mg->allocs) cudaFree(p);
     delete mg;
+}
+
+template <typename T>
+void mg_wait_coarse(MG<T>* mg, cudaStream_t st) {
+    if (!mg->pending) return;
+    TOPO_CUDA(cudaStreamWaitEvent(st, mg->ready, 0));
+    mg->pending = false;
 }
 
 template <typename T, int DIM>
@@ -981,6 +994,15 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
     const bool refactor = mg->setups++ % mg->coarse_every == 0;
     if (mg->nc > 0 && refactor) {
         MGLevel<T>& L = mg->lev.back();
+        if (!mg->side) {
+            TOPO_CUDA(cudaStreamCreateWithFlags(&mg->side, cudaStreamNonBlocking));
+            TOPO_CUDA(cudaEventCreateWithFlags(&mg->fork, cudaEventDisableTiming));
+            TOPO_CUDA(cudaEventCreateWithFlags(&mg->ready, cudaEventDisableTiming));
+        }
+        // the rest of this set-up runs on the side stream; mg_wait_coarse joins it
+        TOPO_CUDA(cudaEventRecord(mg->fork, st));
+        TOPO_CUDA(cudaStreamWaitEvent(mg->side, mg->fork, 0));
+        st = mg->side;
         k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.fixed, mg->A);
         TOPO_CHECK_LAUNCH();
         // A_work holds the original diagonal during the factorization, then W = L^{-1};
@@ -999,11 +1021,15 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
         TOPO_CHECK_LAUNCH();
         k_chol_wtw<T><<<dim3(div_up(nc, 128), nc), 128, 0, st>>>(nc, mg->A_work, L.fixed, mg->Ainv);
         TOPO_CHECK_LAUNCH();
+        TOPO_CUDA(cudaEventRecord(mg->ready, st));
+        mg->pending = true;
     }
 }
 
 template <typename T>
 void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
+    // the previous factorization may still read the coarsest stencils when no V-cycle joined it
+    mg_wait_coarse<T>(mg, st);
     mg->E = E;
     if (g->d.dim == 3)
         setup_dim<T, 3>(g, mg, E, st);
@@ -1102,6 +1128,8 @@ template MG<double>* mg_create<double>(to_grid*, int, int, double);
 template MG<float>* mg_create<float>(to_grid*, int, int, double);
 template void mg_destroy<double>(MG<double>*);
 template void mg_destroy<float>(MG<float>*);
+template void mg_wait_coarse<double>(MG<double>*, cudaStream_t);
+template void mg_wait_coarse<float>(MG<float>*, cudaStream_t);
 template void mg_setup<double>(to_grid*, MG<double>*, const double*, cudaStream_t);
 template void mg_setup<float>(to_grid*, MG<float>*, const float*, cudaStream_t);
 template double* mg_vcycle<double>(to_grid*, MG<double>*, const double*, const int*, cudaStream_t, PcgScalars*,

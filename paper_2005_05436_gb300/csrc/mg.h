@@ -46,6 +46,11 @@ struct MG {
     const T* E = nullptr;   // fine modulus of the current set-up
     int coarse_every = 1;   // rebuild the coarsest inverse at every k-th set-up
     long long setups = 0;
+    // the coarsest factorization runs on a stream of its own (one CTA for most
+    // of it), so that other work on the set-up stream overlaps it
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, ready = nullptr;
+    bool pending = false;   // ready has not been waited on yet
     std::vector<void*> allocs;
 };
 
@@ -57,6 +62,10 @@ void mg_destroy(MG<T>* mg);
 // Rebuild every level from the fine modulus E (type T) of the current design.
 template <typename T>
 void mg_setup(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st);
+// Make st wait for the coarsest factorization of the last set-up (before the
+// first V-cycle after a set-up).
+template <typename T>
+void mg_wait_coarse(MG<T>* mg, cudaStream_t st);
 // Enqueue one V-cycle z = M r on level 0; returns the buffer holding z. All
 // launches are skipped while *skip != 0 (skip may be nullptr).
 template <typename T>

@@ -365,6 +365,7 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
     cudaStream_t st = g->st;
     TOPO_CUDA(cudaEventRecord(sv->ev[0], st));
     if (setup) precond_setup<T>(g, P, st);
+    if (P.mg) mg_wait_coarse<T>(P.mg, st);
     if (!P.loop) {
         build_loop_graph<T>(g, P);
         P.body_kernels = captured_launches_reset();
@@ -534,13 +535,13 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         Pcg<float>& P = sv->p32;
         double* x64 = sv->p64.x;
         double* r64 = sv->p64.r;
-        if (!pre) {
-            k_cast_mask<double, float><<<div_up(d.nel, 256), 256, 0, st>>>(d.nel, g->E, P.E, nullptr);
-            count_launches(1);
+        if (!pre) {  // set up first: the coarsest factorization then overlaps the true residual
+            solver_setup(g);
+            sv->setup_done = false;
         }
         k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, x64, g->fixed);
         TOPO_CHECK_LAUNCH();
-        bool prepared = pre;
+        bool prepared = true;
         const int max_ref = 60;
         true_residual(g, sv, b, x64, r64, P.b);
         rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
@@ -599,7 +600,8 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             if (herr) status = TO_ETIMEOUT;
         }
     }
-    if (pre) sv->t_setup += elapsed_ms(sv->ev_setup[0], sv->ev_setup[1]);  // the stream has drained
+    // the stream has drained
+    if (pre || g->p.precision != TO_FP64) sv->t_setup += elapsed_ms(sv->ev_setup[0], sv->ev_setup[1]);
     if (info) {
         info->iters = iters;
         info->refinements = refinements;
