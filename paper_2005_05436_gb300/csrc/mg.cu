@@ -1,5 +1,6 @@
 // Geometric multigrid: fine-level fused operators, Galerkin coarsening, node
 // stencils, transfer operators, coarsest dense inverse and the V-cycle.
+#include <cstdlib>
 #include <algorithm>
 #include <cmath>
 
@@ -600,6 +601,127 @@ __global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __r
         if (!fixed_f[DIM * f + c]) zf[DIM * f + c] += acc[c];
 }
 
+// Prolongation fused into the first post-smoothing sweep of a 3D coarse level:
+// out = u + omega dinv (r - K u) with u = cur + P zc (P zc added on free DOFs),
+// u never written to memory. A CTA covers a TY x TZ tile of nodes at one x
+// (TY * TZ = 32) with nine threads per node as k_stencil_op3s; it first forms
+// u on the tile and its one-node halo in shared memory, summing P zc in
+// k_prolong_add's order, then sweeps the stencil in k_stencil_op3s's order,
+// so the result is that of the two kernels in sequence.
+template <typename T, int TY>
+__global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, const T* __restrict__ zc,
+                                                          const T* __restrict__ cur, const T* __restrict__ S,
+                                                          const T* __restrict__ R, const T* __restrict__ r,
+                                                          const T* __restrict__ dinv, T* __restrict__ out,
+                                                          const uint8_t* __restrict__ fixed, T omega,
+                                                          const int* skip) {
+    constexpr int TZ = 32 / TY, HY = TY + 2, HZ = TZ + 2, NH = 3 * HZ * HY, Q = 9;
+    constexpr bool REL = rel_form<T>();
+    __shared__ T us[3 * NH];
+    __shared__ T part[9][32];
+    if (skip && *skip) return;
+    const int nty = (d.nny + TY - 1) / TY, ntz = (d.nnz + TZ - 1) / TZ;
+    const int by = blockIdx.x % nty, bz = (blockIdx.x / nty) % ntz, ix = blockIdx.x / (nty * ntz);
+    const int iy0 = by * TY, iz0 = bz * TZ;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = ty / 3, pl = ty % 3;
+    const int ly = tx % TY, lz = tx / TY;
+    const int iy = iy0 + ly, iz = iz0 + lz;
+    const bool valid = iy < d.nny && iz < d.nnz;
+    const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
+    const int mx = ix + pl - 1;
+    const bool plane = valid && mx >= 0 && mx < d.nnx;
+    // this thread's stencil blocks do not depend on u: their loads go out first
+    T sv[27], rv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rv[k] = (REL && pl == 1 && valid) ? R[(long long)(c * 3 + k) * d.nnodes + n] : T(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const int s = pl * 9 + j;
+        const int my = iy + j % 3 - 1, mz = iz + j / 3 - 1;
+        const bool in = plane && !(REL && s == 13) && my >= 0 && my < d.nny && mz >= 0 && mz < d.nnz;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sv[3 * j + k] = in ? S[((long long)s * Q + c * 3 + k) * d.nnodes + n] : T(0);
+    }
+    for (int v = tid; v < 3 * NH; v += 288) {
+        const int h = v / 3, k = v % 3;
+        const int hy = h % HY, hz = (h / HY) % HZ, hx = h / (HY * HZ);
+        const int fx = ix - 1 + hx, fz = iz0 - 1 + hz, fy = iy0 - 1 + hy;
+        T val = T(0);
+        if (fx >= 0 && fx < d.nnx && fy >= 0 && fy < d.nny && fz >= 0 && fz < d.nnz) {
+            const long long f = fy + (long long)d.nny * (fz + (long long)d.nnz * fx);
+            val = cur[3 * f + k];
+            if (!fixed[3 * f + k]) {
+                T acc = T(0);
+                const int nx = (fx & 1) ? 2 : 1, ny = (fy & 1) ? 2 : 1, nz = (fz & 1) ? 2 : 1;
+                for (int a = 0; a < nx; ++a)
+                    for (int b = 0; b < nz; ++b)
+                        for (int e = 0; e < ny; ++e) {
+                            const int NX = (fx >> 1) + a, NZ = (fz >> 1) + b, NY = (fy >> 1) + e;
+                            const T w = (nx == 2 ? T(0.5) : T(1)) * (ny == 2 ? T(0.5) : T(1)) *
+                                        (nz == 2 ? T(0.5) : T(1));
+                            const long long N = NY + (long long)dc.nny * (NZ + (long long)dc.nnz * NX);
+                            acc += w * zc[3 * N + k];
+                        }
+                val += acc;
+            }
+        }
+        us[v] = val;
+    }
+    __syncthreads();
+    const int hc = (ly + 1) + HY * ((lz + 1) + HZ * 1);
+    T acc = T(0);
+    if (valid) {
+        T uc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uc[k] = us[3 * hc + k];
+        if (REL && pl == 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc += rv[k] * uc[k];
+        }
+        if (plane) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int s = pl * 9 + j;
+                if (REL && s == 13) continue;
+                const int dz = j / 3 - 1, dy = j % 3 - 1;
+                const int my = iy + dy, mz = iz + dz;
+                if (my < 0 || my >= d.nny || mz < 0 || mz >= d.nnz) continue;
+                const int hm = (ly + 1 + dy) + HY * ((lz + 1 + dz) + HZ * pl);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T um = REL ? us[3 * hm + k] - uc[k] : us[3 * hm + k];
+                    acc += sv[3 * j + k] * um;
+                }
+            }
+        }
+    }
+    part[ty][tx] = acc;
+    __syncthreads();
+    if (pl != 0 || !valid) return;
+    const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
+    const long long i = 3 * n + c;
+    T o = us[3 * hc + c] + omega * dinv[i] * (r[i] - a);
+    if (fixed[i]) o = T(0);
+    out[i] = o;
+}
+
+// Tile height (nodes along y) of k_prolong_smooth3s with the fewest idle lanes.
+inline int prolong_smooth_ty(const Dims& d) {
+    int best = 8;
+    double bu = -1.0;
+    for (int ty : {8, 16, 32}) {
+        const int tz = 32 / ty;
+        const double u = (double)d.nny / (((d.nny + ty - 1) / ty) * ty) * ((double)d.nnz / (((d.nnz + tz - 1) / tz) * tz));
+        if (u > bu + 1e-9) {
+            bu = u;
+            best = ty;
+        }
+    }
+    return best;
+}
+
 template <typename T>
 __global__ void k_jacobi_first(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
                                T omega, const int* skip) {
@@ -852,6 +974,7 @@ __global__ void k_dense_apply(int n, const T* __restrict__ Ainv, const T* __rest
 // ------------------------------------------------------------ host side
 
 static constexpr long long DENSE_MAX = 1024;
+static constexpr long long FUSE_MAX_NODES = 16384;  // coarse levels with the fused prolongation
 static constexpr long long COARSE_TARGET = 1500;
 
 template <typename U, typename T>
@@ -866,6 +989,8 @@ template <typename T>
 MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
     MG<T>* mg = new MG<T>();
     try {
+        const char* fu = std::getenv("TOPO_MG_FUSE");  // 0: separate prolongation and smoothing kernels
+        mg->fuse_up = !(fu && fu[0] == '0');
         mg->nu = nu;
         mg->omega = (T)omega;
         Dims d = g->d;
@@ -1082,6 +1207,7 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
     T* cur = L.z;
     T* oth = L.t;
     const int nu = coarsest ? 4 * mg->nu : mg->nu;
+    int s0 = 0;  // post-smoothing sweeps already done (1 when fused with the prolongation)
     for (int s = 1; s < nu; ++s) {
         level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st);
         std::swap(cur, oth);
@@ -1101,13 +1227,35 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
             k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip, dc_inv, C.z, mg->omega);
         TOPO_CHECK_LAUNCH();
         T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st, nullptr, nullptr, jf);
-        if (L.d.dim == 3)
-            k_prolong_add<T, 3><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
-        else
-            k_prolong_add<T, 2><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
-        TOPO_CHECK_LAUNCH();
+        // small levels only: on a large one the halo's repeated prolongation costs
+        // more loads than the separate kernel (tiles are one node thick in x)
+        if (L.d.dim == 3 && l > 0 && mg->fuse_up && L.d.nnodes <= FUSE_MAX_NODES) {
+            // the prolongation inside the first post-smoothing sweep
+            const int ty = prolong_smooth_ty(L.d);
+            const long long nb = (long long)div_up(L.d.nny, ty) * div_up(L.d.nnz, 32 / ty) * L.d.nnx;
+            const dim3 blk(32, 9);
+#define TOPO_PS(TYV)                                                                                          \
+    k_prolong_smooth3s<T, TYV><<<(unsigned)nb, blk, 0, st>>>(L.d, C.d, zc, cur, L.S, L.R, rhs, L.dinv, oth, \
+                                                             L.fixed, mg->omega, skip)
+            if (ty == 8)
+                TOPO_PS(8);
+            else if (ty == 16)
+                TOPO_PS(16);
+            else
+                TOPO_PS(32);
+#undef TOPO_PS
+            TOPO_CHECK_LAUNCH();
+            std::swap(cur, oth);
+            s0 = 1;
+        } else {
+            if (L.d.dim == 3)
+                k_prolong_add<T, 3><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
+            else
+                k_prolong_add<T, 2><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
+            TOPO_CHECK_LAUNCH();
+        }
     }
-    for (int s = 0; s < nu; ++s) {
+    for (int s = s0; s < nu; ++s) {
         // the last fine-level sweep also forms r.z and the PCG beta when asked to
         const bool last = l == 0 && s == nu - 1 && fuse_rz;
         level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st, last ? fuse_rz : nullptr);

@@ -51,6 +51,7 @@ struct MG {
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, ready = nullptr;
     bool pending = false;   // ready has not been waited on yet
+    bool fuse_up = true;    // 3D coarse levels: prolongation fused into the first post-sweep
     std::vector<void*> allocs;
 };
 
