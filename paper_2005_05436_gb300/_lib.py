@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
-                ("pae_zeta", C.c_double)]
+                ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("_pad3", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -153,6 +153,7 @@ static void validate(const to_params* p) {
                      p->pae_alpha <= 1.0 && p->pae_zeta >= 0.0 && p->pae_zeta <= 1.0,
                  "Anderson extrapolation: pae_q0 >= 0, pae_q >= 1, pae_m in 1..4, pae_alpha in (0, 1], "
                  "pae_zeta in [0, 1]");
+    TOPO_REQUIRE(p->inner_maxit >= 1, "inner_maxit must be >= 1");
     TOPO_REQUIRE(p->oc_method == TO_OC_BISECTION || p->oc_method == TO_OC_PRIMAL_DUAL ||
                      p->oc_method == TO_OC_PHYSICAL_VOLUME,
                  "oc_method must be TO_OC_BISECTION, TO_OC_PRIMAL_DUAL or TO_OC_PHYSICAL_VOLUME");
@@ -210,6 +211,7 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->pae_m = 4;
     p->pae_alpha = 0.9;
     p->pae_zeta = 1.0;
+    p->inner_maxit = 2000;
     return TO_OK;
 }
 
@@ -334,6 +336,7 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
         g->taps.w = dw;
         g->taps.wf = dwf;
         g->Hs_const = wsum;
+        g->rHs_const = 1.0 / wsum;
     }
 
     // workspaces
@@ -352,6 +355,8 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
         g->Hs = dalloc<double>(g, d.nel);
         launch_fill(d.nel, g->dc, 1.0, g->st);
         launch_filter(d, g->taps, 'D', nullptr, 1.0, g->dc, nullptr, g->Hs, nullptr, nullptr, g->st);
+        g->rHs = dalloc<double>(g, d.nel);
+        launch_recip(d.nel, g->Hs, g->rHs, g->st);
     }
     g->proj_blocks = project_max_blocks();
     g->oc_blocks = oc_max_blocks();
@@ -430,7 +435,7 @@ to_status to_filter(to_grid* g, const double* in, double* out, const double* dpr
     if (in == out) return fail(TO_EINVAL, "out must not alias in");
     TOPO_API_BEGIN
     grid_sync_in(g);
-    launch_filter(g->d, g->taps, (char)g->p.ftBC, g->Hs, g->Hs_const, in, dprj, out, nullptr, nullptr, g->st);
+    launch_filter(g->d, g->taps, (char)g->p.ftBC, g->rHs, g->rHs_const, in, dprj, out, nullptr, nullptr, g->st);
     grid_sync_out(g);
     TOPO_API_END
 }
@@ -480,7 +485,7 @@ to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV
     grid_sync_in(g);
     if (g->p.oc_method == TO_OC_PHYSICAL_VOLUME) {
         TOPO_CUDA(cudaMemsetAsync(g->bar, 0, sizeof(GridBarrier), g->st));
-        launch_oc_filtered(g->d, g->taps, (char)g->p.ftBC, g->Hs, g->Hs_const, x, dc, dV0, g->passive, g->nact,
+        launch_oc_filtered(g->d, g->taps, (char)g->p.ftBC, g->rHs, g->rHs_const, x, dc, dV0, g->passive, g->nact,
                            g->p.move, g->p.volfrac, g->p.ft, g->eta, nullptr, g->beta, g->p.oc_tol, g->p.oc_maxit, g->ocp,
                            g->dV, g->dc, &g->ds->ocf, &g->hs->ocf, g->partials, g->counter, &g->ds->oo, g->st);
     } else {
@@ -555,7 +560,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     s->loop += 1;
     TOPO_CUDA(cudaEventRecord(g->ev_t[0], st));
     // RL.1 physical density: xPhys(act) = xTilde(act), passive keep x
-    launch_filter(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, s->x, nullptr, g->xt, g->passive, s->x, st);
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, s->x, nullptr, g->xt, g->passive, s->x, st);
     if (p.ft > 1) {
         launch_project(d.nel, g->xt, s->xPhys, g->dprj, s->beta, s->eta, p.volfrac, p.ft == 3,
                        p.newton_tol, p.newton_maxit, p.deadline_cycles, g->partials, g->bar,
@@ -584,15 +589,15 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
                        &g->ds->esum, g->partials, g->counter, st);
     launch_dot(d.ndof, g->F, s->U, &g->ds->c, g->partials, g->counter, st);
     launch_dv(d.nel, g->passive, 1.0 / ((double)d.nel * p.volfrac), g->dV, st);
-    launch_filter(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, g->dc, g->dprj, g->dcf, nullptr, nullptr, st);
-    launch_filter(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st);
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dc, g->dprj, g->dcf, nullptr, nullptr, st);
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st);
     TOPO_CUDA(cudaEventRecord(g->ev_t[3], st));
     // RL.4 OC update
     const bool pae_on = p.pae_q0 > 0 && s->loop >= p.pae_q0;
     if (pae_on) pae_before_oc(g, s->x, st);
     if (p.oc_method == TO_OC_PHYSICAL_VOLUME) {
         // the physical field of each candidate, with the step's threshold and sharpness
-        launch_oc_filtered(d, g->taps, (char)p.ftBC, g->Hs, g->Hs_const, s->x, g->dcf, g->dV0, g->passive, g->nact,
+        launch_oc_filtered(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, s->x, g->dcf, g->dV0, g->passive, g->nact,
                            p.move, p.volfrac, p.ft, s->eta, p.ft == 3 ? &g->ds->po.eta : nullptr, s->beta, p.oc_tol,
                            p.oc_maxit, g->ocp, g->dV, g->dc,
                            &g->ds->ocf, &g->hs->ocf, g->partials, g->counter, &g->ds->oo, st);

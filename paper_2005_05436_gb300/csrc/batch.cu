@@ -808,10 +808,11 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
     const int nb_n = b->n_nt, nb_e = b->n_et, tn = b->nty * b->ntx, te = b->ety * b->etx;
     const int ft = p.ft;
     // Each FP32 inner solve restarts from the FP64 residual after at most
-    // INNER_CAP iterations: long FP32 Krylov runs lose orthogonality on
-    // high-contrast designs and can return a correction that raises the FP64
-    // residual; a restarted run still reduces the energy-norm error.
-    const int inner_cap = b->mg ? p.cg_maxit : std::min(p.cg_maxit, INNER_CAP);
+    // inner_maxit iterations (and INNER_CAP with the Jacobi preconditioner):
+    // long FP32 Krylov runs lose orthogonality on high-contrast designs and can
+    // return a correction that raises the FP64 residual; a restarted run still
+    // reduces the energy-norm error.
+    const int inner_cap = std::min(std::min(p.cg_maxit, p.inner_maxit), b->mg ? p.inner_maxit : INNER_CAP);
     const int max_ref = MAX_REFINE;
     cudaStream_t st = b->st;
     captured_launches_reset();
@@ -960,7 +961,8 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
     if (base->precision != TO_MIXED) return api_fail(TO_EINVAL, "batched solve is TO_MIXED (FP32 + FP64 refinement)");
     if (base->ftBC != 'N') return api_fail(TO_EINVAL, "batched filter supports 'N' padding only");
     if (base->ft < 1 || base->ft > 3) return api_fail(TO_EINVAL, "ft must be 1, 2 or 3");
-    if (!(base->inner_rtol > 0.0 && base->inner_rtol < 1.0) || base->cg_maxit < 1 || !(base->cg_rtol > 0.0))
+    if (!(base->inner_rtol > 0.0 && base->inner_rtol < 1.0) || base->cg_maxit < 1 || !(base->cg_rtol > 0.0) ||
+        base->inner_maxit < 1)
         return api_fail(TO_EINVAL, "bad solver tolerances");
     to_batch* b = new to_batch();
     TOPO_BATCH_BEGIN

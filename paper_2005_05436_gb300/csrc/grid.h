@@ -63,6 +63,9 @@ struct to_grid {
     topo::FilterTaps taps{};
     double Hs_const = 1.0;
     double* Hs = nullptr;  // 'D' only
+    // 1/Hs, which the filters multiply by (an FP64 divide is a long sequence at the FP64 rate)
+    double rHs_const = 1.0;
+    double* rHs = nullptr;  // 'D' only
 
     // workspaces
     double *E = nullptr, *xt = nullptr, *dprj = nullptr, *dc = nullptr, *dcf = nullptr;

@@ -69,10 +69,12 @@ template <typename T>
 void launch_modulus(long long n, const double* x, double penal, double E0, double Emin, T* E,
                     cudaStream_t st);
 
-// Forward filter out = (A in)/Hs (dprj == nullptr) or chain rule
-// out = A (dprj * in / Hs). If passive_keep != nullptr (forward only), passive
-// elements take the value of `keep` instead (xPhys(act) = xTilde(act)).
-void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+// Forward filter out = (A in) / Hs (dprj == nullptr) or chain rule
+// out = A (dprj * in / Hs), with the division as a product with rHs = 1/Hs
+// (the array, or rHs_const where it is nullptr). If passive_keep != nullptr
+// (forward only), passive elements take the value of `keep` instead
+// (xPhys(act) = xTilde(act)).
+void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                    const double* in, const double* dprj, double* out, const int8_t* passive,
                    const double* keep, cudaStream_t st);
 
@@ -108,7 +110,7 @@ struct OcfState {
 // (candidate, forward filter, projected volume with the bracket update in the
 // last block); the host checks the phase every four steps. xc, xf: [nEl]
 // scratch; on return x holds the last candidate and out the last lm.
-void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                         double* x, const double* dc, const double* dV0, const int8_t* passive, long long nact,
                         double move, double volfrac, int ft, double eta, const double* eta_dev, double beta,
                         double tol, int maxit, double* ocp, double* xc, double* xf, OcfState* sdev,
@@ -128,6 +130,8 @@ void launch_dot(long long n, const double* a, const double* b, double* out, doub
 void launch_change(long long n, const double* a, double* b, double* out, int copy,
                    double* partials, unsigned* counter, cudaStream_t st);
 void launch_fill(long long n, double* a, double v, cudaStream_t st);
+// out = 1 / in
+void launch_recip(long long n, const double* in, double* out, cudaStream_t st);
 void launch_dv(long long n, const int8_t* passive, double v, double* dV, cudaStream_t st);
 
 // ---- PCG vector kernels (kernels_design.cu) ----

@@ -26,8 +26,8 @@ template void launch_modulus<float>(long long, const double*, double, double, do
 
 // -------------------------------------------------------------- filter --
 
-__global__ void __launch_bounds__(256) k_filter(Dims d, FilterTaps taps, int bcN, const double* __restrict__ Hs,
-                                                double Hs_const, const double* __restrict__ in,
+__global__ void __launch_bounds__(256) k_filter(Dims d, FilterTaps taps, int bcN, const double* __restrict__ rHs,
+                                                double rHs_const, const double* __restrict__ in,
                                                 const double* __restrict__ dprj, double* __restrict__ out,
                                                 const int8_t* __restrict__ passive,
                                                 const double* __restrict__ keep) {
@@ -49,19 +49,29 @@ __global__ void __launch_bounds__(256) k_filter(Dims d, FilterTaps taps, int bcN
         }
         const long long j = jy + (long long)d.nely * (jz + (long long)d.nelz * jx);
         double v = in[j];
-        if (dprj) v = v * dprj[j] / (Hs ? Hs[j] : Hs_const);
+        if (dprj) v = v * dprj[j] * (rHs ? rHs[j] : rHs_const);
         s += taps.w[k] * v;
     }
-    if (!dprj) s = s / (Hs ? Hs[e] : Hs_const);
+    if (!dprj) s = s * (rHs ? rHs[e] : rHs_const);
     if (passive && passive[e] != 0) s = keep[e];
     out[e] = s;
 }
 
-void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                    const double* in, const double* dprj, double* out, const int8_t* passive,
                    const double* keep, cudaStream_t st) {
-    k_filter<<<div_up(d.nel, 256), 256, 0, st>>>(d, taps, bc == 'N', Hs, Hs_const, in, dprj, out,
+    k_filter<<<div_up(d.nel, 256), 256, 0, st>>>(d, taps, bc == 'N', rHs, rHs_const, in, dprj, out,
                                                  passive, keep);
+    TOPO_CHECK_LAUNCH();
+}
+
+__global__ void k_recip(long long n, const double* __restrict__ in, double* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = 1.0 / in[i];
+}
+
+void launch_recip(long long n, const double* in, double* out, cudaStream_t st) {
+    k_recip<<<div_up(n, 256), 256, 0, st>>>(n, in, out);
     TOPO_CHECK_LAUNCH();
 }
 
@@ -321,10 +331,11 @@ __global__ void __launch_bounds__(ONT) k_oc(long long n, double* __restrict__ x,
             }
         }
         if ((l2 - l1) / (l1 + l2) > tol) status = (int)TO_ENOTCONV;
+        const double inv_lm = 1.0 / lmid;
         for (long long i = i0; i < n; i += stride) {
             if (passive && passive[i] != 0) continue;
             const double xi = x[i];
-            x[i] = fmax(fmax(fmin(fmin(ocp[i] / lmid, xi + move), 1.0), xi - move), 0.0);
+            x[i] = fmax(fmax(fmin(fmin(ocp[i] * inv_lm, xi + move), 1.0), xi - move), 0.0);
         }
     } else {
         lmid = 0.0;
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(256) k_ocf_vol(long long n, const double* __re
     }
 }
 
-void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* Hs, double Hs_const,
+void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                         double* x, const double* dc, const double* dV0, const int8_t* passive, long long nact,
                         double move, double volfrac, int ft, double eta, const double* eta_dev, double beta,
                         double tol, int maxit, double* ocp, double* xc, double* xf, OcfState* sdev,
@@ -498,7 +509,7 @@ void launch_oc_filtered(const Dims& d, const FilterTaps& taps, char bc, const do
         for (int k = 0; k < 4; ++k, ++done) {
             k_ocf_cand<<<nbe, 256, 0, st>>>(n, x, ocp, passive, move, sdev, xc);
             TOPO_CHECK_LAUNCH();
-            launch_filter(d, taps, bc, Hs, Hs_const, xc, nullptr, xf, passive, xc, st);
+            launch_filter(d, taps, bc, rHs, rHs_const, xc, nullptr, xf, passive, xc, st);
             k_ocf_vol<<<nbr, 256, 0, st>>>(n, xf, ft, eta, eta_dev, beta, volfrac, tol, maxit, sdev, partials,
                                            counter);
             TOPO_CHECK_LAUNCH();

@@ -566,7 +566,9 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
                 break;
             }
             // the preconditioner is set up once per solve
-            const PcgScalars h = run_pcg<float>(g, sv, P, g->p.inner_rtol, g->p.cg_maxit - iters, true, !prepared);
+            // each inner solve is capped: a stalled FP32 run still hands the FP64 step a direction
+            const PcgScalars h = run_pcg<float>(g, sv, P, g->p.inner_rtol,
+                                                std::min(g->p.inner_maxit, g->p.cg_maxit - iters), true, !prepared);
             prepared = true;
             iters += h.iters;
             if (h.done == 3) {

@@ -59,8 +59,9 @@ def test_zero_load(precision, shape):
 
 @pytest.mark.parametrize("ft", [1, 2])
 def test_filter_only_and_fixed_threshold(ft):
+    # the FP64 Jacobi-PCG floor of these void-region designs sits near 1e-12
     _parity((30, 10, 0), 8, ft=ft, volfrac=0.4, rmin=2.0, beta=4.0, eta=0.45, newton_tol=1e-14, oc_tol=1e-15,
-            cg_rtol=1e-12, cg_maxit=100000)
+            cg_rtol=1e-11, cg_maxit=100000)
 
 
 @pytest.mark.parametrize("volfrac", [0.05, 0.95])
