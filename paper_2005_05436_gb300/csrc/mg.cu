@@ -319,6 +319,62 @@ __global__ void k_stencil_build(Dims d, const T* __restrict__ Kel, T* __restrict
     for (int q = 0; q < Q; ++q) R[(long long)q * d.nnodes + n] = rs[q];
 }
 
+// 3D stencils with one thread per (node, stencil block): block (SB_NODES, 27),
+// each thread sums its block over the (up to 8) shared elements as
+// k_stencil_build does, and nine threads per node then add the 27 blocks in
+// stencil order for R, so S and R are those of k_stencil_build.
+template <typename T>
+struct StencilNodes {
+    static constexpr int v = sizeof(T) == 8 ? 16 : 32;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(27 * StencilNodes<T>::v) k_stencil_build3s(Dims d, const T* __restrict__ Kel,
+                                                                          T* __restrict__ S, T* __restrict__ R) {
+    constexpr int NB = StencilNodes<T>::v, D = 24, DD = D * D, Q = 9;
+    __shared__ T part[27][NB][Q];
+    const int tx = threadIdx.x, s = threadIdx.y;
+    const long long n = (long long)blockIdx.x * NB + tx;
+    const bool valid = n < d.nnodes;
+    T blk[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) blk[q] = T(0);
+    if (valid) {
+        const int iy = (int)(n % d.nny);
+        const long long t = n / d.nny;
+        const int iz = (int)(t % d.nnz);
+        const int ix = (int)(t / d.nnz);
+        const int dx = s / 9 - 1, dz = (s / 3) % 3 - 1, dy = s % 3 - 1;
+        const int mx = ix + dx, my = iy + dy, mz = iz + dz;
+        if (mx >= 0 && mx < d.nnx && my >= 0 && my < d.nny && mz >= 0 && mz < d.nnz) {
+            for (int o = 0; o < 8; ++o) {
+                const int exo = (o >> 2) & 1, ezo = (o >> 1) & 1, eyo = o & 1;
+                const int ex = ix - 1 + exo, ey = iy - 1 + eyo, ez = iz - 1 + ezo;
+                if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) continue;
+                const int bx = mx - ex, brow = my - ey, bz = mz - ez;
+                if (bx < 0 || bx > 1 || brow < 0 || brow > 1 || bz < 0 || bz > 1) continue;
+                const int Ln = local_node(1 - exo, eyo, 1 - ezo);
+                const int Lm = local_node(bx, 1 - brow, bz);
+                const T* Ke = Kel + (ey + (long long)d.nely * (ez + (long long)d.nelz * ex)) * DD;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) blk[c * 3 + k] += Ke[(Ln * 3 + c) * D + Lm * 3 + k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) S[((long long)s * Q + q) * d.nnodes + n] = blk[q];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) part[s][tx][q] = blk[q];
+    __syncthreads();
+    if (s < Q && valid) {
+        T rs = T(0);
+        for (int k = 0; k < 27; ++k) rs += part[k][tx][s];
+        R[(long long)s * d.nnodes + n] = rs;
+    }
+}
+
 // l1-Jacobi smoother weights: dinv = 1 / sum_j |A_ij| (row sums of absolute
 // values), so that lambda_max(D^-1 A) <= 1 (Gershgorin) for any modulus
 // contrast and the damped sweep contracts; coarse DOFs whose diagonal is zero
@@ -1109,7 +1165,12 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
                                                                         nullptr, mg->lev[l - 1].Kel, nullptr, L.Kel);
         }
         TOPO_CHECK_LAUNCH();
-        k_stencil_build<T, DIM><<<div_up(L.d.nnodes, 128), 128, 0, st>>>(L.d, L.Kel, L.S, L.R);
+        if (DIM == 3) {
+            constexpr int NB = StencilNodes<T>::v;
+            k_stencil_build3s<T><<<div_up(L.d.nnodes, NB), dim3(NB, 27), 0, st>>>(L.d, L.Kel, L.S, L.R);
+        } else {
+            k_stencil_build<T, DIM><<<div_up(L.d.nnodes, 128), 128, 0, st>>>(L.d, L.Kel, L.S, L.R);
+        }
         TOPO_CHECK_LAUNCH();
         if (l > 0) {
             k_stencil_diag<T, DIM><<<div_up(L.d.nnodes, 256), 256, 0, st>>>(L.d, L.S, L.dinv, L.fixed);
