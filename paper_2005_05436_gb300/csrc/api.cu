@@ -508,6 +508,7 @@ to_status to_solve(to_grid* g, const double* xPhys, const double* F, double* U, 
     to_status st = TO_OK;
     TOPO_API_BEGIN
     grid_sync_in(g);
+    solver_discard_setup(g);
     launch_modulus<double>(g->d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, g->E, g->st);
     st = solve_state(g, F ? F : g->F, U, &si);
     grid_sync_out(g);
@@ -551,6 +552,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     to_iter_info it{};
     TOPO_API_BEGIN
     grid_sync_in(g);
+    solver_discard_setup(g);
     const Dims& d = g->d;
     const to_params& p = g->p;
     cudaStream_t st = g->st;

@@ -130,6 +130,8 @@ void solver_free(to_grid* g);
 // Solve K(E)(free, free) U = b with g->E already set; U: warm start in, solution out.
 // Preconditioner set-up for the modulus in g->E on the grid stream; the next solve_state skips it.
 void solver_setup(to_grid* g);
+// Forget a set-up that no solve consumed (an entry point that failed after solver_setup).
+void solver_discard_setup(to_grid* g);
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info);
 // Tensor-core FP32 fine operator (ku_tc.cu); modes as launch_fine_op.
 void launch_fine_op_tc(const to_grid* g, int mode, const float* E, const float* u, const float* r, const float* dinv,

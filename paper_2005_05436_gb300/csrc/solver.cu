@@ -495,6 +495,10 @@ void solver_setup(to_grid* g) {
     sv->setup_done = true;
 }
 
+void solver_discard_setup(to_grid* g) {
+    if (g->solver) g->solver->setup_done = false;
+}
+
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info) {
     Solver* sv = g->solver;
     const Dims& d = g->d;

@@ -269,6 +269,20 @@ void warm_free(to_grid* g) {
     g->warm = nullptr;
 }
 
+// Makes the grid stream wait for everything enqueued on the warm-start stream,
+// also when the warm start ends by an exception (the grid stream then never
+// runs ahead of kernels still reading U or the grid's buffers).
+struct AuxJoin {
+    WarmWS* w;
+    cudaStream_t st;
+    bool done = false;
+    ~AuxJoin() {
+        if (done) return;
+        cudaEventRecord(w->join, w->aux);
+        cudaStreamWaitEvent(st, w->join, 0);
+    }
+};
+
 // U <- argmin of the energy over span{U, U_h}; E(xPhys) in g->E (FP64).
 void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy) {
     WarmWS* w = warm_ws(g);
@@ -279,6 +293,7 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     // the grid stream meanwhile (the two share no buffer that either writes).
     TOPO_CUDA(cudaEventRecord(w->fork, st));
     TOPO_CUDA(cudaStreamWaitEvent(ax, w->fork, 0));
+    AuxJoin joiner{w, st};
     TOPO_CUDA(cudaEventRecord(w->e0, ax));
     features(g, w, xPhys, w->x, ax);
     net_forward_on(g->net, w->x, 1, w->D, w->H, w->W, w->y, ax);
@@ -325,6 +340,7 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     TOPO_CUDA(cudaEventRecord(w->e1, ax));
     TOPO_CUDA(cudaEventRecord(w->join, ax));
     TOPO_CUDA(cudaStreamWaitEvent(st, w->join, 0));
+    joiner.done = true;
     TOPO_CUDA(cudaEventSynchronize(w->e1));
     float t = 0.f;
     TOPO_CUDA(cudaEventElapsedTime(&t, w->e0, w->e1));

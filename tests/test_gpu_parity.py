@@ -147,6 +147,10 @@ def test_oc_update(shape, tol):
     xt = to_cuda(x)
     lm = g.oc_update(xt, to_cuda(dc), to_cuda(dV0))
     assert abs(lm - lm_ref) <= max(tol, 1e-14) * 4 * lm_ref
+    # the same bisection decisions give the same midpoints up to the rounding of the initial
+    # bracket; one different decision (e.g. a wrongly trusted FP32 screen) moves lm by at least
+    # half the bracket width at that step
+    assert abs(lm - lm_ref) <= 1e-12 * lm_ref, (lm, lm_ref)
     assert rel(xt.cpu().numpy(), xr) <= (1e-12 if tol < 1e-10 else 1e-3)
     if tol < 1e-10:
         assert abs(xt.mean().item() - 0.4) <= 1e-10
