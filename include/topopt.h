@@ -120,9 +120,10 @@ typedef struct to_params {
     int32_t pae_m;          /* history columns m_r, 1..4 (4) */
     double pae_alpha;       /* damping of the other steps, x += alpha r (0.9) */
     double pae_zeta;        /* damping of the extrapolated step (1) */
-    int32_t inner_maxit;    /* TO_MIXED: iteration cap of each FP32 inner solve (2000); a stalled
-                               inner solve hands its iterate to the FP64 flexible-CG step, whose
-                               exact line search still lowers the energy */
+    int32_t inner_maxit;    /* TO_MIXED (to_step, to_solve and the batched solve): iteration cap of
+                               each FP32 inner solve (2000); a stalled inner solve hands its
+                               iterate to the FP64 flexible-CG step, whose exact line search still
+                               lowers the energy. >= 1, else TO_EINVAL */
     int32_t _pad3;
 } to_params;
 
