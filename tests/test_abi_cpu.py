@@ -54,10 +54,12 @@ def test_params_defaults_follow_the_paper(lib):
     assert chr(p.ftBC) == "N" and p.ft == 3
     assert (p.penal_cnt.istart, p.penal_cnt.maxpar, p.penal_cnt.isteps, p.penal_cnt.delta) == (1, 3.0, 25, 0.25)
     assert (p.newton_tol, p.oc_tol) == (1e-6, 1e-4)
+    assert (p.inner_rtol, p.inner_maxit) == (1e-3, 2000)
 
 
 @pytest.mark.parametrize("field,value", [("dim", 4), ("nelx", 0), ("volfrac", 1.5), ("ft", 7),
-                                         ("ftBC", ord("X")), ("rmin", -1.0), ("nelz", 3)])
+                                         ("ftBC", ord("X")), ("rmin", -1.0), ("nelz", 3), ("inner_maxit", 0),
+                                         ("oc_method", 7), ("pae_m", 5), ("inner_rtol", 1.0)])
 def test_invalid_params_rejected_on_host(lib, field, value):
     from paper_2005_05436_gb300 import _lib as L
     p = L.default_params(2, 8, 4)
