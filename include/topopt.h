@@ -20,7 +20,10 @@
  *  - Work is enqueued on the stream given to to_init_grid (NULL = the legacy
  *    default stream). Entry points that return host scalars (pointers marked
  *    "host out") synchronise that stream before returning; the others are
- *    asynchronous.
+ *    asynchronous. Inside to_step and to_solve the handle also uses private
+ *    streams (the learned warm start, the coarsest multigrid factorization);
+ *    they fork from and join back into that stream, so a caller sees all of
+ *    their work ordered on it.
  *  - Layouts follow the paper's column-major numbering (Sec. 3, PRE.2),
  *    0-based: node n = iy + (nely+1)(iz + (nelz+1) ix), element
  *    e = iy + nely (iz + nelz ix), DOF = dim*n + c with c = 0 (X, along ix),
