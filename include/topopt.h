@@ -21,9 +21,10 @@
  *    default stream). Entry points that return host scalars (pointers marked
  *    "host out") synchronise that stream before returning; the others are
  *    asynchronous. Inside to_step and to_solve the handle also uses private
- *    streams (the learned warm start, the coarsest multigrid factorization);
- *    they fork from and join back into that stream, so a caller sees all of
- *    their work ordered on it.
+ *    streams: the learned warm start forks from that stream and is joined
+ *    back before the call's later work; the coarsest multigrid factorization
+ *    touches only buffers of the handle and is joined before the first
+ *    V-cycle (or the next set-up) that uses it, and by to_destroy.
  *  - Layouts follow the paper's column-major numbering (Sec. 3, PRE.2),
  *    0-based: node n = iy + (nely+1)(iz + (nelz+1) ix), element
  *    e = iy + nely (iz + nelz ix), DOF = dim*n + c with c = 0 (X, along ix),
