@@ -320,16 +320,39 @@ def solve_direct(g: Grid, Ke, E, F, fixed):
     return U
 
 
-def solve_pcg(g: Grid, Ke, E, F, fixed, rtol=1e-8, maxit=100000, U0=None):
+def _row_blocks_matvec(A, threads):
+    """y = A x with the rows of the CSR matrix A split into `threads` blocks, one
+    thread each (scipy's CSR product releases the GIL). Every row is summed by
+    the same routine in the same order as the one-block product, so the result
+    is bitwise that of A @ x; only the execution is parallel."""
+    if threads <= 1:
+        return lambda x: A @ x
+    from concurrent.futures import ThreadPoolExecutor
+    n = A.shape[0]
+    cuts = [n * k // threads for k in range(threads + 1)]
+    blocks = [A[cuts[k]:cuts[k + 1]] for k in range(threads)]
+    pool = ThreadPoolExecutor(threads)
+
+    def mv(x):
+        out = np.empty(n)
+        for k, y in enumerate(pool.map(lambda B: B @ x, blocks)):
+            out[cuts[k]:cuts[k + 1]] = y
+        return out
+    return mv
+
+
+def solve_pcg(g: Grid, Ke, E, F, fixed, rtol=1e-8, maxit=100000, U0=None, threads=1):
     """Jacobi-preconditioned CG on K(free, free) (used where a direct solve does
-    not fit). Returns (U, iterations, relative residual)."""
+    not fit). threads > 1 runs the matrix products on that many host threads
+    (bitwise the same iterates). Returns (U, iterations, relative residual)."""
     K = full_from_lower(assemble_lower(g, Ke, E))
     free = np.nonzero(~fixed.astype(bool))[0]
     Kff = K[free][:, free].tocsr()
+    Kmv = _row_blocks_matvec(Kff, threads)
     b = F[free]
     x = np.zeros(len(free)) if U0 is None else np.array(U0[free], float)
     dinv = 1.0 / Kff.diagonal()
-    r = b - Kff @ x
+    r = b - Kmv(x)
     bn = np.linalg.norm(b)
     z = dinv * r
     p = z.copy()
@@ -337,7 +360,7 @@ def solve_pcg(g: Grid, Ke, E, F, fixed, rtol=1e-8, maxit=100000, U0=None):
     it = 0
     rel = np.linalg.norm(r) / bn if bn > 0 else 0.0
     while rel > rtol and it < maxit:
-        Ap = Kff @ p
+        Ap = Kmv(p)
         alpha = rz / (p @ Ap)
         x += alpha * p
         r -= alpha * Ap
@@ -767,6 +790,7 @@ class Params:
     pae_zeta: float = 1.0
     solver: str = "direct"
     cg_rtol: float = 1e-10
+    threads: int = 1              # host threads of the PCG matrix products (same iterates for any count)
 
     @classmethod
     def parity(cls, **kw):
@@ -830,7 +854,7 @@ def design_step(p: Params, s: State, F, fixed, passive=None, Ke=None):
     if p.solver == "direct":
         U = solve_direct(g, Ke, E, F, fixed)
     else:
-        U, n_cg, _ = solve_pcg(g, Ke, E, F, fixed, rtol=p.cg_rtol, U0=s.U)
+        U, n_cg, _ = solve_pcg(g, Ke, E, F, fixed, rtol=p.cg_rtol, U0=s.U, threads=p.threads)
     s.U = U
     # RL.3 sensitivities and back-filter
     dc, c, _ = sensitivity(g, Ke, xphys, U, F, s.penal, p.E0, p.Emin, act)

@@ -63,3 +63,27 @@ def design_field(shape, seed, rmin=2.5, beta=8.0, lo=0.0):
     z = (x - np.median(x)) / max(np.std(x), 1e-12)   # unit-variance coherent field
     x = O.prj(0.5 + 0.25 * z, 0.5, beta)              # mostly solid or void, smooth edges
     return np.clip(x, lo, 1.0)
+
+
+def max_abs(a, b):
+    """Largest elementwise |a - b| (0 for empty arrays)."""
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.max(np.abs(a - b))) if b.size else 0.0
+
+
+def assert_design_matches(tag, got, ref, xphys, xphys_ref, x, x_ref, tol=1e-8, lm_rtol=1e-7):
+    """One design iteration of the CUDA path against the oracle's.
+
+    x and xPhys lie in [0, 1], so besides the normwise difference every element
+    must lie within ``tol`` of the oracle's (an error confined to a boundary tile
+    or a ragged edge cannot hide under the norm). ch and V are bounded by the
+    elementwise error (|d ch| <= 2 max|d xPhys|, |d V| <= max|d xPhys|); the OC
+    multiplier follows dc, which tracks c, so it gets a relative bound."""
+    e_p, e_x = max_abs(xphys, xphys_ref), max_abs(x, x_ref)
+    assert rel(xphys, xphys_ref) <= tol and e_p <= tol, (tag, "xPhys", rel(xphys, xphys_ref), e_p)
+    assert rel(x, x_ref) <= tol and e_x <= tol, (tag, "x", rel(x, x_ref), e_x)
+    assert abs(got["ch"] - ref["ch"]) <= 2 * tol, (tag, "ch", got["ch"], ref["ch"])
+    assert abs(got["V"] - ref["V"]) <= tol, (tag, "V", got["V"], ref["V"])
+    assert abs(got["lm"] - ref["lm"]) <= lm_rtol * abs(ref["lm"]), (tag, "lm", got["lm"], ref["lm"])
+    return max(e_p, e_x)

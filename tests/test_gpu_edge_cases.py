@@ -9,7 +9,7 @@ import pytest
 
 from oracle import topopt_oracle as O
 from paper_2005_05436_gb300 import inputs as I
-from tests._util import make_grid, rel, to_cuda
+from tests._util import assert_design_matches, make_grid, max_abs, rel, to_cuda
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -34,8 +34,7 @@ def _parity(shape, n_iter, F=None, fixed=None, tol_x=1e-8, **kw):
     for k in range(n_iter):
         ref = O.design_step(op, s, F, fixed, None, Ke)
         got = d.step()
-        assert rel(d.xPhys.cpu().numpy(), s.xphys) <= tol_x, (k, rel(d.xPhys.cpu().numpy(), s.xphys))
-        assert rel(d.x.cpu().numpy(), s.x) <= tol_x, k
+        assert_design_matches(k, got, ref, d.xPhys.cpu().numpy(), s.xphys, d.x.cpu().numpy(), s.x, tol=tol_x)
         assert abs(got["c"] - ref["c"]) <= 1e-8 * max(abs(ref["c"]), 1e-300), (k, got["c"], ref["c"])
         assert abs(got["V"] - ref["V"]) <= 1e-10
         infos.append((got, ref))
@@ -100,6 +99,8 @@ def test_zero_load_instance_in_a_batch():
             ref = O.design_step(ops[k], states[k], q.F, q.fixed, None, Ke)
             sl = slice(b.el_off[k], b.el_off[k + 1])
             assert rel(x[sl], states[k].x) <= 1e-8, (it, k)
+            assert max_abs(x[sl], states[k].x) <= 1e-8, (it, k)
+            assert abs(res["lm"][k] - ref["lm"]) <= 1e-7 * abs(ref["lm"]), (it, k)
             assert abs(res["c"][k] - ref["c"]) <= 1e-8 * max(abs(ref["c"]), 1e-300), (it, k)
         assert res["c"][1] == 0.0 and res["lm"][1] == 0.0
         sl1 = slice(b.el_off[1], b.el_off[2])

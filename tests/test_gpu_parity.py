@@ -12,7 +12,7 @@ import pytest
 
 from oracle import topopt_oracle as O
 from paper_2005_05436_gb300 import inputs as I
-from tests._util import make_grid, problem, rel, simp_field, to_cuda
+from tests._util import assert_design_matches, make_grid, max_abs, problem, rel, simp_field, to_cuda
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -156,17 +156,35 @@ def test_oc_update(shape, tol):
         assert abs(xt.mean().item() - 0.4) <= 1e-10
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "gmg"])
 @pytest.mark.parametrize("shape", [(60, 20, 0), (30, 7, 0), (12, 6, 6), (7, 5, 3)])
-def test_solve_against_direct(shape):
-    g, F, fixed = make_grid(shape, penal=3.0, cg_rtol=1e-9, cg_maxit=200000)
+def test_solve_against_direct(shape, precond):
+    """FP64 PCG against the oracle's banded Cholesky solve: U within 1e-8
+    normwise, c = F^T U within 1e-8, at a relative residual of 1e-12 or, where
+    the design's FP64 residual floor is higher, 4 times that floor. The floor is
+    the relative residual ||F - K U_direct|| / ||F|| of the oracle's own direct
+    solution: no FP64 method gets far below it (measured on these designs:
+    1.0e-9 at 60x20 and 1.7e-9 at 30x7 in 2D, where void elements at E = 1.2e-4
+    make plane-stress K very ill-conditioned; 2e-13 and 3e-13 in 3D)."""
+    from paper_2005_05436_gb300 import TO_PC_GMG, TO_PC_JACOBI
     og = O.Grid(*shape)
     Ke = O.element_stiffness(og.dim)
-    xp = np.clip(simp_field(g.nel, 12), 0.05, 1)
-    Ud = O.solve_direct(og, Ke, O.simp_modulus(xp, 3.0), F, fixed)
+    F, fixed = problem(shape)
+    xp = np.clip(simp_field(og.nel, 12), 0.05, 1)
+    E = O.simp_modulus(xp, 3.0)
+    Ud = O.solve_direct(og, Ke, E, F, fixed)
+    res = O.full_from_lower(O.assemble_lower(og, Ke, E)) @ Ud - F
+    res[fixed.astype(bool)] = 0.0
+    floor = np.linalg.norm(res) / np.linalg.norm(F)
+    rtol = max(1e-12, 4.0 * floor)
+    if og.dim == 3:
+        assert rtol <= 1.2e-12, floor  # the 3D designs keep (about) the original target
+    g, _, _ = make_grid(shape, penal=3.0, cg_rtol=rtol, cg_maxit=200000,
+                        precond=TO_PC_GMG if precond == "gmg" else TO_PC_JACOBI)
     U = torch.zeros(g.ndof, dtype=torch.float64, device="cuda")
     info = g.solve(to_cuda(xp), U)
-    assert info.rel_res <= 1e-9
-    assert rel(U.cpu().numpy(), Ud) <= 1e-7
+    assert info.rel_res <= rtol, (info.rel_res, rtol)
+    assert rel(U.cpu().numpy(), Ud) <= 1e-8, rel(U.cpu().numpy(), Ud)
     c_gpu = float(np.dot(F, U.cpu().numpy()))
     assert abs(c_gpu - F @ Ud) <= 1e-8 * abs(F @ Ud)
 
@@ -208,9 +226,8 @@ def _run_parity(shape, n_iter, **kw):
         ref = O.design_step(op, s, F, fixed, None, Ke)
         got = d.step()
         assert got["loop"] == ref["loop"]
-        e_x = rel(d.xPhys.cpu().numpy(), s.xphys)
-        worst = max(worst, e_x)
-        assert e_x <= 1e-8, (k, e_x)
+        worst = max(worst, assert_design_matches(k, got, ref, d.xPhys.cpu().numpy(), s.xphys,
+                                                 d.x.cpu().numpy(), s.x))
         assert abs(got["c"] - ref["c"]) <= 1e-8 * abs(ref["c"]), (k, got["c"], ref["c"])
         assert abs(got["eta"] - ref["eta"]) <= 1e-9
         assert got["penal"] == ref["penal"] and got["beta"] == ref["beta"]
@@ -326,6 +343,56 @@ def test_design_iterations_mbb_60x20_parity():
 def test_design_iterations_cantilever_parity():
     _run_parity((12, 6, 6), 20, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0,
                 newton_tol=1e-14, oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=200000)
+
+
+_TRAJECTORIES = {}
+
+
+def _oracle_trajectory(shape, n_iter):
+    """The oracle's first n_iter design iterations of the 3D cantilever in parity
+    mode (volfrac 0.12, penal 3, rmin sqrt(3), ft 3, beta 2), computed once per
+    module and shared by the GPU arms below."""
+    key = (shape, n_iter)
+    if key not in _TRAJECTORIES:
+        op = O.Params.parity(nelx=shape[0], nely=shape[1], nelz=shape[2], volfrac=0.12, penal=3.0,
+                             rmin=math.sqrt(3), beta=2.0, penal_cnt=(1, 3.0, 25, 0.0),
+                             beta_cnt=(1, 2.0, 25, 0.0))
+        F, fixed = problem(shape)
+        s = O.initial_state(op)
+        Ke = O.element_stiffness(3)
+        traj = []
+        for _ in range(n_iter):
+            ref = O.design_step(op, s, F, fixed, None, Ke)
+            traj.append((dict(ref), s.xphys.copy(), s.x.copy()))
+        _TRAJECTORIES[key] = traj
+    return _TRAJECTORIES[key]
+
+
+@pytest.mark.parametrize("arm", ["fp64_jacobi", "fp64_gmg", "mixed_gmg"])
+def test_design_iterations_cantilever_24x12x12_parity(arm):
+    """20 design iterations of the 24x12x12 cantilever (several Walsh tiles along
+    y and z, four multigrid levels) against the oracle's banded-Cholesky run:
+    xPhys and x elementwise within 1e-8, c within 1e-8, ch, V, eta and the OC
+    multiplier. The mixed arm (FP32 inner PCG, FP64 flexible-CG refinement) is
+    held to the same bounds: its FP64 residual is driven to the same 1e-12."""
+    from paper_2005_05436_gb300 import TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI
+    from paper_2005_05436_gb300.topopt import Design
+    shape, n_iter = (24, 12, 12), 20
+    traj = _oracle_trajectory(shape, n_iter)
+    prec = TO_MIXED if arm.startswith("mixed") else TO_FP64
+    pc = TO_PC_JACOBI if arm.endswith("jacobi") else TO_PC_GMG
+    g, F, fixed = make_grid(shape, volfrac=0.12, penal=3.0, rmin=math.sqrt(3), beta=2.0, newton_tol=1e-14,
+                            oc_tol=1e-15, cg_rtol=1e-12, cg_maxit=200000, precision=prec, precond=pc,
+                            penal_cnt=(1, 3.0, 25, 0.0), beta_cnt=(1, 2.0, 25, 0.0))
+    d = Design(g, to_cuda(I.initial_design(g.nel, 0.12)))
+    for k, (ref, xphys_ref, x_ref) in enumerate(traj):
+        got = d.step()
+        assert got["loop"] == ref["loop"]
+        assert got["rel_res"] <= 1e-12, (k, got["rel_res"])
+        assert_design_matches(k, got, ref, d.xPhys.cpu().numpy(), xphys_ref, d.x.cpu().numpy(), x_ref)
+        assert abs(got["c"] - ref["c"]) <= 1e-8 * abs(ref["c"]), (k, got["c"], ref["c"])
+        assert abs(got["eta"] - ref["eta"]) <= 1e-9, (k, got["eta"], ref["eta"])
+    g.close()
 
 
 def test_design_iterations_with_continuation_and_dirichlet_filter():

@@ -35,15 +35,23 @@ def test_q4_ke_equals_paper_coefficients():
     np.testing.assert_allclose(O.from_lower_vector(ref, 8), Ke, rtol=0, atol=1e-15)
 
 
-def test_h8_ke_first_column_and_diagonal_equal_paper():
-    """Appendix C prints Ke = (a + nu b) / ((1 + nu)(2 nu - 1) 144)."""
+def test_h8_ke_equals_paper_coefficients():
+    """Appendix C prints all 300 lower-triangle coefficients,
+    Ke = (a + nu b) / ((1 + nu)(2 nu - 1) 144): the oracle's quadrature Ke must
+    reproduce every one of them (an off-diagonal sign or index error that kept
+    symmetry and the rigid modes would still fail here)."""
     g = _golden()
+    assert len(g["h8_a"]) == len(g["h8_b"]) == 24 * 25 // 2
     s = 1.0 / ((1 + NU) * (2 * NU - 1) * 144)
-    col = s * (np.array(g["h8_first_column_a"]) + NU * np.array(g["h8_first_column_b"]))
+    ref = s * (np.array(g["h8_a"], float) + NU * np.array(g["h8_b"], float))
     Ke = O.element_stiffness(3, NU)
-    np.testing.assert_allclose(Ke[:, 0], col, rtol=0, atol=1e-15)
-    diag = s * (g["h8_diagonal_a"] + NU * g["h8_diagonal_b"])
-    np.testing.assert_allclose(np.diag(Ke), diag, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.lower_vector(Ke), ref, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.from_lower_vector(ref, 24), Ke, rtol=0, atol=1e-15)
+    # the printed matrix also holds for another Poisson ratio (a and b separately)
+    for nu in (0.0, 0.45):
+        s2 = 1.0 / ((1 + nu) * (2 * nu - 1) * 144)
+        ref2 = s2 * (np.array(g["h8_a"], float) + nu * np.array(g["h8_b"], float))
+        np.testing.assert_allclose(O.lower_vector(O.element_stiffness(3, nu)), ref2, rtol=0, atol=1e-14)
 
 
 def _rigid_modes(dim):
@@ -303,6 +311,19 @@ def test_pcg_matches_direct():
     Up, it, rel = O.solve_pcg(g, Ke, E, F, fixed, rtol=1e-13)
     assert rel <= 1e-13
     assert np.linalg.norm(Up - Ud) <= 1e-7 * np.linalg.norm(Ud)
+
+
+def test_pcg_threaded_products_are_bitwise_the_same():
+    """The row-block threaded matrix product changes only the execution: the
+    iterates, iteration count and residual equal the one-thread run bit for bit."""
+    g = O.Grid(10, 5, 5)
+    Ke = O.element_stiffness(3, NU)
+    F, fixed = I.cantilever_3d(10, 5, 5)
+    E = O.simp_modulus(I.random_design(g.nel, 4), 3.0)
+    U1, it1, rel1 = O.solve_pcg(g, Ke, E, F, fixed, rtol=1e-10)
+    U4, it4, rel4 = O.solve_pcg(g, Ke, E, F, fixed, rtol=1e-10, threads=4)
+    assert it1 == it4 and rel1 == rel4
+    np.testing.assert_array_equal(U1, U4)
 
 
 # ----------------------------------------------------------------- filter --
