@@ -97,11 +97,14 @@ typedef struct to_params {
     double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3) */
     double mg_omega;        /* GMG l1-Jacobi smoother weight (1.0) */
     int32_t mg_nu;          /* GMG pre- and post-smoothing sweeps per level (2) */
-    int32_t ku_impl;        /* 3D stiffness operator: 0 auto (= 3); 1 node-centric gather with the
-                               dense 24x24 Ke (CUDA cores, FP32 and FP64); 2 tensor cores for the
-                               FP32 fine operator of TO_MIXED (tcgen05 TF32 with split operands;
-                               FP64 products as 3); 3 element tiles with Ke factored in the Walsh
-                               basis of the element corners (CUDA cores, FP32 and FP64) */
+    int32_t ku_impl;        /* 3D stiffness operator: 0 auto (= 3);
+                               1 node-centric gather with the dense 24x24 Ke (CUDA cores, FP32 and
+                               FP64); 2 tensor cores for the FP32 fine operator of TO_MIXED (tcgen05
+                               TF32 with split operands; FP64 products as 3); 3 element tiles with
+                               Ke factored in the Walsh basis of the element corners (CUDA cores,
+                               FP32 and FP64); 4 as 3, with the FP32 products computed for two
+                               elements per thread in paired FP32 instructions (FP64 products as 3;
+                               TO_EINVAL if no tile shape fits the grid) */
     int32_t loop_mode;      /* PCG loop: 0 one CUDA-graph launch with a conditional WHILE node
                                (default); 1 the same kernels launched from a host loop, polled
                                every 8 iterations (for profilers that do not follow
@@ -262,14 +265,21 @@ to_status to_sensitivity(to_grid* g, const double* xPhys, const double* U, doubl
  * with lm = sqrt(lambda) found by bisection on [0, lambda#] (Eq. 17) until
  * (l2 - l1)/(l1 + l2) <= oc_tol, testing mean(x) > volfrac. The upper bracket
  * is doubled while it is still feasible-violating. x[nEl] in/out, dc, dV0 [nEl];
- * lm_out (host out, may be NULL). */
+ * lm_out (host out, may be NULL). Returns TO_ENOTCONV, with x and lm_out
+ * holding the last candidate, when the search stops at oc_maxit steps before
+ * the bracket meets oc_tol. */
 to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV0,
                        double* lm_out);
 
 /* One full design iteration (Sec. 3, RL.1-RL.4): filter, projection with
  * volume-preserving eta (ft = 3), ch, state solve (warm-started from s->U),
  * sensitivities, chain rule, OC update and continuation. s (host in/out,
- * device arrays inside), info (host out, may be NULL). */
+ * device arrays inside), info (host out, may be NULL). The iteration is
+ * completed in every case below and info->status repeats the return value:
+ * TO_ENAN when the compliance is not finite, the solve's TO_ENOTCONV when it
+ * stopped above cg_rtol, TO_ENOTCONV when the OC multiplier search stopped at
+ * oc_maxit before meeting oc_tol, TO_ETIMEOUT when a grid-barrier wait passed
+ * deadline_cycles (then s and info are not updated). */
 to_status to_step(to_grid* g, to_state* s, to_iter_info* info);
 
 /* OC update that allocates no device memory. The paper has no counterpart: this
@@ -282,15 +292,24 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info);
  * passive[nel] mask (device; NULL = all active) with the given volfrac, move,
  * oc_tol, oc_maxit and deadline_cycles, on `stream` (a cudaStream_t, NULL =
  * default stream); lm_out (host out, may be NULL) receives lm = sqrt(lambda).
- * Scratch: one file-scope device array of 8,651,520 bytes that every GPU which
- * loads the library holds until the process exits; it bounds nel to
- * 1,048,576 elements (larger nel returns TO_EINVAL). The array keeps the last
- * call's contents; the call clears what must start at zero. All calls share
- * the array, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them. The first call on a device resolves the
- * array's device address with that device current; make that first call
- * before any stream capture. The call synchronises `stream` before returning.
- * It calls no cudaMalloc, cudaFree or allocating library routine. */
+ * Scratch: one file-scope device array of 8,651,520 bytes; it bounds nel to
+ * 1,048,576 elements (larger nel returns TO_EINVAL). CUDA loads the module
+ * that holds the array lazily, so the array is reserved on a device by the
+ * first call there (or when the context is created, under
+ * CUDA_MODULE_LOADING=EAGER) and held until the process exits; that first call
+ * may also synchronise the device. Make one call early on each device, before
+ * handing its free memory to another allocator and before any stream capture:
+ * the first call also resolves the array's device address with that device
+ * current and caches it. A cudaDeviceReset makes the cached address stale: do
+ * not use this entry on a device after resetting it in the same process. The
+ * array keeps the last call's contents; the call clears what must start at
+ * zero. All calls share the array, so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them. The call synchronises
+ * `stream` before returning. Apart from that first module load it calls no
+ * cudaMalloc, cudaFree or allocating library routine. Errors: TO_EINVAL for
+ * a NULL array, nel out of range, bad scalars or no active element;
+ * TO_ETIMEOUT when a grid-barrier wait passed deadline_cycles; TO_ENOTCONV
+ * as to_oc_update; each with a message in to_last_error(). */
 to_status to_oc_update_noalloc(int64_t nel, double* x, const double* dc, const double* dV0,
                                const int8_t* passive, double volfrac, double move, double oc_tol,
                                int32_t oc_maxit, int64_t deadline_cycles, void* stream,

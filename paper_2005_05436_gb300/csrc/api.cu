@@ -148,7 +148,7 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->mg_coarse_every >= 1 && p->mg_coarse_every <= 1000, "mg_coarse_every must be in [1, 1000]");
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
-    TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 3, "ku_impl must be 0, 1, 2 or 3");
+    TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 4, "ku_impl must be 0, 1, 2, 3 or 4");
     TOPO_REQUIRE(p->pae_q0 >= 0 && p->pae_q >= 1 && p->pae_m >= 1 && p->pae_m <= 4 && p->pae_alpha > 0.0 &&
                      p->pae_alpha <= 1.0 && p->pae_zeta >= 0.0 && p->pae_zeta <= 1.0,
                  "Anderson extrapolation: pae_q0 >= 0, pae_q >= 1, pae_m in 1..4, pae_alpha in (0, 1], "
@@ -269,6 +269,10 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
                                (float)w.f, (float)w.g, (float)w.pmq, (float)w.q};
     }
     g->node_centric = p->ku_impl == 1;
+    if (d.dim == 3 && p->ku_impl == 4) {
+        TOPO_REQUIRE(walsh_pair_supported(d), "no element-pair tile shape fits this grid (ku_impl 4)");
+        g->walsh_pair = true;
+    }
     g->Ke_host = K;
     g->Ke_dev = dalloc<double>(g, K.size());
     TOPO_CUDA(cudaMemcpyAsync(g->Ke_dev, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
@@ -499,6 +503,9 @@ to_status to_oc_update(to_grid* g, double* x, const double* dc, const double* dV
     grid_sync_out(g);
     if (g->hbar.error) return fail(TO_ETIMEOUT, "OC: grid barrier deadline passed");
     if (lm_out) *lm_out = g->hs->oo.lm;
+    if (g->hs->oo.status != TO_OK)
+        return fail(TO_ENOTCONV, "OC: the multiplier search stopped at oc_maxit before meeting oc_tol "
+                                 "(x holds the last candidate)");
     TOPO_API_END
 }
 
@@ -656,11 +663,14 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     it.beta = s->beta;
     it.eta = s->eta;
     it.status = (int)sst;
+    if (it.status == TO_OK && h.oo.status != TO_OK) it.status = TO_ENOTCONV;
     if (!std::isfinite(it.c)) it.status = TO_ENAN;
     grid_sync_out(g);
     if (info) *info = it;
     if (it.status == TO_ENAN) return fail(TO_ENAN, "compliance is not finite");
     if (sst != TO_OK) return fail(sst, "state solve did not reach cg_rtol");
+    if (h.oo.status != TO_OK)
+        return fail(TO_ENOTCONV, "OC: the multiplier search stopped at oc_maxit before meeting oc_tol");
     TOPO_API_END
 }
 

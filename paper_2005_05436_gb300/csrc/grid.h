@@ -85,6 +85,7 @@ struct to_grid {
     int* tc_err = nullptr;     // device error word of the tensor-core operator
     bool use_tc = false;       // the FP32 fine operator runs on tensor cores
     bool node_centric = false; // 3D K u by the node-centric dense-Ke kernels (ku_impl 1)
+    bool walsh_pair = false;   // FP32 3D K u by the element-pair kernel (kernels_walsh_pair.cu)
 
     topo::Solver* solver = nullptr;
     to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned

@@ -39,6 +39,15 @@ void launch_walsh_op3(const Dims& d, const WalshK<T>& wk, int mode, const T* E, 
                       PcgScalars* pcg, double* partials, long long npartials, unsigned* counter, int nsm,
                       cudaStream_t st);
 
+// The same FP32 operator and epilogues with two elements per thread in paired
+// FP32 arithmetic (kernels_walsh_pair.cu); walsh_pair_supported: a tile shape
+// fits the grid (3D).
+bool walsh_pair_supported(const Dims& d);
+void launch_walsh_pair3(const Dims& d, const WalshK<float>& wk, int mode, const float* E, const float* u,
+                        const float* r, const float* dinv, float* out, const uint8_t* fixed, bool mask_out,
+                        float omega, const int* skip, PcgScalars* pcg, double* partials, long long npartials,
+                        unsigned* counter, int nsm, cudaStream_t st);
+
 // Jacobi inverse diagonal: dinv[i] = 1 / K_ii (0 at fixed DOFs).
 template <typename T>
 void launch_diag_inv(const Dims& d, const KeP<T, 24>& ke3, const KeP<T, 8>& ke2, const T* E,

@@ -98,6 +98,13 @@ static void fine_op_dispatch(const to_grid* g, const T* E, const T* u, const T* 
     const Dims& d = g->d;
     const int nb = div_up(d.nnodes, 256);
     if (d.dim == 3 && !g->node_centric) {
+        if constexpr (sizeof(T) == 4) {
+            if (g->walsh_pair) {
+                launch_walsh_pair3(d, g->wkf, MODE, E, u, r, dinv, out, g->fixed, true, omega, skip, pcg,
+                                   g->partials, g->npartials, g->counter, g->nsm, st);
+                return;
+            }
+        }
         launch_walsh_op3<T>(d, grid_wk<T>(g), MODE, E, u, r, dinv, out, g->fixed, true, omega, skip, pcg,
                             g->partials, g->npartials, g->counter, g->nsm, st);
         return;

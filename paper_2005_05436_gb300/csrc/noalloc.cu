@@ -2,7 +2,10 @@
 // include/topopt.h). Its scratch is one file-scope device array; the update
 // itself is the same cooperative kernel that to_oc_update launches.
 #include <mutex>
+#include <new>
+#include <string>
 
+#include "grid.h"
 #include "kernels.h"
 
 namespace topo {
@@ -33,7 +36,9 @@ __global__ void k_count_active(long long n, const int8_t* __restrict__ passive,
 }
 
 // Device address of g_oc_scratch, resolved once per device with that device
-// current (in host code the symbol's name is only a host-side stand-in).
+// current (in host code the symbol's name is only a host-side stand-in). The
+// first resolution on a device loads the module that holds the array (CUDA
+// loads modules lazily), which is when the array's memory is reserved.
 static unsigned char* scratch_address(int dev) {
     static std::mutex mu;
     static unsigned char* addr[64] = {};
@@ -55,11 +60,14 @@ extern "C" to_status to_oc_update_noalloc(int64_t nel, double* x, const double* 
                                           const int8_t* passive, double volfrac, double move,
                                           double oc_tol, int32_t oc_maxit, int64_t deadline_cycles,
                                           void* stream, double* lm_out) {
-    if (!x || !dc || !dV0) return TO_EINVAL;
-    if (nel < 1 || nel > NOALLOC_MAX_NEL) return TO_EINVAL;
+    if (!x || !dc || !dV0) return api_fail(TO_EINVAL, "to_oc_update_noalloc: NULL x, dc or dV0");
+    if (nel < 1 || nel > NOALLOC_MAX_NEL)
+        return api_fail(TO_EINVAL, "to_oc_update_noalloc: nel must lie in [1, 1048576] (the size of its "
+                                   "static scratch array)");
     if (!(volfrac > 0.0 && volfrac < 1.0) || !(move > 0.0 && move <= 1.0) || !(oc_tol > 0.0) ||
         oc_maxit < 1 || deadline_cycles <= 0)
-        return TO_EINVAL;
+        return api_fail(TO_EINVAL, "to_oc_update_noalloc: need 0 < volfrac < 1, 0 < move <= 1, oc_tol > 0, "
+                                   "oc_maxit >= 1, deadline_cycles > 0");
     try {
         cudaStream_t st = (cudaStream_t)stream;
         int dev = 0;
@@ -81,7 +89,7 @@ extern "C" to_status to_oc_update_noalloc(int64_t nel, double* x, const double* 
             TOPO_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
             TOPO_CUDA(cudaStreamSynchronize(st));
             nact = (long long)h;
-            if (nact < 1) return TO_EINVAL;
+            if (nact < 1) return api_fail(TO_EINVAL, "to_oc_update_noalloc: no active element");
         }
         int nblocks = oc_max_blocks();
         if (nblocks > NOALLOC_MAX_BLOCKS) nblocks = NOALLOC_MAX_BLOCKS;
@@ -94,10 +102,17 @@ extern "C" to_status to_oc_update_noalloc(int64_t nel, double* x, const double* 
         TOPO_CUDA(cudaMemcpyAsync(&h_out, out, sizeof(h_out), cudaMemcpyDeviceToHost, st));
         TOPO_CUDA(cudaMemcpyAsync(&h_bar, bar, sizeof(h_bar), cudaMemcpyDeviceToHost, st));
         TOPO_CUDA(cudaStreamSynchronize(st));
-        if (h_bar.error) return TO_ETIMEOUT;
+        if (h_bar.error) return api_fail(TO_ETIMEOUT, "to_oc_update_noalloc: grid barrier deadline passed");
         if (lm_out) *lm_out = h_out.lm;
+        if (h_out.status != TO_OK)
+            return api_fail(TO_ENOTCONV, "to_oc_update_noalloc: the multiplier search stopped at oc_maxit "
+                                         "before the bracket met oc_tol (x holds the last candidate)");
     } catch (const topo::Error& e) {
-        return e.code;
+        return api_fail(e.code, e.what());
+    } catch (const std::bad_alloc&) {
+        return api_fail(TO_ENOMEM, "to_oc_update_noalloc: host allocation failed");
+    } catch (const std::exception& e) {
+        return api_fail(TO_ECUDA, e.what());
     }
     return TO_OK;
 }

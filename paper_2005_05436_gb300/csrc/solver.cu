@@ -625,8 +625,9 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
 void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, int impl) {
     Solver* sv = g->solver;
     TOPO_REQUIRE(g->p.precision == TO_MIXED, "handle was created for TO_FP64");
-    TOPO_REQUIRE(impl == 1 || (impl == 2 && g->ke_tc) || (impl == 3 && g->d.dim == 3),
-                 "impl must be 1, or 2 or 3 on a 3D grid");
+    TOPO_REQUIRE(impl == 1 || (impl == 2 && g->ke_tc) || (impl == 3 && g->d.dim == 3) ||
+                     (impl == 4 && g->d.dim == 3 && walsh_pair_supported(g->d)),
+                 "impl must be 1, or 2, 3 or 4 on a 3D grid");
     const Dims& d = g->d;
     const long long n = d.ndof;
     cudaStream_t st = g->st;
@@ -634,18 +635,21 @@ void apply_K_fp32(to_grid* g, const double* xPhys, const double* u, double* y, i
     launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, P.E, st);
     k_cast_mask<double, float><<<div_up(n, 256), 256, 0, st>>>(n, u, P.p, g->fixed);
     TOPO_CHECK_LAUNCH();
-    const bool saved = g->use_tc, saved_nc = g->node_centric;
+    const bool saved = g->use_tc, saved_nc = g->node_centric, saved_wp = g->walsh_pair;
     g->use_tc = impl == 2;
     g->node_centric = impl == 1;
+    g->walsh_pair = impl == 4;
     try {
         launch_fine_op<float>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, 0.f, nullptr, nullptr, st);
     } catch (...) {
         g->use_tc = saved;
         g->node_centric = saved_nc;
+        g->walsh_pair = saved_wp;
         throw;
     }
     g->use_tc = saved;
     g->node_centric = saved_nc;
+    g->walsh_pair = saved_wp;
     k_cast_mask<float, double><<<div_up(n, 256), 256, 0, st>>>(n, P.Ap, y, nullptr);
     TOPO_CHECK_LAUNCH();
     if (g->tc_err) {

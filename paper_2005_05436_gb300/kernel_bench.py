@@ -31,7 +31,7 @@ def bench_ku(a):
     F, fixed = I.cantilever_3d(nelx, nely, nelz) if dim == 3 else I.mbb_half_beam(nelx, nely)
     prec = TO_FP64 if a.precision == "fp64" else TO_MIXED
     p = default_params(dim, nelx, nely, nelz, precision=prec, rmin=math.sqrt(3.0),
-                       ku_impl={"auto": 0, "node": 1, "tc": 2, "walsh": 3}[a.ku_impl])
+                       ku_impl={"auto": 0, "node": 1, "tc": 2, "walsh": 3, "pair": 4}[a.ku_impl])
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
     x = torch.from_numpy(I.random_design(g.nel, 1, "binary").clip(1e-3, 1.0)).cuda()
     us = g.time_apply_K(x, prec, reps=a.reps)
@@ -219,7 +219,7 @@ def main():
     ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh"])
+    ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh", "pair"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--steps", type=int, default=3)

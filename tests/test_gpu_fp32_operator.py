@@ -3,7 +3,8 @@
 impl 1: node-centric gather with the dense Ke (FP32 FMAs on CUDA cores);
 impl 2: tcgen05 tensor cores (TF32 with split operands, FP32 accumulation);
 impl 3: element tiles with Ke factored in the Walsh basis of the corners (FP32
-on CUDA cores). All must reproduce K u to FP32-level accuracy (normwise 1e-5;
+on CUDA cores); impl 4: the same product for two elements per thread in paired
+FP32 instructions. All must reproduce K u to FP32-level accuracy (normwise 1e-5;
 the split TF32 products carry about 21 bits).
 """
 import numpy as np
@@ -34,8 +35,9 @@ def _apply(g, xp, u, impl):
     return y.cpu().numpy()
 
 
-@pytest.mark.parametrize("impl", [1, 2, 3])
-@pytest.mark.parametrize("shape", [(7, 5, 3), (13, 9, 6), (4, 8, 4), (1, 1, 1), (24, 12, 12), (40, 33, 9)])
+@pytest.mark.parametrize("impl", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(7, 5, 3), (13, 9, 6), (4, 8, 4), (1, 1, 1), (24, 12, 12), (40, 33, 9),
+                                   (5, 130, 17), (9, 200, 3), (6, 129, 40), (3, 2, 61), (11, 47, 23)])
 def test_fp32_operator_matches_oracle(shape, impl):
     from paper_2005_05436_gb300 import TO_MIXED
     g, F, fixed = make_grid(shape, precision=TO_MIXED, penal=3.0)
@@ -60,13 +62,16 @@ def test_fp32_operators_agree_at_full_size():
     y1 = _apply(g, xp, u, 1)
     y2 = _apply(g, xp, u, 2)
     y3 = _apply(g, xp, u, 3)
+    y4 = _apply(g, xp, u, 4)
     assert rel(y2, y1) <= 1e-5
     assert rel(y3, y1) <= 1e-5
+    assert rel(y4, y1) <= 1e-5
     og = O.Grid(*shape)
     rows = np.random.default_rng(7).integers(0, g.ndof, 150)
     ref = O.apply_K_rows(og, O.element_stiffness(3), O.simp_modulus(xp, 3.0), u, rows, fixed)
     assert np.abs(y2[rows] - ref).max() <= 1e-5 * np.abs(ref).max()
     assert np.abs(y3[rows] - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs(y4[rows] - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
 def test_translation_invariance_exact():

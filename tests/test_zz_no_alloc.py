@@ -44,12 +44,47 @@ def test_noalloc_oc_matches_handle_entry_twice(tol):
         got = torch.from_numpy(x).cuda()
         lm = C.c_double()
         torch.cuda.synchronize()
+        # the first call on this device has loaded the module that holds the scratch
+        # array; the second must leave the device's free memory and torch's pool as
+        # they were (the property this entry point exists for)
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
         st = lib.to_oc_update_noalloc(n, C.c_void_p(got.data_ptr()), C.c_void_p(dct.data_ptr()),
                                       C.c_void_p(dvt.data_ptr()), None, vf, move, tol, 200,
                                       2_000_000_000, C.c_void_p(stream.cuda_stream), C.byref(lm))
-        assert st == L.TO_OK, (call, st)
+        torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == reserved0
+        assert st == L.TO_OK, (call, st, lib.to_last_error())
         assert abs(lm.value - lm_ref) <= max(tol, 1e-14) * 4 * lm_ref, (call, lm.value, lm_ref)
         assert rel(got.cpu().numpy(), ref.cpu().numpy()) <= 1e-12, call
+
+
+def test_noalloc_oc_against_oracle_and_maxit():
+    """Once directly against the oracle's OC bisection (parity tolerance), then
+    with oc_maxit = 1: the search stops early and the call says so."""
+    from oracle import topopt_oracle as O
+    from paper_2005_05436_gb300 import _lib as L, build
+    build.build()
+    lib = L.load()
+    n, vf, move = 30000, 0.3, 0.2
+    x, dc, dV0 = _case(n, 31, vf)
+    xr, lm_ref, _ = O.oc_update(x, dc, dV0, np.ones(n, bool), move, vf, tol=1e-15)
+    got = torch.from_numpy(x).cuda()
+    dct, dvt = torch.from_numpy(dc).cuda(), torch.from_numpy(dV0).cuda()
+    lm = C.c_double()
+    st = lib.to_oc_update_noalloc(n, C.c_void_p(got.data_ptr()), C.c_void_p(dct.data_ptr()),
+                                  C.c_void_p(dvt.data_ptr()), None, vf, move, 1e-15, 200, 2_000_000_000,
+                                  None, C.byref(lm))
+    assert st == L.TO_OK
+    assert abs(lm.value - lm_ref) <= 1e-12 * lm_ref, (lm.value, lm_ref)
+    assert np.abs(got.cpu().numpy() - xr).max() <= 1e-12
+    got = torch.from_numpy(x).cuda()
+    st = lib.to_oc_update_noalloc(n, C.c_void_p(got.data_ptr()), C.c_void_p(dct.data_ptr()),
+                                  C.c_void_p(dvt.data_ptr()), None, vf, move, 1e-15, 1, 2_000_000_000,
+                                  None, C.byref(lm))
+    assert st == L.TO_ENOTCONV
+    assert b"oc_maxit" in lib.to_last_error()
 
 
 def test_noalloc_oc_with_passive_and_size_limit():
