@@ -56,6 +56,7 @@ enum { TO_FP64 = 0, TO_MIXED = 1 };                        /* to_params.precisio
 enum { TO_PC_JACOBI = 0, TO_PC_GMG = 1 };                  /* to_params.precond */
 enum { TO_CNT_ADD = 0, TO_CNT_MUL = 1 };                   /* to_continuation.kind */
 enum { TO_OC_BISECTION = 0, TO_OC_PRIMAL_DUAL = 1, TO_OC_PHYSICAL_VOLUME = 2 };  /* to_params.oc_method */
+enum { TO_REFINE_RELIABLE = 0, TO_REFINE_FLEXIBLE = 1 };   /* to_params.refine */
 
 /* Continuation parCont = {istart, maxPar, isteps, deltaPar} (Sec. 3): after the
  * OC update of iteration `loop` (1-based), if loop >= istart, par < maxpar and
@@ -131,7 +132,15 @@ typedef struct to_params {
                                each FP32 inner solve (2000); a stalled inner solve hands its
                                iterate to the FP64 flexible-CG step, whose exact line search still
                                lowers the energy. >= 1, else TO_EINVAL */
-    int32_t _pad3;
+    int32_t refine;         /* TO_MIXED, single grid: how the FP64 residual corrects the FP32 solve.
+                               TO_REFINE_RELIABLE (default): one FP32 PCG whose residual is
+                               replaced by the true FP64 residual b - K U (FP64 U += FP32
+                               correction) each time it has fallen by inner_rtol; the search
+                               direction is kept across the replacement, so the Krylov space is
+                               not restarted; if a replacement does not lower the FP64 residual,
+                               the solve continues as TO_REFINE_FLEXIBLE. TO_REFINE_FLEXIBLE:
+                               FP32 inner solves to inner_rtol from scratch, each followed by one
+                               FP64 flexible-CG step (exact line search). */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

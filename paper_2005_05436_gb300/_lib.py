@@ -19,6 +19,7 @@ TO_FP64, TO_MIXED = 0, 1
 TO_PC_JACOBI, TO_PC_GMG = 0, 1
 TO_CNT_ADD, TO_CNT_MUL = 0, 1
 TO_OC_BISECTION, TO_OC_PRIMAL_DUAL, TO_OC_PHYSICAL_VOLUME = 0, 1, 2
+TO_REFINE_RELIABLE, TO_REFINE_FLEXIBLE = 0, 1
 
 
 class Continuation(C.Structure):
@@ -40,7 +41,7 @@ class Params(C.Structure):
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
-                ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("_pad3", C.c_int32)]
+                ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

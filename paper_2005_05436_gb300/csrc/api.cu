@@ -154,6 +154,8 @@ static void validate(const to_params* p) {
                  "Anderson extrapolation: pae_q0 >= 0, pae_q >= 1, pae_m in 1..4, pae_alpha in (0, 1], "
                  "pae_zeta in [0, 1]");
     TOPO_REQUIRE(p->inner_maxit >= 1, "inner_maxit must be >= 1");
+    TOPO_REQUIRE(p->refine == TO_REFINE_RELIABLE || p->refine == TO_REFINE_FLEXIBLE,
+                 "refine must be TO_REFINE_RELIABLE or TO_REFINE_FLEXIBLE");
     TOPO_REQUIRE(p->oc_method == TO_OC_BISECTION || p->oc_method == TO_OC_PRIMAL_DUAL ||
                      p->oc_method == TO_OC_PHYSICAL_VOLUME,
                  "oc_method must be TO_OC_BISECTION, TO_OC_PRIMAL_DUAL or TO_OC_PHYSICAL_VOLUME");
@@ -212,6 +214,7 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->pae_alpha = 0.9;
     p->pae_zeta = 1.0;
     p->inner_maxit = 2000;
+    p->refine = TO_REFINE_RELIABLE;
     return TO_OK;
 }
 

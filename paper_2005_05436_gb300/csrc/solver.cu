@@ -7,10 +7,16 @@
 // (or the iteration cap) sets `done`. The host does not poll.
 //
 // TO_FP64: the PCG and the preconditioner run in FP64.
-// TO_MIXED: FP64 iterative refinement: r = F - K U is formed in FP64, the
-// correction K d = r is solved by an FP32 PCG (FP32 operator and V-cycle,
-// FP64 dot products) to a relative tolerance inner_rtol, and U += d in FP64,
-// until ||F - K U|| <= cg_rtol ||F|| in FP64.
+// TO_MIXED: the FP32 PCG (FP32 operator and V-cycle, float-float dot
+// products) works on corrections of the FP64 iterate U, and the true FP64
+// residual r = F - K U decides convergence, ||r|| <= cg_rtol ||F||. Two ways
+// of joining them (to_params.refine): reliable updates, in which one PCG runs
+// in segments; after each segment (residual fallen by inner_rtol) U += its
+// FP32 correction in FP64 and the FP64 residual replaces the recursive one
+// while the search direction carries on, so the Krylov space is not restarted;
+// or flexible CG, in which each FP32 solve to inner_rtol starts from scratch
+// and is followed by one FP64 CG step along its result, K-orthogonal to the
+// previous step, with the exact line search.
 #include <cmath>
 
 #include "grid.h"
@@ -149,6 +155,13 @@ __global__ void __launch_bounds__(KNT) k_refine_resid(long long n, const double*
         res[0] = tot[0];
         res[1] = tot[1];
     }
+}
+
+// New stopping data of a resumed PCG segment; rz and p of the previous segment stay.
+__global__ void k_pcg_resume(PcgScalars* s, double rtol2, int maxit) {
+    s->rtol2 = rtol2;
+    s->maxit = maxit;
+    s->done = 0;
 }
 
 __global__ void k_refine_update(long long n, double* __restrict__ x64, const float* __restrict__ d32) {
@@ -358,8 +371,12 @@ static void precond_setup(to_grid* g, Pcg<T>& P, cudaStream_t st) {
         launch_diag_inv<T>(g->d, grid_ke3<T>(g), grid_ke2<T>(g), P.E, g->fixed, P.dinv_j, st);
 }
 
+// resume (with x0_zero): continue the previous segment's iteration from the
+// residual now in P.b: its search direction p and r.z are kept, and the new
+// direction is p = z + (r.z / r.z_old) p instead of p = z.
 template <typename T>
-static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int maxit, bool x0_zero, bool setup) {
+static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int maxit, bool x0_zero, bool setup,
+                          bool resume = false) {
     const Dims& d = g->d;
     const long long n = d.ndof;
     cudaStream_t st = g->st;
@@ -371,10 +388,15 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
         P.body_kernels = captured_launches_reset();
     }
     TOPO_CUDA(cudaEventRecord(sv->ev[1], st));
-    PcgScalars init{};
-    init.rtol2 = rtol * rtol;
-    init.maxit = maxit;
-    TOPO_CUDA(cudaMemcpyAsync(P.s, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+    if (resume) {
+        k_pcg_resume<<<1, 1, 0, st>>>(P.s, rtol * rtol, maxit);
+        TOPO_CHECK_LAUNCH();
+    } else {
+        PcgScalars init{};
+        init.rtol2 = rtol * rtol;
+        init.maxit = maxit;
+        TOPO_CUDA(cudaMemcpyAsync(P.s, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+    }
     if (x0_zero) {
         k_zero<T><<<div_up(n, 256), 256, 0, st>>>(n, P.x);
         TOPO_CUDA(cudaMemcpyAsync(P.r, P.b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
@@ -387,13 +409,26 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
     if (P.mg) {
         T* z = mg_vcycle<T>(g, P.mg, P.r, &P.s->done, st);
         (void)z;  // the same buffer the captured body uses
-        k_gpcg_rz<T, true, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, P.p, P.s, g->partials,
-                                                              g->counter);
+        if (resume)
+            k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
+                                                                   g->counter);
+        else
+            k_gpcg_rz<T, true, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, P.p, P.s, g->partials,
+                                                                  g->counter);
     } else {
-        k_gpcg_rz<T, true, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.zj, P.dinv_j, P.p, P.s, g->partials,
-                                                             g->counter);
+        if (resume)
+            k_gpcg_rz<T, false, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.zj, P.dinv_j, nullptr, P.s,
+                                                                  g->partials, g->counter);
+        else
+            k_gpcg_rz<T, true, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.zj, P.dinv_j, P.p, P.s, g->partials,
+                                                                 g->counter);
     }
     TOPO_CHECK_LAUNCH();
+    if (resume) {
+        k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(
+            n, P.mg ? P.z : P.zj, P.p, P.s, cudaGraphConditionalHandle{}, 0);
+        TOPO_CHECK_LAUNCH();
+    }
     if (g->p.loop_mode == 0) {
         TOPO_CUDA(cudaGraphLaunch(P.loop, st));
     } else {
@@ -551,6 +586,8 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
         bool confirmed = true;  // rel is the true FP64 residual (not the recursive one)
         TOPO_CUDA(cudaMemsetAsync(sv->fs, 0, sizeof(FcgS), st));
+        bool reliable = g->p.refine == TO_REFINE_RELIABLE;
+        bool have_dir = false;  // a previous segment left its search direction
         for (;;) {
             if (!std::isfinite(rel)) {
                 status = TO_ENAN;
@@ -568,6 +605,33 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             if (refinements >= max_ref || iters >= g->p.cg_maxit) {
                 status = TO_ENOTCONV;
                 break;
+            }
+            if (reliable) {
+                // one segment of the FP32 PCG until its residual has fallen by inner_rtol, then
+                // U += the FP32 correction in FP64 and the true FP64 residual replaces the
+                // recursive one; the next segment keeps the search direction
+                const PcgScalars h = run_pcg<float>(g, sv, P, g->p.inner_rtol,
+                                                    std::min(g->p.inner_maxit, g->p.cg_maxit - iters), true,
+                                                    !prepared, have_dir);
+                prepared = true;
+                iters += h.iters;
+                if (h.done == 3) {
+                    status = TO_ENAN;
+                    break;
+                }
+                k_refine_update<<<div_up(n, 256), 256, 0, st>>>(n, x64, P.x);
+                TOPO_CHECK_LAUNCH();
+                count_launches(1);
+                const double rel_prev = rel;
+                true_residual(g, sv, b, x64, r64, P.b);
+                rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
+                confirmed = true;
+                ++refinements;
+                have_dir = true;
+                // the FP32 recursion no longer tracks the FP64 residual: continue with the
+                // flexible-CG steps, whose exact FP64 line search cannot raise the energy
+                if (std::isfinite(rel) && rel > 0.5 * rel_prev) reliable = false;
+                continue;
             }
             // the preconditioner is set up once per solve
             // each inner solve is capped: a stalled FP32 run still hands the FP64 step a direction
