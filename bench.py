@@ -65,7 +65,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--mg-nu", type=int, default=1, help="GMG smoothing sweeps per level")
-    ap.add_argument("--inner-rtol", type=float, default=1e-3, help="mixed path: inner FP32 solve tolerance")
+    ap.add_argument("--inner-rtol", type=float, default=3e-3,
+                    help="mixed path: residual drop of each FP32 PCG segment (reliable updates) or inner solve")
     ap.add_argument("--refine", default="reliable", choices=["reliable", "flexible"],
                     help="mixed path: FP32 PCG with FP64 reliable updates, or FP32 solves with FP64 flexible-CG steps")
     ap.add_argument("--oc-method", default="bisection", choices=["bisection", "primal_dual"],

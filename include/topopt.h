@@ -95,7 +95,10 @@ typedef struct to_params {
     int32_t precond;        /* TO_PC_JACOBI or TO_PC_GMG */
     int32_t mg_levels;      /* GMG levels incl. the fine grid, 0 = automatic */
     int64_t deadline_cycles;/* clock64 limit of every device-side wait (2e9) */
-    double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3) */
+    double inner_rtol;      /* TO_MIXED: relative tolerance of each FP32 inner solve (1e-3); with
+                               TO_REFINE_RELIABLE the drop of each PCG segment, or the smaller
+                               drop 0.3 cg_rtol / (current FP64 residual) that still reaches
+                               cg_rtol, when that is larger */
     double mg_omega;        /* GMG l1-Jacobi smoother weight (1.0) */
     int32_t mg_nu;          /* GMG pre- and post-smoothing sweeps per level (2) */
     int32_t ku_impl;        /* 3D stiffness operator: 0 auto (= 3);
@@ -137,10 +140,15 @@ typedef struct to_params {
                                replaced by the true FP64 residual b - K U (FP64 U += FP32
                                correction) each time it has fallen by inner_rtol; the search
                                direction is kept across the replacement, so the Krylov space is
-                               not restarted; if a replacement does not lower the FP64 residual,
-                               the solve continues as TO_REFINE_FLEXIBLE. TO_REFINE_FLEXIBLE:
+                               not restarted; if a segment reaches min(inner_maxit, 400)
+                               iterations or a replacement does not halve the FP64 residual, the
+                               solve continues as TO_REFINE_FLEXIBLE. TO_REFINE_FLEXIBLE:
                                FP32 inner solves to inner_rtol from scratch, each followed by one
                                FP64 flexible-CG step (exact line search). */
+    int32_t mg_unfused;     /* GMG, 3D coarse levels of at most 16,384 nodes: 0 prolongation fused
+                               into the first post-smoothing sweep (default); 1 separate kernels
+                               (same arithmetic and order, for comparison) */
+    int32_t _pad4;
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */
@@ -465,6 +473,9 @@ typedef struct to_net_cfg {
                        accumulated in FP32); 0: FP32 throughout */
     int32_t in_ch;  /* 4: node density and the three load components */
     int32_t out_ch; /* 3: the displacement direction */
+    int32_t cuda_cores_only; /* 0: tcgen05 tensor cores for the BF16 layers with 16, 32 or 64 input
+                                and output channels (default); 1: every layer on CUDA cores */
+    int32_t _pad;
 } to_net_cfg;
 
 /* Creates a network with all parameters 0 (set them with to_net_set_params). */

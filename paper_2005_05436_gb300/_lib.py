@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("mg_omega", C.c_double), ("mg_nu", C.c_int32), ("ku_impl", C.c_int32),
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
-                ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32)]
+                ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32),
+                ("mg_unfused", C.c_int32), ("_pad4", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -88,7 +89,8 @@ class BatchInfo(C.Structure):
 
 
 class NetCfg(C.Structure):
-    _fields_ = [("base", C.c_int32), ("bf16", C.c_int32), ("in_ch", C.c_int32), ("out_ch", C.c_int32)]
+    _fields_ = [("base", C.c_int32), ("bf16", C.c_int32), ("in_ch", C.c_int32), ("out_ch", C.c_int32),
+                ("cuda_cores_only", C.c_int32), ("_pad", C.c_int32)]
 
 
 class TopoptError(RuntimeError):

@@ -344,6 +344,44 @@ to_status to_init_grid(const to_params* p, const double* F, const uint8_t* fixed
         g->taps.wf = dwf;
         g->Hs_const = wsum;
         g->rHs_const = 1.0 / wsum;
+        // the same window as rows along x, padded to whole chunks (tiled filter)
+        std::vector<int> rows;
+        std::vector<double> rw;
+        std::vector<float> rwh, rwl;
+        for (int oz = -Rz; oz <= Rz; ++oz)
+            for (int oy = -R; oy <= R; ++oy) {
+                int dmax = -1;
+                for (int ox = 0; ox <= R; ++ox)
+                    if (p->rmin - std::sqrt((double)(ox * ox + oy * oy + oz * oz)) > 0.0) dmax = ox;
+                if (dmax < 0) continue;
+                const int nch = (2 * dmax + 1 + FILTER_K - 1) / FILTER_K;
+                rows.insert(rows.end(), {oy, oz, -dmax, nch});
+                for (int i = 0; i < nch * FILTER_K; ++i) {
+                    const int ox = -dmax + i;
+                    const double wt =
+                        ox <= dmax ? std::fmax(0.0, p->rmin - std::sqrt((double)(ox * ox + oy * oy + oz * oz))) : 0.0;
+                    rw.push_back(wt);
+                    const float h = (float)wt;
+                    rwh.push_back(h);
+                    rwl.push_back((float)(wt - (double)h));
+                }
+            }
+        g->taps.R = R;
+        g->taps.Rz = Rz;
+        g->taps.nrows = (int)rows.size() / 4;
+        int* drows = dalloc<int>(g, rows.size());
+        double* drw = dalloc<double>(g, rw.size());
+        float* drwh = dalloc<float>(g, rw.size());
+        float* drwl = dalloc<float>(g, rw.size());
+        TOPO_CUDA(cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, g->st));
+        TOPO_CUDA(cudaMemcpyAsync(drw, rw.data(), rw.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
+        TOPO_CUDA(cudaMemcpyAsync(drwh, rwh.data(), rwh.size() * sizeof(float), cudaMemcpyHostToDevice, g->st));
+        TOPO_CUDA(cudaMemcpyAsync(drwl, rwl.data(), rwl.size() * sizeof(float), cudaMemcpyHostToDevice, g->st));
+        TOPO_CUDA(cudaStreamSynchronize(g->st));
+        g->taps.rows = drows;
+        g->taps.rw = drw;
+        g->taps.rwh = drwh;
+        g->taps.rwl = drwl;
     }
 
     // workspaces
@@ -442,7 +480,8 @@ to_status to_filter(to_grid* g, const double* in, double* out, const double* dpr
     if (in == out) return fail(TO_EINVAL, "out must not alias in");
     TOPO_API_BEGIN
     grid_sync_in(g);
-    launch_filter(g->d, g->taps, (char)g->p.ftBC, g->rHs, g->rHs_const, in, dprj, out, nullptr, nullptr, g->st);
+    launch_filter(g->d, g->taps, (char)g->p.ftBC, g->rHs, g->rHs_const, in, dprj, out, nullptr, nullptr, g->st,
+                  g->p.precision == TO_MIXED);
     grid_sync_out(g);
     TOPO_API_END
 }
@@ -572,7 +611,9 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     s->loop += 1;
     TOPO_CUDA(cudaEventRecord(g->ev_t[0], st));
     // RL.1 physical density: xPhys(act) = xTilde(act), passive keep x
-    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, s->x, nullptr, g->xt, g->passive, s->x, st);
+    const bool ffilt = p.precision == TO_MIXED;  // the mixed path filters in float-float arithmetic
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, s->x, nullptr, g->xt, g->passive, s->x, st,
+                  ffilt);
     if (p.ft > 1) {
         launch_project(d.nel, g->xt, s->xPhys, g->dprj, s->beta, s->eta, p.volfrac, p.ft == 3,
                        p.newton_tol, p.newton_maxit, p.deadline_cycles, g->partials, g->bar,
@@ -601,8 +642,10 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
                        &g->ds->esum, g->partials, g->counter, st);
     launch_dot(d.ndof, g->F, s->U, &g->ds->c, g->partials, g->counter, st);
     launch_dv(d.nel, g->passive, 1.0 / ((double)d.nel * p.volfrac), g->dV, st);
-    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dc, g->dprj, g->dcf, nullptr, nullptr, st);
-    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st);
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dc, g->dprj, g->dcf, nullptr, nullptr, st,
+                  ffilt);
+    launch_filter(d, g->taps, (char)p.ftBC, g->rHs, g->rHs_const, g->dV, g->dprj, g->dV0, nullptr, nullptr, st,
+                  ffilt);
     TOPO_CUDA(cudaEventRecord(g->ev_t[3], st));
     // RL.4 OC update
     const bool pae_on = p.pae_q0 > 0 && s->loop >= p.pae_q0;

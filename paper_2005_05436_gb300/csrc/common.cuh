@@ -83,7 +83,20 @@ struct FilterTaps {
     const int* off;   // [nw * 3] (ox, oy, oz)
     const double* w;  // [nw]
     const float* wf;  // [nw]
+    // The same window as rows along x for the tiled filter (kernels_filter.cu):
+    // row k has offsets (oy, oz) = rows[4k], rows[4k + 1], and its x offsets
+    // run from rows[4k + 2] in rows[4k + 3] chunks of FILTER_K; its weights are
+    // rw[rowbase(k) + i] (zero where the cone weight is 0), rowbase(k) = the sum
+    // of FILTER_K * chunks of the rows before; rwh / rwl split them into two
+    // floats (hi = (float) w, lo = (float) (w - hi)).
+    int R, Rz, nrows;
+    const int* rows;
+    const double* rw;
+    const float* rwh;
+    const float* rwl;
 };
+
+constexpr int FILTER_K = 8;  // outputs per thread along x in the tiled filter
 
 __host__ __device__ inline int mirror_index(int j, int n) {
     // Repeated border-duplicating reflection ('N' padding).
@@ -234,7 +247,7 @@ struct GridBarrier {
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, long long deadline) {
     __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {  // one thread per block arrives
         volatile unsigned* vgen = &b->gen;
         volatile int* verr = &b->error;
         unsigned my_gen = *vgen;

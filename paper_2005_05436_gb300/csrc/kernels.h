@@ -83,9 +83,16 @@ void launch_modulus(long long n, const double* x, double penal, double E0, doubl
 // (the array, or rHs_const where it is nullptr). If passive_keep != nullptr
 // (forward only), passive elements take the value of `keep` instead
 // (xPhys(act) = xTilde(act)).
+// The shared-memory tile kernel (kernels_filter.cu) does it when its tile fits
+// shared memory, in FP64 or (float_float) in float-float arithmetic; otherwise
+// one thread per element gathers its taps from global memory in FP64.
 void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                    const double* in, const double* dprj, double* out, const int8_t* passive,
-                   const double* keep, cudaStream_t st);
+                   const double* keep, cudaStream_t st, bool float_float = false);
+// The tile kernel alone; false (nothing launched) when its tile does not fit.
+bool launch_filter_tiled(const Dims& d, const FilterTaps& t, char bc, const double* rHs, double rHs_const,
+                         const double* in, const double* dprj, double* out, const int8_t* passive,
+                         const double* keep, bool float_float, cudaStream_t st);
 
 struct ProjectOut {
     double eta;

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) k_filter(Dims d, FilterTaps taps, int bcN
 
 void launch_filter(const Dims& d, const FilterTaps& taps, char bc, const double* rHs, double rHs_const,
                    const double* in, const double* dprj, double* out, const int8_t* passive,
-                   const double* keep, cudaStream_t st) {
+                   const double* keep, cudaStream_t st, bool float_float) {
+    if (launch_filter_tiled(d, taps, bc, rHs, rHs_const, in, dprj, out, passive, keep, float_float, st)) return;
     k_filter<<<div_up(d.nel, 256), 256, 0, st>>>(d, taps, bc == 'N', rHs, rHs_const, in, dprj, out,
                                                  passive, keep);
     TOPO_CHECK_LAUNCH();

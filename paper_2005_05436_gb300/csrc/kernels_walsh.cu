@@ -273,11 +273,6 @@ static int device_sms() {
     return v;
 }
 
-static int env_int(const char* name) {
-    const char* s = std::getenv(name);
-    return s ? std::atoi(s) : 0;
-}
-
 // Fraction of the threads of a TY x TZ tiling that own an output node.
 static double walsh_util(const Dims& d, int TY, int TZ) {
     const double ty = (double)div_up(d.nny, TY - 1) * TY, tz = (double)div_up(d.nnz, TZ - 1) * TZ;
@@ -294,11 +289,8 @@ static void walsh_launch_tile(const Dims& d, const WalshK<T>& wk, int mode, cons
     const long long tiles = (long long)ntY * ntZ;
     // About 1,536 threads per SM over the launch, at least four planes per
     // block (the first element plane of a block is a halo).
-    int LX = env_int("TOPO_WALSH_LX");
-    if (LX <= 0) {
-        const long long chunks = std::max<long long>(1, (long long)nsm * (1536 / NT) / tiles);
-        LX = std::max(4, div_up(d.nnx, chunks));
-    }
+    const long long chunks = std::max<long long>(1, (long long)nsm * (1536 / NT) / tiles);
+    int LX = std::max(4, div_up(d.nnx, chunks));
     long long nb = tiles * div_up(d.nnx, LX);
     while (pcg && nb > npartials) {  // one partial per block
         LX *= 2;
@@ -331,12 +323,8 @@ void launch_walsh_op3(const Dims& d, const WalshK<T>& wk, int mode, const T* E, 
     // Tile shapes: 32 x 8 (a warp is one y-row), 8 x 8 and 16 x 16 (warps of
     // several rows); the one with the fewest threads per output node wins
     // (grids with nny = 16k + 1 fit 8 x 8 or 16 x 16 tiles better than 31-node rows).
-    static const int forced = env_int("TOPO_WALSH_TILE");  // 1: 32x8, 2: 8x8, 3: 16x16
-    int pick = forced;
-    if (pick < 1 || pick > 3) {
-        const double u1 = walsh_util(d, 32, 8), u2 = walsh_util(d, 8, 8), u3 = walsh_util(d, 16, 16);
-        pick = (u1 >= u2 && u1 >= u3) ? 1 : (u2 >= u3 ? 2 : 3);
-    }
+    const double u1 = walsh_util(d, 32, 8), u2 = walsh_util(d, 8, 8), u3 = walsh_util(d, 16, 16);
+    const int pick = (u1 >= u2 && u1 >= u3) ? 1 : (u2 >= u3 ? 2 : 3);
 #define TOPO_WT(TYV, TZV)                                                                                     \
     walsh_launch_tile<T, TYV, TZV>(d, wk, mode, E, u, r, dinv, out, fixed, mask_out, omega, skip, pcg, partials, \
                                    npartials, counter, nsm, st)

@@ -500,19 +500,18 @@ __global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict_
 // plane order in shared memory, so the result does not depend on scheduling.
 // A single thread per node issues 243 dependent-latency loads; splitting them
 // gives the small coarse grids enough warps in flight.
+// The body of one 32-node block vb (the kernel's blockIdx.x); 288 threads (32, 9).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restrict__ S, const T* __restrict__ R,
-                                                      const T* __restrict__ u, const T* __restrict__ r,
-                                                      const T* __restrict__ dinv, T* __restrict__ out,
-                                                      const uint8_t* __restrict__ fixed, T omega,
-                                                      const int* skip) {
+__device__ __forceinline__ void stencil_op3s_body(int vb, const Dims& d, const T* __restrict__ S,
+                                                  const T* __restrict__ R, const T* __restrict__ u,
+                                                  const T* __restrict__ r, const T* __restrict__ dinv,
+                                                  T* __restrict__ out, const uint8_t* __restrict__ fixed, T omega) {
     constexpr int Q = 9;
     constexpr bool REL = rel_form<T>();
     __shared__ T part[9][32];
-    if (skip && *skip) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = ty / 3, pl = ty % 3;
-    const long long n = (long long)blockIdx.x * 32 + tx;
+    const long long n = (long long)vb * 32 + tx;
     T acc = T(0);
     if (n < d.nnodes) {
         const int iy = (int)(n % d.nny);
@@ -556,6 +555,16 @@ __global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restric
     out[i] = o;
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restrict__ S, const T* __restrict__ R,
+                                                      const T* __restrict__ u, const T* __restrict__ r,
+                                                      const T* __restrict__ dinv, T* __restrict__ out,
+                                                      const uint8_t* __restrict__ fixed, T omega,
+                                                      const int* skip) {
+    if (skip && *skip) return;
+    stencil_op3s_body<T, MODE>(blockIdx.x, d, S, R, u, r, dinv, out, fixed, omega);
+}
+
 // ------------------------------------------------------- transfer operators
 
 // With dinv_c: also the coarse level's first damped Jacobi iterate
@@ -597,15 +606,13 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
 // partials are added in plane order in shared memory (same result as k_restrict
 // up to the order of the three plane sums, fixed for every launch).
 template <typename T>
-__global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* __restrict__ rf,
-                                                    T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
-                                                    const int* skip, const T* __restrict__ dinv_c,
-                                                    T* __restrict__ z_c, T omega) {
+__device__ __forceinline__ void restrict3s_body(int vb, const Dims& dc, const Dims& df, const T* __restrict__ rf,
+                                                T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
+                                                const T* __restrict__ dinv_c, T* __restrict__ z_c, T omega) {
     __shared__ T part[9][32];
-    if (skip && *skip) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = ty / 3, ox = ty % 3 - 1;
-    const long long N = (long long)blockIdx.x * 32 + tx;
+    const long long N = (long long)vb * 32 + tx;
     T acc = T(0);
     if (N < dc.nnodes) {
         const int NY = (int)(N % dc.nny);
@@ -634,6 +641,15 @@ __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* _
     const T v = fixed_c[3 * N + c] ? T(0) : a;
     rc[3 * N + c] = v;
     if (dinv_c) z_c[3 * N + c] = omega * dinv_c[3 * N + c] * v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* __restrict__ rf,
+                                                    T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
+                                                    const int* skip, const T* __restrict__ dinv_c,
+                                                    T* __restrict__ z_c, T omega) {
+    if (skip && *skip) return;
+    restrict3s_body<T>(blockIdx.x, dc, df, rf, rc, fixed_c, dinv_c, z_c, omega);
 }
 
 template <typename T, int DIM>
@@ -672,19 +688,17 @@ __global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __r
 // k_prolong_add's order, then sweeps the stencil in k_stencil_op3s's order,
 // so the result is that of the two kernels in sequence.
 template <typename T, int TY>
-__global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, const T* __restrict__ zc,
-                                                          const T* __restrict__ cur, const T* __restrict__ S,
-                                                          const T* __restrict__ R, const T* __restrict__ r,
-                                                          const T* __restrict__ dinv, T* __restrict__ out,
-                                                          const uint8_t* __restrict__ fixed, T omega,
-                                                          const int* skip) {
+__device__ __forceinline__ void prolong_smooth3s_body(int vb, const Dims& d, const Dims& dc, const T* __restrict__ zc,
+                                                      const T* __restrict__ cur, const T* __restrict__ S,
+                                                      const T* __restrict__ R, const T* __restrict__ r,
+                                                      const T* __restrict__ dinv, T* __restrict__ out,
+                                                      const uint8_t* __restrict__ fixed, T omega) {
     constexpr int TZ = 32 / TY, HY = TY + 2, HZ = TZ + 2, NH = 3 * HZ * HY, Q = 9;
     constexpr bool REL = rel_form<T>();
     __shared__ T us[3 * NH];
     __shared__ T part[9][32];
-    if (skip && *skip) return;
     const int nty = (d.nny + TY - 1) / TY, ntz = (d.nnz + TZ - 1) / TZ;
-    const int by = blockIdx.x % nty, bz = (blockIdx.x / nty) % ntz, ix = blockIdx.x / (nty * ntz);
+    const int by = vb % nty, bz = (vb / nty) % ntz, ix = vb / (nty * ntz);
     const int iy0 = by * TY, iz0 = bz * TZ;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -768,6 +782,17 @@ __global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, co
     T o = us[3 * hc + c] + omega * dinv[i] * (r[i] - a);
     if (fixed[i]) o = T(0);
     out[i] = o;
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, const T* __restrict__ zc,
+                                                          const T* __restrict__ cur, const T* __restrict__ S,
+                                                          const T* __restrict__ R, const T* __restrict__ r,
+                                                          const T* __restrict__ dinv, T* __restrict__ out,
+                                                          const uint8_t* __restrict__ fixed, T omega,
+                                                          const int* skip) {
+    if (skip && *skip) return;
+    prolong_smooth3s_body<T, TY>(blockIdx.x, d, dc, zc, cur, S, R, r, dinv, out, fixed, omega);
 }
 
 // Tile height (nodes along y) of k_prolong_smooth3s with the fewest idle lanes.
@@ -1052,8 +1077,7 @@ template <typename T>
 MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
     MG<T>* mg = new MG<T>();
     try {
-        const char* fu = std::getenv("TOPO_MG_FUSE");  // 0: separate prolongation and smoothing kernels
-        mg->fuse_up = !(fu && fu[0] == '0');
+        mg->fuse_up = g->p.mg_unfused == 0;
         mg->nu = nu;
         mg->omega = (T)omega;
         Dims d = g->d;

@@ -654,10 +654,7 @@ void ensure_ws(to_net* n, const Shape& s) {
 }
 
 bool tc_layer(const to_net* n, int k) {
-    static const bool on = [] {
-        const char* e = std::getenv("TOPO_NET_TC");
-        return !(e && e[0] == '0');
-    }();
+    const bool on = n->cfg.cuda_cores_only == 0;
     const NLayer& Lk = n->L[k];
     auto ok = [](int c) { return c == 16 || c == 32 || c == 64; };
     // 16-byte cp.async of the packed weights: the layer's offset must be a multiple of 8 BF16 values

@@ -17,6 +17,7 @@
 // or flexible CG, in which each FP32 solve to inner_rtol starts from scratch
 // and is followed by one FP64 CG step along its result, K-orthogonal to the
 // previous step, with the exact line search.
+#include <algorithm>
 #include <cmath>
 
 #include "grid.h"
@@ -27,6 +28,9 @@ namespace topo {
 // ------------------------------------------------------------------ kernels
 
 constexpr int KNT = 256;
+// iteration cap of one reliable-update segment (a segment of the 96x48x48
+// cantilever takes about 40 iterations, of the 1200x400 MBB beam about 60)
+constexpr int RELIABLE_SEG_MAX = 400;
 
 static int kblocks(long long n) {
     int nb = div_up(n, KNT * 4);
@@ -607,12 +611,15 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
                 break;
             }
             if (reliable) {
-                // one segment of the FP32 PCG until its residual has fallen by inner_rtol, then
-                // U += the FP32 correction in FP64 and the true FP64 residual replaces the
-                // recursive one; the next segment keeps the search direction
-                const PcgScalars h = run_pcg<float>(g, sv, P, g->p.inner_rtol,
-                                                    std::min(g->p.inner_maxit, g->p.cg_maxit - iters), true,
-                                                    !prepared, have_dir);
+                // one segment of the FP32 PCG until its residual has fallen by inner_rtol (or by
+                // less, when less reaches cg_rtol with a margin for the drift of the FP32
+                // recursion), then U += the FP32 correction in FP64 and the true FP64 residual
+                // replaces the recursive one; the next segment keeps the search direction
+                const double drop = std::max(g->p.inner_rtol, std::min(0.5, 0.3 * g->p.cg_rtol / rel));
+                // a segment that needs more than RELIABLE_SEG_MAX iterations has stalled in FP32
+                const PcgScalars h = run_pcg<float>(
+                    g, sv, P, drop, std::min({g->p.inner_maxit, RELIABLE_SEG_MAX, g->p.cg_maxit - iters}), true,
+                    !prepared, have_dir);
                 prepared = true;
                 iters += h.iters;
                 if (h.done == 3) {
@@ -628,9 +635,10 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
                 confirmed = true;
                 ++refinements;
                 have_dir = true;
-                // the FP32 recursion no longer tracks the FP64 residual: continue with the
-                // flexible-CG steps, whose exact FP64 line search cannot raise the energy
-                if (std::isfinite(rel) && rel > 0.5 * rel_prev) reliable = false;
+                // the FP32 recursion stalled (segment cap) or no longer tracks the FP64
+                // residual: continue with the flexible-CG steps, whose exact FP64 line search
+                // cannot raise the energy
+                if (h.done == 2 || (std::isfinite(rel) && rel > 0.5 * rel_prev)) reliable = false;
                 continue;
             }
             // the preconditioner is set up once per solve

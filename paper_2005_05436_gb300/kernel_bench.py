@@ -113,23 +113,31 @@ def bench_frame(a):
 
 
 def bench_pae(a):
-    """The convergence study of Sec. 3.6 (Table 2) on the half MBB beam (300 x 100,
-    f = 0.5, rmin = 8.75, penal 3, no continuation): T1 density filter (ft 1), T2
-    filter + volume-preserving projection (ft 3, beta 2); each without and with
-    periodic Anderson extrapolation (q0 = 20, q = 4, m_r = 4, alpha 0.9, zeta 1),
-    run until ||xPhys_k - xPhys_k-1|| / sqrt(m) < 1e-6 or 2500 design iterations
-    (FP64 + GMG state solves to 1e-8)."""
+    """The convergence study of Sec. 3.6 (Table 2) on the half MBB beam (f = 0.5,
+    rmin = 8.75, FP64 + GMG state solves to 1e-8), each case without and with
+    periodic Anderson extrapolation (q = 4, m_r = 4, alpha 0.9, zeta 1), run until
+    ||xPhys_k - xPhys_k-1|| / sqrt(m) < 1e-6 or --steps design iterations:
+    T1 density filter alone (ft 1, p = 3, q0 = 20); T2 + volume-preserving
+    projection (ft 3, beta 2, q0 = 20); T3 as T2 with continuation betaCnt =
+    {250, 16, 25, 2}, penalCnt = {50, 3, 25, 0.25} from p = 1 (q0 = 500); T4 as T2
+    on 600 x 200. --cases selects them, --ftbc the filter padding."""
     from . import TO_FP64, TO_PC_GMG
     from .topopt import Design, Grid
-    nelx, nely = (int(v) for v in a.grid.split("x")[:2])
-    F, fixed = I.mbb_half_beam(nelx, nely)
-    out = {"grid": f"{nelx}x{nely}", "paper_iterations": {"T1": 2500, "T1-PAE": 828, "T2": 2500, "T2-PAE": 352}}
-    for case, ft in (("T1", 1), ("T2", 3)):
+    paper = {"T1": (2500, 252.7), "T1-PAE": (828, 258.9), "T2": (2500, 246.1), "T2-PAE": (352, 253.9),
+             "T3": (2500, 199.6), "T3-PAE": (752, 197.5), "T4": (2500, 191.8), "T4-PAE": (818, 192.1)}
+    out = {"ftBC": a.ftbc, "paper_iterations_c": paper}
+    for case in a.cases.split(","):
+        nelx, nely = (600, 200) if case == "T4" else (300, 100)
+        F, fixed = I.mbb_half_beam(nelx, nely)
+        ft = 1 if case == "T1" else 3
+        penal, pcnt, bcnt, q0 = 3.0, (1, 3.0, 10 ** 6, 0.0), (1, 2.0, 10 ** 6, 0.0), 20
+        if case == "T3":
+            penal, pcnt, bcnt, q0 = 1.0, (50, 3.0, 25, 0.25), (250, 16.0, 25, 2.0), 500
         for pae in (False, True):
-            p = default_params(2, nelx, nely, 0, volfrac=0.5, penal=3.0, rmin=8.75, ft=ft, eta=0.5, beta=2.0,
-                               precision=TO_FP64, precond=TO_PC_GMG, mg_nu=1, cg_rtol=1e-8, cg_maxit=50000,
-                               penal_cnt=(1, 3.0, 1000000, 0.0), beta_cnt=(1, 2.0, 1000000, 0.0),
-                               pae_q0=20 if pae else 0, pae_q=4, pae_m=4, pae_alpha=0.9, pae_zeta=1.0)
+            p = default_params(2, nelx, nely, 0, volfrac=0.5, penal=penal, rmin=8.75, ft=ft, ftBC=a.ftbc, eta=0.5,
+                               beta=2.0, precision=TO_FP64, precond=TO_PC_GMG, mg_nu=1, cg_rtol=1e-8,
+                               cg_maxit=50000, penal_cnt=pcnt, beta_cnt=bcnt,
+                               pae_q0=q0 if pae else 0, pae_q=4, pae_m=4, pae_alpha=0.9, pae_zeta=1.0)
             g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
             d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.5)).cuda())
             t0 = time.perf_counter()
@@ -139,11 +147,148 @@ def bench_pae(a):
                 if info["ch"] < 1e-6 or info["loop"] >= a.steps:
                     break
             dt = time.perf_counter() - t0
+            x = d.xPhys
+            mnd = float(100.0 * 4.0 * (x * (1.0 - x)).mean())  # non-discreteness measure of Sec. 3.6
             out[case + ("-PAE" if pae else "")] = {"iterations": info["loop"], "c": round(info["c"], 2),
-                                                   "ch": info["ch"], "s": round(dt, 2),
+                                                   "ch": info["ch"], "m_ND": round(mnd, 4), "penal": info["penal"],
+                                                   "beta": info["beta"], "s": round(dt, 2),
                                                    "ms_per_iteration": round(1e3 * dt / info["loop"], 2)}
             g.close()
     print(json.dumps(out))
+
+
+def bench_mbb(a):
+    """The 2D half MBB beam of Sec. 3 / Table 3 on the grids of --grids, each with
+    the plain FP64 path and the mixed path (GMG-PCG to 1e-8 either way):
+    config2 = volfrac 0.3, penal 1 -> 3 (+0.25 every 25 iterations), beta 2 -> 16
+    (doubling every 25), rmin 0.03 nelx, ft 3; paper = the setting of Table 3
+    (volfrac 0.5, penal 3, rmin = nelx / 75, i.e. 4, 8, 16, ft 3, beta 2, no
+    continuation). Times design iterations warmup+1 .. warmup+steps with CUDA
+    events, and one forward filter application."""
+    from . import TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG
+    from .topopt import Design, Grid
+    out = {"variant": a.variant, "grids": {}}
+    for spec in a.grids.split(","):
+        nelx, nely = (int(v) for v in spec.split("x"))
+        F, fixed = I.mbb_half_beam(nelx, nely)
+        if a.variant == "config2":
+            kw = dict(volfrac=0.3, penal=1.0, rmin=0.03 * nelx, penal_cnt=(1, 3.0, 25, 0.25),
+                      beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+        else:
+            kw = dict(volfrac=0.5, penal=3.0, rmin=nelx / 75.0, penal_cnt=(1, 3.0, 10 ** 6, 0.0),
+                      beta_cnt=(1, 2.0, 10 ** 6, 0.0))
+        res = {}
+        for name, prec in (("fp64_gmg", TO_FP64), ("mixed_gmg", TO_MIXED)):
+            p = default_params(2, nelx, nely, 0, ft=3, eta=0.5, beta=2.0, move=0.2, cg_rtol=1e-8, cg_maxit=100000,
+                               precision=prec, precond=TO_PC_GMG, mg_nu=1, inner_rtol=3e-3, **kw)
+            g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+            d = Design(g, torch.from_numpy(I.initial_design(g.nel, p.volfrac)).cuda())
+            for _ in range(a.warmup):
+                d.step()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            infos = [d.step() for _ in range(a.steps)]
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / a.steps
+            xt = torch.empty_like(d.xPhys)
+            g.filter(d.x, xt)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(5):
+                g.filter(d.x, xt)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = {"design_it_per_s": round(1e3 / ms, 3), "ms_per_iteration": round(ms, 3),
+                         "iterations": f"{a.warmup + 1}..{a.warmup + a.steps}",
+                         "n_cg": [i["n_cg"] for i in infos], "rel_res_max": max(i["rel_res"] for i in infos),
+                         "c_last": infos[-1]["c"],
+                         "mean_ms": {k: round(sum(i[k] for i in infos) / len(infos), 3)
+                                     for k in ("t_filter_ms", "t_solve_ms", "t_sens_ms", "t_oc_ms")},
+                         "filter_us": round(1e3 * e0.elapsed_time(e1) / 5, 2)}
+            g.close()
+        res["rmin"] = kw["rmin"]
+        res["mixed_speedup"] = round(res["fp64_gmg"]["ms_per_iteration"] / res["mixed_gmg"]["ms_per_iteration"], 2)
+        res["c_rel_diff_last"] = abs(res["mixed_gmg"]["c_last"] - res["fp64_gmg"]["c_last"]) / abs(res["fp64_gmg"]["c_last"])
+        out["grids"][spec] = res
+    print(json.dumps(out))
+
+
+def bench_learned(a):
+    """The learned warm start at the scale of the 160x80x80 workload: samples
+    (xPhys, F, and the converged compliance for the energy objective) from
+    --runs seeded cantilever-family runs of the method on 40x20x20, 60x30x30 and
+    80x40x40 grids (every design iteration after --warmup, --iters per run), a
+    BF16 network with 16 base channels trained on the GPU for --epochs, then
+    --steps design iterations of the 160x80x80 cantilever (volfrac 0.12, penal
+    3, rmin sqrt(3), beta 2 -> 16 doubling every 25, mixed precision + GMG-PCG to
+    1e-8) with and without the network from the same state, and the first state
+    solve from U = 0 with and without it."""
+    from . import TO_CNT_MUL, TO_MIXED, TO_PC_GMG, learned as Lr
+    from .topopt import Design, Grid
+    t0 = time.perf_counter()
+    shapes = [(40, 20, 20), (60, 30, 30), (80, 40, 40)]
+    samples, grids = Lr.generate_energy(shapes, runs=a.runs, iters=a.iters, seed=100, warmup=a.warmup)
+    t_gen = time.perf_counter() - t0
+    net = Lr.Net(base=16, bf16=True)
+    net.set_params(Lr.he_init(16, seed=1))
+    t0 = time.perf_counter()
+    hist = Lr.train_energy(net, samples, grids, epochs=a.epochs, lr=2e-3, lr_final=1e-4, batch=4)
+    t_train = time.perf_counter() - t0
+    n_samples = len(samples)
+    for g in grids:
+        g.close()
+    del samples, grids
+    torch.cuda.empty_cache()
+    nelx, nely, nelz = (int(v) for v in a.grid.split("x"))
+    F, fixed = I.cantilever_3d(nelx, nely, nelz)
+    p = default_params(3, nelx, nely, nelz, volfrac=0.12, penal=3.0, rmin=math.sqrt(3.0), ft=3, beta=2.0,
+                       cg_rtol=1e-8, cg_maxit=50000, precision=TO_MIXED, precond=TO_PC_GMG, mg_nu=1,
+                       inner_rtol=3e-3, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+    g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
+    d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.12)).cuda())
+    # the first state solve from U = 0, without and with the network
+    first = {}
+    snap = [t.clone() for t in (d.x, d.xPhys, d.xOld, d.U)], (d.st.eta, d.st.penal, d.st.beta, d.st.loop)
+    for mode in ("plain", "learned"):
+        for t, s in zip((d.x, d.xPhys, d.xOld, d.U), snap[0]):
+            t.copy_(s)
+        d.st.eta, d.st.penal, d.st.beta, d.st.loop = snap[1]
+        Lr.attach(g, net if mode == "learned" else None)
+        info = d.step()
+        first[mode] = {"n_cg": info["n_cg"], "warm_err": info["warm_err"], "c": info["c"],
+                       "t_solve_ms": round(info["t_solve_ms"], 2)}
+    Lr.attach(g, None)
+    for _ in range(a.warmup):
+        d.step()
+    snap = [t.clone() for t in (d.x, d.xPhys, d.xOld, d.U)], (d.st.eta, d.st.penal, d.st.beta, d.st.loop)
+    runs = {}
+    for mode in ("plain", "learned"):
+        for t, s in zip((d.x, d.xPhys, d.xOld, d.U), snap[0]):
+            t.copy_(s)
+        d.st.eta, d.st.penal, d.st.beta, d.st.loop = snap[1]
+        Lr.attach(g, net if mode == "learned" else None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        infos = [d.step() for _ in range(a.steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        runs[mode] = {"design_it_per_s": round(1e3 / ms, 3), "n_cg": [i["n_cg"] for i in infos],
+                      "warm_err": [round(i["warm_err"], 6) for i in infos],
+                      "warm_err_prev": [round(i["warm_err_prev"], 6) for i in infos],
+                      "rel_res_max": max(i["rel_res"] for i in infos), "c_last": infos[-1]["c"]}
+    Lr.attach(g, None)
+    g.close()
+    print(json.dumps({"grid": a.grid, "training_samples": n_samples, "training_shapes": shapes,
+                      "runs": a.runs, "generate_s": round(t_gen, 1), "train_s": round(t_train, 1),
+                      "epochs": a.epochs, "energy_loss_first_last": [round(hist[0], 4), round(hist[-1], 4)],
+                      "first_solve": first, "iterations": f"{a.warmup + 2}..{a.warmup + 1 + a.steps}",
+                      "runs_from_same_state": runs,
+                      "c_rel_diff": abs(runs["learned"]["c_last"] - runs["plain"]["c_last"]) /
+                      abs(runs["plain"]["c_last"])}))
 
 
 def bench_batch(a):
@@ -216,7 +361,15 @@ def bench_net(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae"])
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae", "mbb", "learned"])
+    ap.add_argument("--runs", type=int, default=100)
+    ap.add_argument("--iters", type=int, default=54)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--grids", default="300x100,600x200,1200x400")
+    ap.add_argument("--variant", default="config2", choices=["config2", "paper"])
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--cases", default="T1,T2,T3,T4")
+    ap.add_argument("--ftbc", default="N", choices=["N", "D"])
     ap.add_argument("--grid", default="256x128x128")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ku-impl", default="auto", choices=["auto", "node", "tc", "walsh", "pair"])
@@ -229,7 +382,7 @@ def main():
     a = ap.parse_args()
     B.build()
     {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc, "frame": bench_frame,
-     "pae": bench_pae}[a.what](a)
+     "pae": bench_pae, "mbb": bench_mbb, "learned": bench_learned}[a.what](a)
 
 
 if __name__ == "__main__":

@@ -41,11 +41,11 @@ def _fp(t, name, n=None, dtype=torch.float32):
 
 
 class Net:
-    def __init__(self, base=16, bf16=True, stream=None):
+    def __init__(self, base=16, bf16=True, stream=None, tensor_cores=True):
         self.lib = L.load()
         self.base = base
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        cfg = L.NetCfg(int(base), 1 if bf16 else 0, 4, 3)
+        cfg = L.NetCfg(int(base), 1 if bf16 else 0, 4, 3, 0 if tensor_cores else 1, 0)
         h = C.c_void_p()
         L.check(self.lib.to_net_create(C.byref(cfg), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h

@@ -1,12 +1,7 @@
 """The tensor-core (tcgen05, BF16 x BF16 -> FP32) forward convolutions of the
 warm-start network: against the FP64 network oracle at base 16 (every
 16/32/64-channel layer on tensor cores), and against the CUDA-core BF16 kernels
-(TOPO_NET_TC=0, read once per process, hence the subprocess) on the shape the
-96x48x48 warm start uses."""
-import os
-import subprocess
-import sys
-
+(to_net_cfg.cuda_cores_only = 1) on the shape the 96x48x48 warm start uses."""
 import numpy as np
 import pytest
 
@@ -15,9 +10,6 @@ from tests._util import rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
 
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
@@ -38,29 +30,19 @@ def test_tc_forward_matches_oracle_base16():
     assert rel(y, y_ref) <= 3e-2, rel(y, y_ref)
 
 
-SCRIPT = r'''
-import sys
-import numpy as np, torch
-sys.path.insert(0, {root!r})
-from paper_2005_05436_gb300 import learned as Lr
-net = Lr.Net(base=16, bf16=True)
-net.set_params(Lr.he_init(16, seed=5))
-r = np.random.default_rng(6)
-x = torch.from_numpy(r.standard_normal({shape} + (4,)).astype(np.float32)).cuda()
-np.save({out!r}, net.forward(x).cpu().numpy())
-'''
-
-
 @pytest.mark.parametrize("shape", [(2, 12, 16, 8), (1, 52, 28, 28)])
-def test_tc_forward_matches_cuda_core_forward(tmp_path, shape):
+def test_tc_forward_matches_cuda_core_forward(shape):
+    """The same BF16 network with its eligible layers on tensor cores and with
+    every layer on CUDA cores (to_net_cfg.cuda_cores_only): same BF16 operands
+    per layer, only the FP32 summation order differs."""
+    from paper_2005_05436_gb300 import learned as Lr
+    r = np.random.default_rng(6)
+    x = torch.from_numpy(r.standard_normal(tuple(shape) + (4,)).astype(np.float32)).cuda()
     outs = []
-    for tc in ("1", "0"):
-        out = str(tmp_path / f"y_{tc}.npy")
-        env = dict(os.environ, TOPO_NET_TC=tc)
-        res = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, shape=tuple(shape), out=out)],
-                             env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
-        assert res.returncode == 0, res.stderr[-3000:]
-        outs.append(np.load(out))
-    # same BF16 operands per layer; only the FP32 summation order differs
+    for tc in (True, False):
+        net = Lr.Net(base=16, bf16=True, tensor_cores=tc)
+        net.set_params(Lr.he_init(16, seed=5))
+        outs.append(net.forward(x).cpu().numpy())
+        net.close()
     assert rel(outs[0], outs[1]) <= 1e-2, rel(outs[0], outs[1])
     assert np.abs(outs[0]).max() > 0
