@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--loop-mode", type=int, default=0, choices=[0, 1],
                     help="0: PCG loop as one conditional-WHILE graph launch; 1: host-driven loop "
                          "of the same kernels (lets profilers see every launch)")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the PCG iteration's kernels without programmatic dependent launch")
     return ap.parse_args()
 
 
@@ -189,7 +191,7 @@ def _make_design(args, w, precision, precond, ku_impl, stream):
                        ku_impl=ku_impl, loop_mode=args.loop_mode, mg_nu=args.mg_nu,
                        inner_rtol=args.inner_rtol, mg_coarse_every=args.mg_coarse_every,
                        refine=0 if args.refine == "reliable" else 1,
-                       oc_method=0 if args.oc_method == "bisection" else 1,
+                       oc_method=0 if args.oc_method == "bisection" else 1, pdl_off=1 if args.no_pdl else 0,
                        penal_cnt=(1, 3.0, 25, 0.25),
                        beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
@@ -416,7 +418,7 @@ def run_ours(args):
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
                    "mg_nu": args.mg_nu, "inner_rtol": args.inner_rtol, "mg_coarse_every": args.mg_coarse_every,
-                   "refine": args.refine,
+                   "refine": args.refine, "pdl": not args.no_pdl,
                    "oc_method": args.oc_method,
                    "learned_warm_start": learned_info,
                    "l2": "flushed between timed steps (256 MB write)",

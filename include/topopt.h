@@ -104,7 +104,9 @@ typedef struct to_params {
     int32_t ku_impl;        /* 3D stiffness operator: 0 auto (= 3);
                                1 node-centric gather with the dense 24x24 Ke (CUDA cores, FP32 and
                                FP64); 2 tensor cores for the FP32 fine operator of TO_MIXED (tcgen05
-                               TF32 with split operands; FP64 products as 3); 3 element tiles with
+                               TF32 MMAs with split operands, element slabs streamed along x, A
+                               operands read in place from the staged node planes; FP64
+                               products as 3); 3 element tiles with
                                Ke factored in the Walsh basis of the element corners (CUDA cores,
                                FP32 and FP64); 4 as 3, with the FP32 products computed for two
                                elements per thread in paired FP32 instructions (FP64 products as 3;
@@ -148,7 +150,10 @@ typedef struct to_params {
     int32_t mg_unfused;     /* GMG, 3D coarse levels of at most 16,384 nodes: 0 prolongation fused
                                into the first post-smoothing sweep (default); 1 separate kernels
                                (same arithmetic and order, for comparison) */
-    int32_t _pad4;
+    int32_t pdl_off;        /* 0 (default): the kernels of a PCG iteration are launched with
+                               programmatic dependent launch, so that each grid is scheduled while
+                               its predecessor runs and waits for it before reading memory (same
+                               arithmetic and order); 1: plain stream-ordered launches */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */
@@ -351,6 +356,20 @@ int64_t to_kernel_launches(void);
  * around `reps` back-to-back launches on the handle's stream, in the launch
  * configuration the solver uses. */
 to_status to_time_apply_K(to_grid* g, const double* xPhys, int32_t precision, int32_t reps, double* us);
+
+/* Instrumentation (no counterpart in the paper): cost of the tensor-core
+ * instruction the FP32 operator of ku_impl 2 is built from. On every SM,
+ * blocks_per_sm (1, 2 or 4) blocks each run `issuers` (1..8) threads that
+ * issue `reps` tcgen05.mma kind::tf32 of shape m x n x 8 (m 64 or 128; n 8..256,
+ * a multiple of 16 for m = 128; issuers x n <= 512 / blocks_per_sm) into
+ * their own tensor-memory accumulators from zero-filled shared memory.
+ * cycles (host out): clock64 cycles per MMA seen by one issuing thread, from
+ * its first issue to the completion of its last; mac_per_cycle (host out):
+ * multiply-adds per cycle of one SM. Runs on the current device's default
+ * stream and waits for it; allocates and frees its own scratch. TO_EINVAL on other arguments, TO_ETIMEOUT if a
+ * completion wait passes its limit. */
+to_status to_time_tf32_mma(int32_t m, int32_t n, int32_t issuers, int32_t blocks_per_sm, int32_t reps,
+                           double* cycles, double* mac_per_cycle);
 
 /* ------------------------------------------------------------------------
  * Batched uneven 2D instances (no counterpart in the paper, which solves one

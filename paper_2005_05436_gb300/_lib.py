@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
                 ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32),
-                ("mg_unfused", C.c_int32), ("_pad4", C.c_int32)]
+                ("mg_unfused", C.c_int32), ("pdl_off", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -122,6 +122,8 @@ _SIGS = {
     "to_kernel_launches": (C.c_int64, []),
     "to_apply_K_fp32": (C.c_int, [P, P, P, P, C.c_int32]),
     "to_time_apply_K": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
+    "to_time_tf32_mma": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "to_batch_init": (C.c_int, [C.POINTER(Params), C.c_int32, C.POINTER(Instance), P, P, P, C.POINTER(P)]),
     "to_batch_offsets": (C.c_int, [P, P, P]),
     "to_batch_autotune": (C.c_int, [P, C.c_int32, C.POINTER(TileInfo)]),

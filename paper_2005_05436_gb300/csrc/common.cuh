@@ -39,6 +39,43 @@ long long captured_launches_reset();  // kernels enqueued during captures since 
         ::topo::count_launches(1);      \
     } while (0)
 
+// Programmatic dependent launch. Launches made through launch_k while
+// set_pdl(true) is in effect on the calling thread carry the programmatic
+// stream-serialisation attribute: the grid may be scheduled as soon as every
+// block of the preceding grid has passed pdl_begin(), and its own pdl_begin()
+// blocks until that grid has completed and its memory is visible. Every kernel
+// launched through launch_k calls pdl_begin() before it touches global memory;
+// for a grid launched without the attribute both instructions are no-ops.
+bool pdl_on();
+void set_pdl(bool on);
+struct PdlScope {  // set_pdl(on) for the lifetime of the scope
+    bool prev;
+    explicit PdlScope(bool on) : prev(pdl_on()) { set_pdl(on); }
+    ~PdlScope() { set_pdl(prev); }
+};
+
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_on() ? 1 : 0;
+    TOPO_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...));
+    count_launches(1);
+}
+
 #define TOPO_REQUIRE(cond, msg)                                                      \
     do {                                                                             \
         if (!(cond)) throw ::topo::Error(TO_EINVAL, msg);                            \

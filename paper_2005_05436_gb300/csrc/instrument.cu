@@ -1,5 +1,6 @@
 // Instrumentation entry points (no counterpart in the paper): kernel-launch
-// accounting and CUDA-event timing of the matrix-free operator kernel.
+// accounting, the programmatic-dependent-launch switch of the calling thread
+// and CUDA-event timing of the matrix-free operator kernel.
 #include <atomic>
 #include <string>
 
@@ -24,6 +25,10 @@ long long captured_launches_reset() {
 }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 void set_capturing(bool on) { g_capturing = on; }
+
+static thread_local bool g_pdl = false;
+bool pdl_on() { return g_pdl; }
+void set_pdl(bool on) { g_pdl = on; }
 
 }  // namespace topo
 

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(TY * TZ, (WalshMinBlocks<T, TY * TZ>::v))
     constexpr int NPRE = (PN + NT - 1) / NT;  // staged values per thread
     __shared__ __align__(16) T sp[3][PN];     // node planes in flight (three-deep pipeline)
     __shared__ T sr[2][3][TZ][TY];
+    pdl_begin();
     if (skip && *skip) return;
 
     const int tid = threadIdx.x, ty = tid % TY, tz = tid / TY;
@@ -296,10 +297,9 @@ static void walsh_launch_tile(const Dims& d, const WalshK<T>& wk, int mode, cons
         LX *= 2;
         nb = tiles * div_up(d.nnx, LX);
     }
-#define TOPO_W(MV, PV)                                                                                   \
-    k_walsh3<T, TY, TZ, MV, PV><<<(unsigned)nb, NT, 0, st>>>(d, wk, LX, ntY, ntZ, E, u, r, dinv, out, fixed, \
-                                                             mask_out ? 1 : 0, omega, skip, pcg, partials,   \
-                                                             counter)
+#define TOPO_W(MV, PV)                                                                                  \
+    launch_k(k_walsh3<T, TY, TZ, MV, PV>, (unsigned)nb, NT, 0, st, d, wk, LX, ntY, ntZ, E, u, r, dinv, out, \
+             fixed, mask_out ? 1 : 0, omega, skip, pcg, partials, counter)
     if (mode == 0 && pcg)
         TOPO_W(0, true);
     else if (mode == 1 && pcg)
@@ -311,7 +311,6 @@ static void walsh_launch_tile(const Dims& d, const WalshK<T>& wk, int mode, cons
     else
         TOPO_W(2, false);
 #undef TOPO_W
-    TOPO_CHECK_LAUNCH();
 }
 
 template <typename T>

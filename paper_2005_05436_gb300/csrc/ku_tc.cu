@@ -1,60 +1,81 @@
 // Tensor-core (tcgen05) form of the FP32 matrix-free operator K(xPhys) u on H8
-// grids: the element contraction Ke u_e of Eqs. 4-5, batched over the elements
-// of a brick, runs as TF32 MMAs with FP32 accumulation in tensor memory.
+// grids (Eqs. 4-5): the element products Ke u_e of a slab of elements run as
+// TF32 MMAs with FP32 accumulation in tensor memory; the E_e-scaled corner
+// rows are summed into nodes on the CUDA cores, with the smoother, residual
+// and PCG-dot epilogues of the fine multigrid level fused.
 //
-// A CTA owns an 8 x 4 x 4 (y, z, x) brick of nodes and computes the 9 x 5 x 5
-// elements touching it (two M = 128 row tiles, rows 225..255 zero):
-//   A[e][k] = u_e[k] - u_e[node 0 of e][k % 3]    (24 columns, K = 24)
-//   B[j][k] = Ke[j][k]                             (N = 32, rows 24..31 zero)
-//   D = A B^T  ->  D[e][j] = (Ke u_e)_j, exact for the translation shift because
-//   the rows of Ke annihilate rigid translations.
-// A and B are split into TF32 high and low parts and D = Ah Bh + Al Bh + Ah Bl,
-// which carries about 21 bits, close to FP32. Each owned node then sums, from
-// shared memory, the E_e-scaled rows of its 8 elements, so every output is
-// written by exactly one thread and the smoother / residual / PCG-dot epilogues
-// of the CUDA-core operator stay fused.
+// Blocking. A block owns a 15 x 15 column of nodes in (y, z) and LX node
+// planes along x, marching along x one element plane (slab) at a time. Its
+// elements are the 16 x 16 element columns touching those nodes (a one-element
+// halo in -y and -z), as two M = 128 tiles of 8 (y) x 16 (z) elements. Node
+// planes of 17 x 17 nodes are staged into a four-deep ring in shared memory,
+// one node per 16 bytes (u_x, u_y, u_z, 0), as the TF32 high and low parts of
+// u - c, where c is the displacement of one node of the block: the rows of Ke
+// annihilate rigid translations, so the product is unchanged while the
+// rounding acts on displacement differences (a constant added to u leaves the
+// result bit-identical).
 //
-// Operands use the canonical no-swizzle K-major layout: 8-row x 16-byte core
-// matrices, LBO = 128 B between core matrices along K, SBO = 768 B between
-// 8-row groups (6 core matrices of K per row group).
+// Operands. In the canonical no-swizzle K-major layout a core matrix is 8 rows
+// of 16 bytes, so 8 consecutive nodes along y of one staged row form a core
+// matrix as they lie. For element corner offsets (gy, gz) the A operand of a
+// tile is addressed directly in the staged planes: it starts at node
+// (8 t + gy, gz), its 8-row groups are one staged row apart (SBO) and its two K
+// halves, corners gx = 0 and gx = 1, one plane apart (LBO; for the ring slot
+// pair (3, 0) the halves are swapped and so is B). One MMA per (gy, gz) and
+// operand part: K = 8 (two corners x (3 components + a zero)), N = 32 (8
+// output corners x 3 components, then 8 zero rows). Per slab and tile
+// D = Ah Bh + Al Bh + Ah Bl, 12 MMAs, about 21 correct bits.
+//
+// Epilogue. A thread holds one element's 24 outputs (one TMEM lane) and scales
+// them by E_e; the +x corners carry to the next slab in registers, the -y
+// neighbour arrives by warp shuffle (lanes are y-consecutive in groups of 8;
+// across the tile seam through shared memory), the -z neighbour through shared
+// memory. Every node is written once, by its owner thread, in a fixed order.
+//
+// Pipeline. MMAs for slab s + 2 are issued after the barrier of slab s, into
+// the TMEM buffer slab s has just been read from (two buffers of 64 columns);
+// node plane s + 3 is loaded while slab s waits for its MMAs. Every mbarrier
+// wait is bounded; on timeout the block sets the error word and leaves the
+// loop together, waits (bounded) for the MMAs it issued and frees its TMEM.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "grid.h"
 #include "ku_device.cuh"
-#include "mg.h"
 
 namespace topo {
 
 namespace tc {
 
-constexpr int OY = 8, OZ = 4, OX = 4;              // owned nodes per CTA
-constexpr int EY = OY + 1, EZ = OZ + 1, EX = OX + 1;  // elements touching them
-constexpr int NEL = EY * EZ * EX;                  // 225
-constexpr int PY = OY + 2, PZ = OZ + 2, PX = OX + 2;  // input node patch
-constexpr int NPATCH = PY * PZ * PX;               // 360
-constexpr int ROWS = 256;                          // two M = 128 tiles
-constexpr int KDIM = 24, NDIM = 32, KG = KDIM / 4;  // K in 4-element (16 B) core columns
-constexpr int RSTRIDE = 25;                        // element-result row stride (floats)
-constexpr int NT = 256;
-constexpr int TMEM_COLS = 64;                      // two tiles x 32 columns
-constexpr long long WAIT_LIMIT = 1LL << 26;        // mbarrier polls before giving up
-
-// shared-memory layout (bytes)
-constexpr int A_BYTES = ROWS * KDIM * 4;           // 24576
-constexpr int B_BYTES = NDIM * KDIM * 4;           // 3072
-constexpr int OFF_AHI = 0;
-constexpr int OFF_ALO = OFF_AHI + A_BYTES;
-constexpr int OFF_BHI = OFF_ALO + A_BYTES;
-constexpr int OFF_BLO = OFF_BHI + B_BYTES;
-constexpr int OFF_E = OFF_BLO + B_BYTES;           // 256 floats
-constexpr int OFF_U = OFF_E + 256 * 4;             // NPATCH * 3 floats
-constexpr int OFF_BAR = OFF_U + ((NPATCH * 3 * 4 + 15) / 16) * 16;
-constexpr int SMEM_BYTES = OFF_BAR + 16;
-static_assert(NEL * RSTRIDE * 4 <= A_BYTES, "element results reuse the A(hi) buffer");
-
-// Float offset of element (row r, column k) in the core-matrix layout.
-__host__ __device__ constexpr int core_off(int r, int k) { return ((r >> 3) * KG + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+constexpr int NT = 288;                 // eight staging / epilogue warps and one MMA warp
+constexpr int NE = 256;                 // staging / epilogue threads
+constexpr int TN = 15;                 // owned nodes per block along y and along z
+constexpr int SN = TN + 2;             // staged nodes per row and rows per plane
+constexpr int ROWB = SN * 16;          // bytes per staged row (the A operand's SBO)
+constexpr int PLANEB = SN * ROWB;      // bytes per staged plane (the A operand's LBO)
+constexpr int RING = 4;
+constexpr int NSTG = (SN * SN + NE - 1) / NE;  // staged nodes per thread and plane
+constexpr int B_HL = 64 * 8;                  // floats of the N = 64 B tile [Bh | Bl] (K = 8)
+constexpr int B_H = 32 * 8;                    // floats of the N = 32 B tile Bh
+constexpr int B_SET = B_HL + B_H;
+constexpr int B_FLOATS = 2 * 4 * B_SET;        // [K order][(gy, gz)]
+constexpr int X_FLOATS = 2 * 2 * 16 * 8 * 3;   // z exchange [parity][tile][z][y][component]
+constexpr int YB_FLOATS = 2 * 16 * 6;          // tile seam [parity][z][component][gz]
+constexpr int RAW = 3;                         // planes in flight as raw FP32 (cp.async ring)
+constexpr int RAW_FLOATS = RAW * SN * SN * 3;
+constexpr int OFF_HI = 0;
+constexpr int OFF_LO = OFF_HI + RING * PLANEB;
+constexpr int OFF_B = OFF_LO + RING * PLANEB;
+constexpr int OFF_X = OFF_B + B_FLOATS * 4;
+constexpr int OFF_YB = OFF_X + X_FLOATS * 4;
+constexpr int OFF_RAW = OFF_YB + YB_FLOATS * 4;
+constexpr int OFF_BAR = (OFF_RAW + RAW_FLOATS * 4 + 15) / 16 * 16;
+constexpr int SMEM_BYTES = OFF_BAR + 8 * (RING + 8);  // mbarriers: full[RING], tdone[2][2], tfree[2][2]
+constexpr int TMEM_COLS = 256;                 // two buffers x two tiles x 64 columns
+constexpr long long WAIT_LIMIT = 1LL << 26;    // mbarrier polls before giving up
+static_assert(OFF_B % 16 == 0 && OFF_BAR % 8 == 0, "operand and barrier alignment");
+static_assert(3 * PLANEB / 16 < (1 << 14) && ROWB / 16 < (1 << 14), "descriptor offsets fit 14 bits");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,14 +95,17 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, LBO mode 0, layout SWIZZLE_NONE (0)
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, N = 32, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NDIM >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptors: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64 or 32.
+constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+constexpr uint32_t IDESC64 = idesc_tf32(64), IDESC32 = idesc_tf32(32);
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -98,7 +122,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -107,31 +143,56 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 4-byte asynchronous global -> shared copy, zero-filled when !pred.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(pred ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Offset (floats) of the B tiles of (K order, (gy, gz)) -- the N = 64 tile
+// [Bh | Bl] first, the N = 32 tile Bh after it -- and of entry (n, k) inside a
+// tile: core matrices (n / 8, k / 4) of 8 rows x 4 floats, K-adjacent ones 128
+// bytes apart (LBO), N-adjacent ones 256 bytes apart (SBO).
+__host__ __device__ constexpr int b_set(int order, int m) { return (order * 4 + m) * B_SET; }
+__host__ __device__ constexpr int b_off(int n, int k) { return ((n >> 3) * 2 + (k >> 2)) * 32 + (n & 7) * 4 + (k & 3); }
+
 }  // namespace tc
 
 template <int MODE, bool PCG>
-__global__ void __launch_bounds__(tc::NT, 2) k_fine_op3_tc(Dims d, const float* __restrict__ E,
-                                                           const float* __restrict__ u, const float* __restrict__ r,
-                                                           const float* __restrict__ dinv, float* __restrict__ out,
-                                                           const uint8_t* __restrict__ fixed, float omega,
-                                                           const float* __restrict__ Bpack, const int* skip,
-                                                           PcgScalars* pcg, double* partials, unsigned* counter,
-                                                           int* err) {
+__global__ void __launch_bounds__(tc::NT, 2)
+    k_ku_tc(Dims d, int LX, int ntY, int ntZ, const float* __restrict__ E, const float* __restrict__ u,
+            const float* __restrict__ r, const float* __restrict__ dinv, float* __restrict__ out,
+            const uint8_t* __restrict__ fixed, float omega, const float* __restrict__ Bpack, const int* skip,
+            PcgScalars* pcg, double* partials, unsigned* counter, int* err) {
     using namespace tc;
+    pdl_begin();
     if (skip && *skip) return;  // uniform, before any tensor-memory use
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* Ahi = (float*)(smem + OFF_AHI);
-    float* Alo = (float*)(smem + OFF_ALO);
-    float* Bhi = (float*)(smem + OFF_BHI);
-    float* Blo = (float*)(smem + OFF_BLO);
-    float* Es = (float*)(smem + OFF_E);
-    float* pu = (float*)(smem + OFF_U);
-    uint64_t* bar = (uint64_t*)(smem + OFF_BAR);
+    float* X = reinterpret_cast<float*>(smem + OFF_X);
+    float* YB = reinterpret_cast<float*>(smem + OFF_YB);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + OFF_BAR);  // [RING] plane staged (NE arrivals)
+    uint64_t* tdone = full + RING;                                  // [buffer][tile] MMAs complete (commit)
+    uint64_t* tfree = tdone + 4;                                    // [buffer][tile] TMEM read (128 arrivals)
     __shared__ uint32_t tmem_base;
-    __shared__ int wait_ok;
+    __shared__ int fail[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int by0 = blockIdx.x * OY, bz0 = blockIdx.y * OZ, bx0 = blockIdx.z * OX;
+    const bool epi = tid < NE;  // staging / epilogue threads; warp NE / 32 issues the MMAs
+    int bid = blockIdx.x;
+    const int tY = bid % ntY;
+    bid /= ntY;
+    const int tZ = bid % ntZ;
+    const int X0 = (bid / ntZ) * LX;
+    const int Y0 = tY * TN, Z0 = tZ * TN;  // first owned node
+    const int nny = d.nny, nnz = d.nnz, nnx = d.nnx;
+    const int nsteps = min(LX, nnx - X0);  // output planes X0 .. X0 + nsteps - 1
+    const int nslab = nsteps + 1;          // element planes X0 - 1 .. X0 + nsteps - 1
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -139,183 +200,323 @@ __global__ void __launch_bounds__(tc::NT, 2) k_fine_op3_tc(Dims d, const float* 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
-        wait_ok = 1;
-    }
-    // node patch (0 outside the grid), element moduli (0 outside), packed Ke halves
-    for (int i = tid; i < NPATCH * 3; i += NT) {
-        const int p = i / 3, c = i % 3;
-        const int py = p % PY, pz = (p / PY) % PZ, px = p / (PY * PZ);
-        const int gy = by0 - 1 + py, gz = bz0 - 1 + pz, gx = bx0 - 1 + px;
-        float v = 0.f;
-        if (gy >= 0 && gy < d.nny && gz >= 0 && gz < d.nnz && gx >= 0 && gx < d.nnx)
-            v = u[3 * (gy + (long long)d.nny * (gz + (long long)d.nnz * gx)) + c];
-        pu[i] = v;
-    }
-    for (int i = tid; i < ROWS; i += NT) {
-        float v = 0.f;
-        if (i < NEL) {
-            const int ly = i % EY, lz = (i / EY) % EZ, lx = i / (EY * EZ);
-            const int ey = by0 - 1 + ly, ez = bz0 - 1 + lz, ex = bx0 - 1 + lx;
-            if (ey >= 0 && ey < d.nely && ez >= 0 && ez < d.nelz && ex >= 0 && ex < d.nelx)
-                v = E[ey + (long long)d.nely * (ez + (long long)d.nelz * ex)];
+        for (int i = 0; i < RING; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(full + i)), "r"(NE));
+        for (int i = 0; i < 4; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(tdone + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(tfree + i)), "r"(NE / 2));
         }
-        Es[i] = v;
+        fail[0] = fail[1] = 0;
     }
-    for (int i = tid; i < 2 * NDIM * KDIM; i += NT) (i < NDIM * KDIM ? Bhi : Blo)[i % (NDIM * KDIM)] = Bpack[i];
-    __syncthreads();
-    // A rows: thread tid builds row tid (rows >= NEL are zero)
-    {
-        const int row = tid;
-        float vals[KDIM];
-        if (row < NEL) {
-            const int ly = row % EY, lz = (row / EY) % EZ, lx = row / (EY * EZ);
-            float ref[3];
+    for (int i = tid; i < B_FLOATS / 4; i += NT)
+        reinterpret_cast<float4*>(smem + OFF_B)[i] = reinterpret_cast<const float4*>(Bpack)[i];
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_before_sync();
+    __syncthreads();  // barriers, B tiles and the TMEM address published
+    fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t s_hi = smem_u32(smem + OFF_HI), s_lo = smem_u32(smem + OFF_LO), s_b = smem_u32(smem + OFF_B);
+
+    double dot_out = 0.0;  // this thread's share of the PCG dot product
+    if (!epi) {
+        // ---- MMA issue warp: slab s (planes s, s + 1) into TMEM buffer s & 1,
+        // tile t at 64 columns: Ah [Bh | Bl] + Al [Bh | 0]; completion on tdone[2 (s & 1) + t]
+        if (lane == 0) {
+            bool ok = true;
+            int issued = -1;
+            for (int s = 0; s < nslab && ok; ++s) {
+                for (int jp = s == 0 ? 0 : s + 1; jp <= s + 1 && ok; ++jp)
+                    ok = mbar_wait(smem_u32(full + (jp & (RING - 1))), (uint32_t)((jp >> 2) & 1));
+                if (ok && s >= 2)
+                    for (int tt = 0; tt < 2 && ok; ++tt)
+                        ok = mbar_wait(smem_u32(tfree + 2 * (s & 1) + tt), (uint32_t)(((s - 2) >> 1) & 1));
+                if (!ok) break;
+                fence_after_sync();
+                const int slot = s & (RING - 1);
+                const int order = slot == RING - 1 ? 1 : 0;  // ring pair (3, 0): K halves swapped
+                const uint32_t kslot = order ? 0u : (uint32_t)slot;
+                const uint32_t lbo = order ? (uint32_t)((RING - 1) * PLANEB) : (uint32_t)PLANEB;
 #pragma unroll
-            for (int M = 0; M < 8; ++M) {
-                const int p = (ly + 1 - lny(M)) + PY * ((lz + lnz(M)) + PZ * (lx + lnx(M)));
+                for (int tt = 0; tt < 2; ++tt) {
+                    const uint32_t dcol = tmem + (uint32_t)((s & 1) * 128 + tt * 64);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float v = pu[3 * p + c];
-                    if (M == 0) ref[c] = v;
-                    vals[3 * M + c] = v - ref[c];
+                    for (int m = 0; m < 4; ++m) {
+                        const int gy = m >> 1, gz = m & 1;
+                        const uint32_t aoff = kslot * PLANEB + (uint32_t)((gz * SN + 8 * tt + gy) * 16);
+                        const uint64_t bhl = make_desc(s_b + 4u * b_set(order, m), 128, 256);
+                        const uint64_t bh = make_desc(s_b + 4u * (b_set(order, m) + B_HL), 128, 256);
+                        mma_tf32(dcol, make_desc(s_hi + aoff, lbo, ROWB), bhl, IDESC64, m > 0 ? 1u : 0u);
+                        mma_tf32(dcol, make_desc(s_lo + aoff, lbo, ROWB), bh, IDESC32, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                     smem_u32(tdone + 2 * (s & 1) + tt))
+                                 : "memory");
+                }
+                issued = s;
+            }
+            if (!ok && err) atomicExch(err, (int)TO_ETIMEOUT);
+            // nothing may be in flight when the block frees its tensor memory
+            if (issued >= 0) (void)mbar_wait(smem_u32(tdone + 2 * (issued & 1) + 1), (uint32_t)((issued >> 1) & 1));
+        }
+    } else {
+        // ---- staging and epilogue warps
+        // the block's reference displacement c
+        const long long cref = 3 * (min(Y0, nny - 1) + (long long)nny * (min(Z0, nnz - 1) + (long long)nnz * min(X0, nnx - 1)));
+        const float c0 = u[cref], c1 = u[cref + 1], c2 = u[cref + 2];
+        // staged nodes of this thread: k = tid + j NE -> (ys, zs) = (k % SN, k / SN)
+        const long long pstride = 3LL * nny * nnz;
+        int goff[NSTG], soff[NSTG];
+#pragma unroll
+        for (int j = 0; j < NSTG; ++j) {
+            const int k = tid + j * NE;
+            const int ys = k % SN, zs = k / SN;
+            const int gy = Y0 - 1 + ys, gz = Z0 - 1 + zs;
+            goff[j] = (k < SN * SN && gy >= 0 && gy < nny && gz >= 0 && gz < nnz) ? 3 * (gy + nny * gz) : -1;
+            soff[j] = k < SN * SN ? (zs * SN + ys) * 16 : -1;
+        }
+        // Node plane jp: raw FP32 values by cp.async into raw slot jp % RAW (one
+        // commit group per call, empty past the last plane), then, once landed,
+        // u - c split into the TF32 parts of ring slot jp % RING, and an arrival
+        // on full[jp % RING]. Each thread converts only the values it copied.
+        float* raw = reinterpret_cast<float*>(smem + OFF_RAW);
+        auto raw_issue = [&](int jp) {
+            if (jp <= nslab) {
+                const int nx = X0 - 1 + jp;
+                const bool pv = nx >= 0 && nx < nnx;
+                float* dst = raw + (jp % RAW) * (SN * SN * 3);
+#pragma unroll
+                for (int j = 0; j < NSTG; ++j) {
+                    if (soff[j] < 0) continue;
+                    const bool ok = pv && goff[j] >= 0;
+                    const float* src = u + (ok ? nx * pstride + goff[j] : 0);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) cp_async4(dst + 3 * (tid + j * NE) + i, src + (ok ? i : 0), ok);
                 }
             }
-        } else {
+            cp_async_commit();
+        };
+        auto store_plane = [&](int jp) {
+            if (jp > nslab) return;
+            const int slot = jp & (RING - 1);
+            const int nx = X0 - 1 + jp;
+            const bool pv = nx >= 0 && nx < nnx;
+            const float* src = raw + (jp % RAW) * (SN * SN * 3);
 #pragma unroll
-            for (int k = 0; k < KDIM; ++k) vals[k] = 0.f;
-        }
-#pragma unroll
-        for (int kg = 0; kg < KG; ++kg) {
-            float4 h, l;
-            h.x = to_tf32(vals[4 * kg + 0]);
-            h.y = to_tf32(vals[4 * kg + 1]);
-            h.z = to_tf32(vals[4 * kg + 2]);
-            h.w = to_tf32(vals[4 * kg + 3]);
-            l.x = to_tf32(vals[4 * kg + 0] - h.x);
-            l.y = to_tf32(vals[4 * kg + 1] - h.y);
-            l.z = to_tf32(vals[4 * kg + 2] - h.z);
-            l.w = to_tf32(vals[4 * kg + 3] - h.w);
-            *(float4*)(Ahi + core_off(row, 4 * kg)) = h;
-            *(float4*)(Alo + core_off(row, 4 * kg)) = l;
-        }
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = tmem_base;
+            for (int j = 0; j < NSTG; ++j) {
+                if (soff[j] < 0) continue;
+                const bool ok = pv && goff[j] >= 0;  // outside the grid: 0, not -c
+                const float* w = src + 3 * (tid + j * NE);
+                const float v0 = ok ? w[0] - c0 : 0.f, v1 = ok ? w[1] - c1 : 0.f, v2 = ok ? w[2] - c2 : 0.f;
+                float4 h, l;
+                h.x = to_tf32(v0);
+                h.y = to_tf32(v1);
+                h.z = to_tf32(v2);
+                h.w = 0.f;
+                l.x = to_tf32(v0 - h.x);
+                l.y = to_tf32(v1 - h.y);
+                l.z = to_tf32(v2 - h.z);
+                l.w = 0.f;
+                *reinterpret_cast<float4*>(smem + OFF_HI + slot * PLANEB + soff[j]) = h;
+                *reinterpret_cast<float4*>(smem + OFF_LO + slot * PLANEB + soff[j]) = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(full + slot)) : "memory");
+        };
 
-    if (tid == 0) {
-        const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+        // this thread's element column: tile t, TMEM lane row; (yl, zl) in the block's element frame
+        const int t = warp >> 2, row = 32 * (warp & 3) + lane;
+        const int yq = row & 7, zl = row >> 3, yl = 8 * t + yq;
+        const int ey = Y0 - 1 + yl, ez = Z0 - 1 + zl;
+        const bool eyz = ey >= 0 && ey < d.nely && ez >= 0 && ez < d.nelz;
+        const long long eoff = ey + (long long)d.nely * ez, estride = (long long)d.nely * d.nelz;
+        auto loadE = [&](int s) {
+            const int ex = X0 - 1 + s;
+            return (eyz && ex >= 0 && ex < d.nelx) ? E[eoff + ex * estride] : 0.f;
+        };
+        const bool owner = yl >= 1 && zl >= 1 && ey < nny && ez < nnz;  // node (ey, ez) of each plane
+
+        // prologue: planes 0, 1, 2 staged, 3 and 4 in flight
+        raw_issue(0);
+        raw_issue(1);
+        raw_issue(2);
+        cp_async_wait<0>();
+        store_plane(0);
+        store_plane(1);
+        store_plane(2);
+        raw_issue(3);
+        raw_issue(4);
+
+        float Enext = loadE(0);
+        float cin[3][4];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const uint32_t dt = tmem + 32 * t;                 // column offset of tile t
-            const uint32_t arow = (uint32_t)(t * 16 * KG * 128);  // 16 row groups per tile
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                const uint32_t kofs = (uint32_t)(2 * s * 128);      // two core columns per K step
-                const uint64_t dah = make_desc(ahi + arow + kofs, 128, KG * 128);
-                const uint64_t dal = make_desc(alo + arow + kofs, 128, KG * 128);
-                const uint64_t dbh = make_desc(bhi + kofs, 128, KG * 128);
-                const uint64_t dbl = make_desc(blo + kofs, 128, KG * 128);
-                mma_tf32(dt, dah, dbh, s > 0 ? 1u : 0u);
-                mma_tf32(dt, dal, dbh, 1u);
-                mma_tf32(dt, dah, dbl, 1u);
+            for (int q = 0; q < 4; ++q) cin[i][q] = 0.f;
+        // epilogue operands of the owned node in output plane X0 - 1 + s, fetched one slab ahead
+        float rn[3], dn[3], un[3];
+        unsigned fn[3];  // the raw flags: tested where used, so the load does not stall the fetch
+        auto fetch = [&](int s1) {
+            const bool em = s1 > 0 && s1 < nslab && owner;
+            const long long g1 = 3 * (ey + (long long)nny * (ez + (long long)nnz * (X0 - 1 + s1)));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                rn[i] = (MODE != 0 && em) ? r[g1 + i] : 0.f;
+                dn[i] = (MODE == 1 && em) ? dinv[g1 + i] : 0.f;
+                un[i] = ((MODE == 1 || PCG) && em) ? u[g1 + i] : 0.f;
+                fn[i] = em ? (unsigned)fixed[g1 + i] : 0u;
+            }
+        };
+        fetch(1);
+        DotAcc<float> dot;
+        for (int s = 0; s < nslab; ++s) {
+            raw_issue(s + 5);  // two slabs of slack for the copy
+            const float Es = Enext;
+            if (s + 1 < nslab) Enext = loadE(s + 1);
+            const bool emit = s > 0 && owner;  // output node plane X0 - 1 + s
+            const long long gn = 3 * (ey + (long long)nny * (ez + (long long)nnz * (X0 - 1 + s)));
+            float rr[3], di[3], uo[3];
+            unsigned fx[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                rr[i] = rn[i];
+                di[i] = dn[i];
+                uo[i] = un[i];
+                fx[i] = fn[i];
+            }
+            if (s > 0) fetch(s + 1);  // (at s = 0 the registers already hold slab 1)
+            const int par = s & 1;
+            if (!mbar_wait(smem_u32(tdone + 2 * par + t), (uint32_t)((s >> 1) & 1))) {
+                fail[par] = 1;
+                if (err) atomicExch(err, (int)TO_ETIMEOUT);
+            }
+            fence_after_sync();
+            float D[24];
+            {
+                float Dl[24];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(par * 128 + t * 64);
+                tmem_ld16(taddr, D);
+                tmem_ld8(taddr + 16, D + 16);
+                tmem_ld16(taddr + 32, Dl);
+                tmem_ld8(taddr + 48, Dl + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int n = 0; n < 24; ++n) D[n] += Dl[n];  // (Ah Bh + Al Bh) + Ah Bl
+            }
+            fence_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(tfree + 2 * par + t)) : "memory");
+            // x: the gx = 0 corners of this slab plus the carried gx = 1 corners of the previous one;
+            // corner q = 2 hy + hz of output row 3 (4 hx + q) + i
+            float p[3][4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    p[i][q] = fmaf(Es, D[3 * q + i], cin[i][q]);
+                    cin[i][q] = Es * D[3 * (4 + q) + i];
+                }
+            // y: the hy = 1 corners of the element column at yl - 1 (lane - 1 inside a group of 8)
+            float q0[3], q1[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float y0 = __shfl_up_sync(0xffffffffu, p[i][2], 1, 8);
+                const float y1 = __shfl_up_sync(0xffffffffu, p[i][3], 1, 8);
+                q0[i] = p[i][0] + (yq ? y0 : 0.f);
+                q1[i] = p[i][1] + (yq ? y1 : 0.f);
+            }
+            float* Xp = X + par * (X_FLOATS / 2);
+            float* Yp = YB + par * (YB_FLOATS / 2);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Xp[((t * 16 + zl) * 8 + yq) * 3 + i] = q1[i];
+            if (t == 0 && yq == 7) {  // the tile seam: tile 1's first y row needs these
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    Yp[(zl * 3 + i) * 2] = p[i][2];
+                    Yp[(zl * 3 + i) * 2 + 1] = p[i][3];
+                }
+            }
+            // plane s + 3 goes to the ring slot of plane s - 1, which the MMAs of slab s - 1
+            // (both tiles, issued before those of slab s this thread waited for) no longer read
+            cp_async_wait<2>();  // plane s + 3 has landed (s + 4, s + 5 may be in flight)
+            store_plane(s + 3);
+            asm volatile("bar.sync 1, %0;\n" ::"n"(NE) : "memory");  // the staging / epilogue warps only
+            if (fail[par]) break;  // the same value in every thread: written before this barrier only
+            if (emit) {
+                // z: the gz = 1 corners of the element column at zl - 1
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float o = q0[i] + Xp[((t * 16 + zl - 1) * 8 + yq) * 3 + i];
+                    if (t == 1 && yq == 0) o += Yp[(zl * 3 + i) * 2] + Yp[((zl - 1) * 3 + i) * 2 + 1];
+                    if (MODE == 1) o = uo[i] + omega * di[i] * (rr[i] - o);
+                    if (MODE == 2) o = rr[i] - o;
+                    if (fx[i] != 0u) o = 0.f;
+                    out[gn + i] = o;
+                    if (PCG) dot.add(MODE == 1 ? rr[i] : uo[i], o);
+                }
             }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         smem_u32(bar))
-                     : "memory");
+        cp_async_wait<0>();
+        if (PCG) dot_out = dot.value();
     }
-    if (!mbar_wait(smem_u32(bar), 0)) {
-        wait_ok = 0;
-        if (err) atomicExch(err, (int)TO_ETIMEOUT);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // D rows back to registers: warp w reads tile w / 4, lanes 32 (w % 4) ...
-    float dv[KDIM];
-    {
-        const int t = warp >> 2, q = warp & 3;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * t);
-        float v8[8];
-#pragma unroll
-        for (int c8 = 0; c8 < 3; ++c8) {
-            tc::tmem_ld8(taddr + 8 * c8, v8);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) dv[8 * c8 + i] = v8[i];
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();  // all MMAs consumed: A(hi) becomes the element-result buffer
-    {
-        const int row = 128 * (warp >> 2) + 32 * (warp & 3) + lane;
-        float* R = Ahi;
-        if (row < NEL) {
-            const float s = wait_ok ? Es[row] : 0.f;
-#pragma unroll
-            for (int j = 0; j < KDIM; ++j) R[row * RSTRIDE + j] = s * dv[j];
-        }
-    }
+    fence_before_sync();
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        fence_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
     }
-    // owned nodes: sum the rows of their 8 elements, fused epilogue
-    DotAcc<float> dot;
-    const float* R = Ahi;
-    for (int item = tid; item < OY * OZ * OX * 3; item += NT) {
-        const int o = item / 3, c = item % 3;
-        const int oy = o % OY, oz = (o / OY) % OZ, ox = o / (OY * OZ);
-        const int iy = by0 + oy, iz = bz0 + oz, ix = bx0 + ox;
-        if (iy >= d.nny || iz >= d.nnz || ix >= d.nnx) continue;
-        float a = 0.f;
-#pragma unroll
-        for (int e8 = 0; e8 < 8; ++e8) {
-            const int exo = e8 >> 2, ezo = (e8 >> 1) & 1, eyo = e8 & 1;
-            const int row = (oy + eyo) + EY * ((oz + ezo) + EZ * (ox + exo));
-            const int L = local_node(1 - exo, eyo, 1 - ezo);
-            a += R[row * RSTRIDE + 3 * L + c];
-        }
-        const long long i = 3 * (iy + (long long)d.nny * (iz + (long long)d.nnz * ix)) + c;
-        float o_ = a;
-        if (MODE == 1) o_ = u[i] + omega * dinv[i] * (r[i] - a);
-        if (MODE == 2) o_ = r[i] - a;
-        if (fixed[i]) o_ = 0.f;
-        out[i] = o_;
-        if (PCG) dot.add(u[i], o_);
-    }
     if (PCG) {
-        double v[1] = {dot.value()}, tot[1];
-        if (last_block_totals<tc::NT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
-            pcg->pAp = tot[0];
-            pcg->alpha = pcg->rz / tot[0];
+        double vv[1] = {dot_out}, tot[1];
+        if (last_block_totals<NT, 1>(vv, partials, counter, tot) && threadIdx.x == 0) {
+            if (MODE == 1) {  // last V-cycle sweep: rz = r.z, beta = rz / rz_old
+                pcg->beta = tot[0] / pcg->rz;
+                pcg->rz = tot[0];
+            } else {          // K p: alpha = rz / p.Ap
+                pcg->pAp = tot[0];
+                pcg->alpha = pcg->rz / tot[0];
+            }
         }
     }
 }
 
-// Pack Ke (FP32) into the B operand: high and low TF32 halves, N = 32 rows
-// (24..31 zero), core-matrix layout; [2][32 * 24] floats.
+// Round to TF32 as cvt.rna does (nearest, ties away from zero).
 static float tf32_host(float v) {
     uint32_t b;
     std::memcpy(&b, &v, 4);
-    if ((b & 0x7f800000u) != 0x7f800000u) b = (b + 0x1000u) & 0xffffe000u;  // round half away from zero
+    if ((b & 0x7f800000u) != 0x7f800000u) b = (b + 0x1000u) & 0xffffe000u;
     float r;
     std::memcpy(&r, &b, 4);
     return r;
 }
 
+// Pack Ke (rounded to FP32) as the B operand tiles of the tensor-core operator.
+// For each K order (gx = 0 then 1, or swapped) and element corner offsets
+// (gy, gz): an N = 64 tile whose rows n < 24 hold the TF32 high part of
+// B[n][k] = Ke[3 Lo + co][3 Li + ci] and rows 32 + n its TF32 low part, and an
+// N = 32 tile of the high part alone; n = 3 (4 hx + 2 hy + hz) + co, k =
+// 4 (gx or 1 - gx) + ci (ci = 3 and the other rows zero); Lo, Li the local node
+// numbers of the output corner (hx, hy, hz) and the input corner (gx, gy, gz)
+// of the element in grid orientation.
 void tc_pack_ke(const std::vector<double>& Ke, std::vector<float>& pack) {
     using namespace tc;
-    pack.assign(2 * NDIM * KDIM, 0.f);
-    for (int j = 0; j < NDIM; ++j)
-        for (int k = 0; k < KDIM; ++k) {
-            const float v = j < 24 ? (float)Ke[(size_t)j * 24 + k] : 0.f;
-            const float h = tf32_host(v);
-            pack[core_off(j, k)] = h;
-            pack[NDIM * KDIM + core_off(j, k)] = tf32_host(v - h);
+    pack.assign(B_FLOATS, 0.f);
+    auto lof = [](int gx, int gy, int gz) { return local_node(gx, 1 - gy, gz); };
+    for (int order = 0; order < 2; ++order)
+        for (int m = 0; m < 4; ++m) {
+            const int gy = m >> 1, gz = m & 1;
+            float* hl = pack.data() + b_set(order, m);
+            float* h_only = hl + B_HL;
+            for (int n = 0; n < 24; ++n) {
+                const int go = n / 3, co = n % 3;
+                const int Lo = lof(go >> 2, (go >> 1) & 1, go & 1);
+                for (int k = 0; k < 8; ++k) {
+                    const int ci = k & 3;
+                    if (ci == 3) continue;
+                    const int gx = order ? 1 - (k >> 2) : (k >> 2);
+                    const float v = (float)Ke[(size_t)(3 * Lo + co) * 24 + 3 * lof(gx, gy, gz) + ci];
+                    const float h = tf32_host(v);
+                    hl[b_off(n, k)] = h;
+                    hl[b_off(32 + n, k)] = tf32_host(v - h);
+                    h_only[b_off(n, k)] = h;
+                }
+            }
         }
 }
 
@@ -323,16 +524,26 @@ template <int MODE, bool PCG>
 static void tc_dispatch(const to_grid* g, const float* E, const float* u, const float* r, const float* dinv, float* out,
                         float omega, const int* skip, PcgScalars* pcg, cudaStream_t st) {
     using namespace tc;
-    static bool attr_set = false;
+    static bool attr_set = false;  // the same attribute value on every call
     if (!attr_set) {
-        TOPO_CUDA(cudaFuncSetAttribute(k_fine_op3_tc<MODE, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        TOPO_CUDA(cudaFuncSetAttribute(k_ku_tc<MODE, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
         attr_set = true;
     }
     const Dims& d = g->d;
-    dim3 grid(div_up(d.nny, OY), div_up(d.nnz, OZ), div_up(d.nnx, OX));
-    k_fine_op3_tc<MODE, PCG><<<grid, NT, SMEM_BYTES, st>>>(d, E, u, r, dinv, out, g->fixed, omega, g->ke_tc, skip, pcg,
-                                                         g->partials, g->counter, g->tc_err);
-    TOPO_CHECK_LAUNCH();
+    const int ntY = div_up(d.nny, TN), ntZ = div_up(d.nnz, TN);
+    const long long tiles = (long long)ntY * ntZ;
+    const int nsm = g->nsm > 0 ? g->nsm : 148;
+    // about four blocks per SM over the launch, at least four planes per block
+    // (the first element plane of a block only carries into the next)
+    const long long chunks = std::max<long long>(1, 4LL * nsm / tiles);
+    int LX = std::max(4, div_up(d.nnx, chunks));
+    long long nb = tiles * div_up(d.nnx, LX);
+    while (PCG && nb > g->npartials) {  // one partial per block
+        LX *= 2;
+        nb = tiles * div_up(d.nnx, LX);
+    }
+    launch_k(k_ku_tc<MODE, PCG>, (unsigned)nb, NT, SMEM_BYTES, st, d, LX, ntY, ntZ, E, u, r, dinv, out,
+             (const uint8_t*)g->fixed, omega, (const float*)g->ke_tc, skip, pcg, g->partials, g->counter, g->tc_err);
 }
 
 void launch_fine_op_tc(const to_grid* g, int mode, const float* E, const float* u, const float* r, const float* dinv,
@@ -342,6 +553,8 @@ void launch_fine_op_tc(const to_grid* g, int mode, const float* E, const float* 
         tc_dispatch<0, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
     else if (mode == 0)
         tc_dispatch<0, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
+    else if (mode == 1 && pcg)
+        tc_dispatch<1, true>(g, E, u, r, dinv, out, omega, skip, pcg, st);
     else if (mode == 1)
         tc_dispatch<1, false>(g, E, u, r, dinv, out, omega, skip, nullptr, st);
     else

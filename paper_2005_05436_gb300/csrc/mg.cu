@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, c
                                                   const uint8_t* __restrict__ fixed, T omega,
                                                   const int* skip, PcgScalars* pcg, double* partials,
                                                   unsigned* counter) {
+    pdl_begin();
     if (skip && *skip) return;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     DotAcc<T> dot;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, co
                                                   const uint8_t* __restrict__ fixed, T omega,
                                                   const int* skip, PcgScalars* pcg, double* partials,
                                                   unsigned* counter) {
+    pdl_begin();
     if (skip && *skip) return;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     DotAcc<T> dot;
@@ -110,12 +112,11 @@ static void fine_op_dispatch(const to_grid* g, const T* E, const T* u, const T* 
         return;
     }
     if (d.dim == 3)
-        k_fine_op3<T, MODE, PCG><<<nb, 256, 0, st>>>(d, grid_ke3<T>(g), E, u, r, dinv, out, g->fixed, omega,
-                                                     skip, pcg, g->partials, g->counter);
+        launch_k(k_fine_op3<T, MODE, PCG>, nb, 256, 0, st, d, grid_ke3<T>(g), E, u, r, dinv, out, g->fixed, omega,
+                 skip, pcg, g->partials, g->counter);
     else
-        k_fine_op2<T, MODE, PCG><<<nb, 256, 0, st>>>(d, grid_ke2<T>(g), E, u, r, dinv, out, g->fixed, omega,
-                                                     skip, pcg, g->partials, g->counter);
-    TOPO_CHECK_LAUNCH();
+        launch_k(k_fine_op2<T, MODE, PCG>, nb, 256, 0, st, d, grid_ke2<T>(g), E, u, r, dinv, out, g->fixed, omega,
+                 skip, pcg, g->partials, g->counter);
 }
 
 template <typename T>
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict_
                                                     const int* skip) {
     constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
     constexpr bool REL = rel_form<T>();
+    pdl_begin();
     if (skip && *skip) return;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.nnodes) return;
@@ -561,6 +563,7 @@ __global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restric
                                                       const T* __restrict__ dinv, T* __restrict__ out,
                                                       const uint8_t* __restrict__ fixed, T omega,
                                                       const int* skip) {
+    pdl_begin();
     if (skip && *skip) return;
     stencil_op3s_body<T, MODE>(blockIdx.x, d, S, R, u, r, dinv, out, fixed, omega);
 }
@@ -573,6 +576,7 @@ template <typename T, int DIM>
 __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __restrict__ rc,
                            const uint8_t* __restrict__ fixed_c, const int* skip, const T* __restrict__ dinv_c,
                            T* __restrict__ z_c, T omega) {
+    pdl_begin();
     if (skip && *skip) return;
     const long long N = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (N >= dc.nnodes) return;
@@ -648,6 +652,7 @@ __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* _
                                                     T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
                                                     const int* skip, const T* __restrict__ dinv_c,
                                                     T* __restrict__ z_c, T omega) {
+    pdl_begin();
     if (skip && *skip) return;
     restrict3s_body<T>(blockIdx.x, dc, df, rf, rc, fixed_c, dinv_c, z_c, omega);
 }
@@ -655,6 +660,7 @@ __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* _
 template <typename T, int DIM>
 __global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __restrict__ zf,
                               const uint8_t* __restrict__ fixed_f, const int* skip) {
+    pdl_begin();
     if (skip && *skip) return;
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= df.nnodes) return;
@@ -791,6 +797,7 @@ __global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, co
                                                           const T* __restrict__ dinv, T* __restrict__ out,
                                                           const uint8_t* __restrict__ fixed, T omega,
                                                           const int* skip) {
+    pdl_begin();
     if (skip && *skip) return;
     prolong_smooth3s_body<T, TY>(blockIdx.x, d, dc, zc, cur, S, R, r, dinv, out, fixed, omega);
 }
@@ -813,6 +820,7 @@ inline int prolong_smooth_ty(const Dims& d) {
 template <typename T>
 __global__ void k_jacobi_first(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
                                T omega, const int* skip) {
+    pdl_begin();
     if (skip && *skip) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) z[i] = omega * dinv[i] * r[i];
@@ -1049,6 +1057,7 @@ __global__ void k_chol_wtw(int n, const T* __restrict__ W, const uint8_t* __rest
 template <typename T>
 __global__ void k_dense_apply(int n, const T* __restrict__ Ainv, const T* __restrict__ r, T* __restrict__ z,
                               const int* skip) {
+    pdl_begin();
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1264,22 +1273,18 @@ static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T
     }
     const int nb = div_up(L.d.nnodes, 256);
     const T w = mg->omega;
-#define TOPO_SOP(DIMV, MODEV)                                                                      \
-    k_stencil_op<T, DIMV, MODEV><<<nb, 256, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip)
+#define TOPO_SOP(DIMV, MODEV) \
+    launch_k(k_stencil_op<T, DIMV, MODEV>, nb, 256, 0, st, L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip)
+#define TOPO_SOP3(MODEV)                                                                                  \
+    launch_k(k_stencil_op3s<T, MODEV>, div_up(L.d.nnodes, 32), dim3(32, 9), 0, st, L.d, L.S, L.R, u, r, \
+             L.dinv, out, L.fixed, w, skip)
     if (L.d.dim == 3) {
-        const dim3 blk(32, 9);
-        const int nbs = div_up(L.d.nnodes, 32);
-        if (mode == 1)
-            k_stencil_op3s<T, 1><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
-        else if (mode == 2)
-            k_stencil_op3s<T, 2><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
-        else
-            k_stencil_op3s<T, 0><<<nbs, blk, 0, st>>>(L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip);
+        if (mode == 1) TOPO_SOP3(1); else if (mode == 2) TOPO_SOP3(2); else TOPO_SOP3(0);
     } else {
         if (mode == 1) TOPO_SOP(2, 1); else if (mode == 2) TOPO_SOP(2, 2); else TOPO_SOP(2, 0);
     }
+#undef TOPO_SOP3
 #undef TOPO_SOP
-    TOPO_CHECK_LAUNCH();
 }
 
 template <typename T>
@@ -1288,14 +1293,13 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
     MGLevel<T>& L = mg->lev[l];
     const bool coarsest = l == mg->nlev - 1;
     if (coarsest && mg->nc > 0) {
-        k_dense_apply<T><<<div_up((long long)mg->nc * 32, 256), 256, 0, st>>>(mg->nc, mg->Ainv, rhs, L.z, skip);
-        TOPO_CHECK_LAUNCH();
+        launch_k(k_dense_apply<T>, div_up((long long)mg->nc * 32, 256), 256, 0, st, mg->nc, (const T*)mg->Ainv,
+                 rhs, L.z, skip);
         return L.z;
     }
-    if (!first_done) {
-        k_jacobi_first<T><<<div_up(L.d.ndof, 256), 256, 0, st>>>(L.d.ndof, L.dinv, rhs, L.z, mg->omega, skip);
-        TOPO_CHECK_LAUNCH();
-    }
+    if (!first_done)
+        launch_k(k_jacobi_first<T>, div_up(L.d.ndof, 256), 256, 0, st, L.d.ndof, (const T*)L.dinv, rhs, L.z,
+                 mg->omega, skip);
     T* cur = L.z;
     T* oth = L.t;
     const int nu = coarsest ? 4 * mg->nu : mg->nu;
@@ -1313,11 +1317,11 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         const bool jf = !(l + 1 == mg->nlev - 1 && mg->nc > 0);
         const T* dc_inv = jf ? C.dinv : nullptr;
         if (L.d.dim == 3)
-            k_restrict3s<T><<<div_up(C.d.nnodes, 32), dim3(32, 9), 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip,
-                                                                            dc_inv, C.z, mg->omega);
+            launch_k(k_restrict3s<T>, div_up(C.d.nnodes, 32), dim3(32, 9), 0, st, C.d, L.d, (const T*)L.w, C.r,
+                     (const uint8_t*)C.fixed, skip, dc_inv, C.z, mg->omega);
         else
-            k_restrict<T, 2><<<nbc, 256, 0, st>>>(C.d, L.d, L.w, C.r, C.fixed, skip, dc_inv, C.z, mg->omega);
-        TOPO_CHECK_LAUNCH();
+            launch_k(k_restrict<T, 2>, nbc, 256, 0, st, C.d, L.d, (const T*)L.w, C.r, (const uint8_t*)C.fixed,
+                     skip, dc_inv, C.z, mg->omega);
         T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st, nullptr, nullptr, jf);
         // small levels only: on a large one the halo's repeated prolongation costs
         // more loads than the separate kernel (tiles are one node thick in x)
@@ -1326,9 +1330,9 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
             const int ty = prolong_smooth_ty(L.d);
             const long long nb = (long long)div_up(L.d.nny, ty) * div_up(L.d.nnz, 32 / ty) * L.d.nnx;
             const dim3 blk(32, 9);
-#define TOPO_PS(TYV)                                                                                          \
-    k_prolong_smooth3s<T, TYV><<<(unsigned)nb, blk, 0, st>>>(L.d, C.d, zc, cur, L.S, L.R, rhs, L.dinv, oth, \
-                                                             L.fixed, mg->omega, skip)
+#define TOPO_PS(TYV)                                                                                   \
+    launch_k(k_prolong_smooth3s<T, TYV>, (unsigned)nb, blk, 0, st, L.d, C.d, (const T*)zc, (const T*)cur, \
+             (const T*)L.S, (const T*)L.R, rhs, (const T*)L.dinv, oth, (const uint8_t*)L.fixed, mg->omega, skip)
             if (ty == 8)
                 TOPO_PS(8);
             else if (ty == 16)
@@ -1336,15 +1340,15 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
             else
                 TOPO_PS(32);
 #undef TOPO_PS
-            TOPO_CHECK_LAUNCH();
             std::swap(cur, oth);
             s0 = 1;
         } else {
             if (L.d.dim == 3)
-                k_prolong_add<T, 3><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
+                launch_k(k_prolong_add<T, 3>, nbf, 256, 0, st, L.d, C.d, (const T*)zc, cur,
+                         (const uint8_t*)L.fixed, skip);
             else
-                k_prolong_add<T, 2><<<nbf, 256, 0, st>>>(L.d, C.d, zc, cur, L.fixed, skip);
-            TOPO_CHECK_LAUNCH();
+                launch_k(k_prolong_add<T, 2>, nbf, 256, 0, st, L.d, C.d, (const T*)zc, cur,
+                         (const uint8_t*)L.fixed, skip);
         }
     }
     for (int s = s0; s < nu; ++s) {

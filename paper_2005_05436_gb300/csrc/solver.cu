@@ -69,6 +69,7 @@ template <typename T, bool FIRST, bool JAC>
 __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restrict__ r, T* __restrict__ z,
                                                  const T* __restrict__ dinv, T* __restrict__ p, PcgScalars* s,
                                                  double* partials, unsigned* counter) {
+    pdl_begin();
     if (s->done) return;
     DotAcc<T> acc;
     double tot[1];
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
                                                  const T* __restrict__ p, const T* __restrict__ Ap, PcgScalars* s,
                                                  double* partials, unsigned* counter, const T* __restrict__ dinv0,
                                                  T* __restrict__ z0, T omega) {
+    pdl_begin();
     if (s->done) return;
     const T alpha = (T)s->alpha;
     DotAcc<T> acc;
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
 template <typename T>
 __global__ void k_gpcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const PcgScalars* s,
                          cudaGraphConditionalHandle cond, int set_cond) {
+    pdl_begin();
     const int done = s->done;
     if (!done) {
         const T beta = (T)s->beta;
@@ -252,6 +255,7 @@ struct Pcg {
     PcgScalars* s = nullptr;     // device
     cudaGraphExec_t loop = nullptr;
     long long body_kernels = 0;  // kernels per loop iteration
+    bool pdl = false;            // the body's kernels use programmatic dependent launch
     T* z = nullptr;              // preconditioner output buffer (fixed at capture)
 };
 
@@ -310,32 +314,26 @@ static void enqueue_body(to_grid* g, Pcg<T>& P, cudaGraphConditionalHandle cond,
     const int* skip = &P.s->done;
     launch_fine_op<T>(g, 0, P.E, P.p, nullptr, nullptr, P.Ap, T(0), skip, P.s, st);
     const MGLevel<T>* L0 = P.mg ? &P.mg->lev[0] : nullptr;
-    k_gpcg_xr<T><<<kblocks(n), KNT, 0, st>>>(n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter,
-                                             L0 ? L0->dinv : nullptr, L0 ? L0->z : nullptr,
-                                             P.mg ? P.mg->omega : T(0));
-    TOPO_CHECK_LAUNCH();
+    launch_k(k_gpcg_xr<T>, kblocks(n), KNT, 0, st, n, P.x, P.r, P.p, P.Ap, P.s, g->partials, g->counter,
+             L0 ? L0->dinv : nullptr, L0 ? L0->z : nullptr, P.mg ? P.mg->omega : T(0));
     if (P.mg) {
-        // the tensor-core operator has no fused r.z epilogue
-        const bool tc = sizeof(T) == 4 && g->use_tc;
         bool fused = false;
-        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st, tc ? nullptr : P.s, &fused, true);
-        if (!fused) {
-            k_gpcg_rz<T, false, false><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, nullptr, nullptr, P.s, g->partials,
-                                                                   g->counter);
-            TOPO_CHECK_LAUNCH();
-        }
+        P.z = mg_vcycle<T>(g, P.mg, P.r, skip, st, P.s, &fused, true);
+        if (!fused)
+            launch_k(k_gpcg_rz<T, false, false>, kblocks(n), KNT, 0, st, n, P.r, P.z, (const T*)nullptr,
+                     (T*)nullptr, P.s, g->partials, g->counter);
     } else {
         P.z = P.zj;
-        k_gpcg_rz<T, false, true><<<kblocks(n), KNT, 0, st>>>(n, P.r, P.z, P.mg ? nullptr : P.dinv_j, nullptr,
-                                                              P.s, g->partials, g->counter);
-        TOPO_CHECK_LAUNCH();
+        launch_k(k_gpcg_rz<T, false, true>, kblocks(n), KNT, 0, st, n, P.r, P.z, P.dinv_j, (T*)nullptr, P.s,
+                 g->partials, g->counter);
     }
-    k_gpcg_p<T><<<div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st>>>(n, P.z, P.p, P.s, cond, set_cond);
-    TOPO_CHECK_LAUNCH();
+    launch_k(k_gpcg_p<T>, div_up(n, 256) < 2048 ? div_up(n, 256) : 2048, 256, 0, st, n, P.z, P.p, P.s, cond,
+             set_cond);
 }
 
 template <typename T>
-static void build_loop_graph(to_grid* g, Pcg<T>& P) {
+static void build_loop_graph(to_grid* g, Pcg<T>& P, bool pdl) {
+    PdlScope pdl_scope(pdl);
     cudaGraph_t graph = nullptr;
     TOPO_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle cond;
@@ -360,8 +358,19 @@ static void build_loop_graph(to_grid* g, Pcg<T>& P) {
     }
     set_capturing(false);
     TOPO_CUDA(cudaStreamEndCapture(g->st, &body));
-    TOPO_CUDA(cudaGraphInstantiate(&P.loop, graph, 0));
-    TOPO_CUDA(cudaGraphDestroy(graph));
+    const cudaError_t e = cudaGraphInstantiate(&P.loop, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        P.loop = nullptr;
+        (void)cudaGetLastError();
+        if (pdl) {  // programmatic edges refused in the body: plain launches
+            captured_launches_reset();
+            build_loop_graph<T>(g, P, false);
+            return;
+        }
+        TOPO_CUDA(e);
+    }
+    P.pdl = pdl;
 }
 
 // Set up the preconditioner from P.E (when `setup`), r = b - K x (or r = b for
@@ -388,9 +397,10 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
     if (setup) precond_setup<T>(g, P, st);
     if (P.mg) mg_wait_coarse<T>(P.mg, st);
     if (!P.loop) {
-        build_loop_graph<T>(g, P);
+        build_loop_graph<T>(g, P, g->p.pdl_off == 0);
         P.body_kernels = captured_launches_reset();
     }
+    PdlScope pdl_scope(P.pdl);
     TOPO_CUDA(cudaEventRecord(sv->ev[1], st));
     if (resume) {
         k_pcg_resume<<<1, 1, 0, st>>>(P.s, rtol * rtol, maxit);

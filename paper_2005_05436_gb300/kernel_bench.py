@@ -45,6 +45,24 @@ def bench_ku(a):
                       "us_per_launch": round(us, 3), **{k: round(v, 3) for k, v in rate.items()}}))
 
 
+def bench_mma(a):
+    """Cost of one tcgen05.mma kind::tf32 (K = 8) by shape, issuing threads per
+    block and blocks per SM (to_time_tf32_mma): the instruction the tensor-core
+    FP32 operator is built from."""
+    import ctypes as C
+    from . import _lib as L
+    lib = L.load()
+    cases = [(128, 32, 1, 1), (128, 64, 1, 1), (128, 128, 1, 1), (128, 256, 1, 1), (64, 32, 1, 1), (64, 256, 1, 1),
+             (128, 32, 2, 1), (128, 32, 4, 1), (128, 32, 8, 1), (128, 64, 4, 1), (128, 32, 1, 2), (128, 32, 1, 4),
+             (128, 32, 2, 2), (128, 64, 2, 2), (128, 256, 1, 2)]
+    for m, n, iss, bps in cases:
+        cyc, mac = C.c_double(), C.c_double()
+        L.check(lib.to_time_tf32_mma(m, n, iss, bps, a.reps, C.byref(cyc), C.byref(mac)))
+        print(json.dumps({"m": m, "n": n, "k": 8, "issuers_per_block": iss, "blocks_per_sm": bps,
+                          "cycles_per_mma_per_issuer": round(cyc.value, 1),
+                          "mac_per_cycle_per_sm": round(mac.value, 1)}))
+
+
 def bench_oc(a):
     """OC update (to_oc_update) with the bisection (paper tolerance 1e-4), the
     explicit primal-dual iteration and the bisection on the physical volume
@@ -361,7 +379,7 @@ def bench_net(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae", "mbb", "learned"])
+    ap.add_argument("--what", default="ku", choices=["ku", "batch", "net", "oc", "frame", "pae", "mbb", "learned", "mma"])
     ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--iters", type=int, default=54)
     ap.add_argument("--epochs", type=int, default=8)
@@ -382,7 +400,7 @@ def main():
     a = ap.parse_args()
     B.build()
     {"ku": bench_ku, "batch": bench_batch, "net": bench_net, "oc": bench_oc, "frame": bench_frame,
-     "pae": bench_pae, "mbb": bench_mbb, "learned": bench_learned}[a.what](a)
+     "pae": bench_pae, "mbb": bench_mbb, "learned": bench_learned, "mma": bench_mma}[a.what](a)
 
 
 if __name__ == "__main__":

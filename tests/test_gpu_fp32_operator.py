@@ -1,7 +1,8 @@
 """The FP32 stiffness operators of the mixed path against the FP64 oracle.
 
 impl 1: node-centric gather with the dense Ke (FP32 FMAs on CUDA cores);
-impl 2: tcgen05 tensor cores (TF32 with split operands, FP32 accumulation);
+impl 2: tcgen05 tensor cores (TF32 with split operands, FP32 accumulation in tensor
+memory, streaming element slabs);
 impl 3: element tiles with Ke factored in the Walsh basis of the corners (FP32
 on CUDA cores); impl 4: the same product for two elements per thread in paired
 FP32 instructions. All must reproduce K u to FP32-level accuracy (normwise 1e-5;
@@ -76,8 +77,9 @@ def test_fp32_operators_agree_at_full_size():
 
 def test_translation_invariance_exact():
     """Adding a rigid translation to u leaves the tensor-core K u bit-identical:
-    the element rows are shifted by one of their nodes before rounding, so with
-    u and u + t exactly representable in FP32 the shifted rows are the same."""
+    each block stages its displacements relative to one of its nodes before
+    rounding to TF32 parts, so with u and u + t exactly representable in FP32
+    the staged differences are the same."""
     from paper_2005_05436_gb300 import TO_MIXED
     shape = (13, 9, 6)
     F, fixed = I.cantilever_3d(*shape)

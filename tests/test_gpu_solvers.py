@@ -53,6 +53,28 @@ def test_solve_matches_direct(shape, precision, precond):
         assert info.refinements >= 1
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "gmg"])
+@pytest.mark.parametrize("shape", [(24, 12, 12), (16, 8, 8), (13, 7, 5), (31, 17, 46)])
+def test_mixed_solve_on_tensor_cores_matches_direct(shape, precond):
+    """The mixed solve with its FP32 fine operator on tensor cores (ku_impl 2:
+    K p with p.Ap, the last smoothing sweep with r.z and the residual, all as
+    TF32 MMAs) reaches the FP64 residual and the oracle's direct solution as the
+    CUDA-core operator does."""
+    rtol = 1e-8
+    g, F, fixed = make_grid(shape, **_kw("mixed", precond, penal=3.0, cg_rtol=rtol, cg_maxit=100000, ku_impl=2))
+    og = O.Grid(*shape)
+    Ke = O.element_stiffness(og.dim)
+    xp = design_field(shape, 12, lo=0.02)
+    Ud = O.solve_direct(og, Ke, O.simp_modulus(xp, 3.0), F, fixed)
+    U = torch.zeros(g.ndof, dtype=torch.float64, device="cuda")
+    info = g.solve(to_cuda(xp), U)
+    assert info.rel_res <= rtol, (info.rel_res, info.iters, info.refinements)
+    Ug = U.cpu().numpy()
+    assert rel(Ug, Ud) <= 1e-5
+    assert abs(F @ Ug - F @ Ud) <= 1e-6 * abs(F @ Ud)
+    assert info.refinements >= 1
+
+
 @pytest.mark.parametrize("precision,precond", COMBOS)
 def test_solve_full_size_cantilever(precision, precond):
     """96x48x48 cantilever at rtol 1e-8 (FP64 residual); all four solvers agree on c."""
