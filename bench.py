@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--loop-mode", type=int, default=0, choices=[0, 1],
                     help="0: PCG loop as one conditional-WHILE graph launch; 1: host-driven loop "
                          "of the same kernels (lets profilers see every launch)")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the 2D MBB (300x100 .. 1200x400) and 256-instance batched measurements")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the PCG iteration's kernels without programmatic dependent launch")
     return ap.parse_args()
@@ -236,6 +238,68 @@ def _timed_steps(d, steps, flush, stream):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     return infos, [a.elapsed_time(b) for a, b in ev]
+
+
+def mbb_config2(flush, stream, warmup=3, steps=5):
+    """The 2D half MBB beam of Sec. 3 on the Table 3 meshes 300x100, 600x200 and
+    1200x400 (volfrac 0.3, penal 1 -> 3 by 0.25 every 25 iterations, beta 2 -> 16
+    doubling every 25, rmin 0.03 nelx, ft 3, GMG-PCG to 1e-8): design iterations
+    warmup+1 .. warmup+steps of the plain FP64 path and of the mixed path,
+    timed like the headline (CUDA events, L2 flushed between steps)."""
+    import torch
+
+    from paper_2005_05436_gb300 import TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG, default_params, inputs as I
+    from paper_2005_05436_gb300.topopt import Design, Grid
+    out = {}
+    for nelx, nely in ((300, 100), (600, 200), (1200, 400)):
+        F, fixed = I.mbb_half_beam(nelx, nely)
+        res = {}
+        for name, prec in (("fp64_gmg", TO_FP64), ("mixed_gmg", TO_MIXED)):
+            p = default_params(2, nelx, nely, 0, volfrac=0.3, penal=1.0, rmin=0.03 * nelx, ft=3, eta=0.5, beta=2.0,
+                               move=0.2, cg_rtol=1e-8, cg_maxit=100000, precision=prec, precond=TO_PC_GMG, mg_nu=1,
+                               inner_rtol=3e-3, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+            g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
+            d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.3)).cuda())
+            for _ in range(warmup):
+                d.step()
+            infos, ms = _timed_steps(d, steps, flush, stream)
+            g.close()
+            res[name] = {"value": round(steps / (sum(ms) / 1000.0), 3), "max_rel_res": max(t["rel_res"] for t in infos),
+                         "c_last": infos[-1]["c"]}
+        res["mixed_speedup"] = round(res["mixed_gmg"]["value"] / res["fp64_gmg"]["value"], 2)
+        res["c_rel_diff"] = abs(res["mixed_gmg"]["c_last"] - res["fp64_gmg"]["c_last"]) / abs(res["fp64_gmg"]["c_last"])
+        out[f"{nelx}x{nely}"] = res
+    return {"workload": "2D half MBB beam, rmin 0.03 nelx, volfrac 0.3, continuation, GMG-PCG to 1e-8",
+            "unit": UNIT, "iterations": f"{warmup + 1}..{warmup + steps}", "grids": out}
+
+
+def batched_256(steps=4):
+    """256 uneven seeded 2D instances (nelx 60..480, aspect 2..4, volfrac 0.2..0.5,
+    rmin 0.02 nelx, 1-3 loads, clamped segments) advanced together, one CUDA-graph
+    launch per design iteration, mixed precision + GMG, tiles autotuned; the
+    first iteration is untimed (capture), the rest averaged."""
+    import numpy as np
+    import torch
+
+    from paper_2005_05436_gb300 import TO_MIXED, TO_PC_GMG, default_params, inputs as I
+    from paper_2005_05436_gb300.topopt import Batch
+    insts = I.batched_instances(256, seed=20050543)
+    p = default_params(2, 8, 4, precision=TO_MIXED, precond=TO_PC_GMG, mg_nu=1, penal=3.0, beta=2.0, cg_rtol=1e-8,
+                       cg_maxit=100000, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, 1))
+    F = torch.from_numpy(np.concatenate([q.F for q in insts])).cuda()
+    fixed = torch.from_numpy(np.concatenate([q.fixed for q in insts])).cuda()
+    x0 = torch.from_numpy(np.concatenate([I.initial_design(q.nelx * q.nely, q.volfrac) for q in insts])).cuda()
+    b = Batch(p, [(q.nelx, q.nely, q.volfrac, q.rmin) for q in insts], F, fixed, x0)
+    tune = b.autotune(reps=3)
+    infos = [b.step() for _ in range(steps)]
+    ms = [i["ms"] for i in infos[1:]]
+    t = sum(ms) / len(ms)
+    b.close()
+    return {"workload": "256 uneven 2D instances (config 4), mixed + GMG, one graph launch per iteration",
+            "elements": int(b.nel), "design_iterations_per_s": round(1000.0 / t, 3),
+            "elements_per_s": round(b.nel * 1000.0 / t, 1), "ms_per_iteration": round(t, 2),
+            "tiles": {"node": tune["node"], "elem": tune["elem"]},
+            "max_rel_res": max(i["max_rel_res"] for i in infos), "kernels_per_iteration": infos[-1]["kernels"]}
 
 
 def run_ours(args):
@@ -397,6 +461,9 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args.grid)
+    other = None
+    if not args.no_other_configs and world == 1:
+        other = {"mbb_2d": mbb_config2(flush, stream), "batched_2d": batched_256()}
 
     last = timed[-1]
     # the metric's own comparison: learned + mixed against the plain FP64 GPU path
@@ -424,7 +491,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": roof, "cpu_baseline": cpu, "compare": compare,
+        "roofline": roof, "cpu_baseline": cpu, "compare": compare, "other_configs": other,
         "clocks": clk.summary(),
         "per_step": {"ms": [round(m, 2) for m in step_ms], "n_cg": [t["n_cg"] for t in timed],
                      "n_refine": [t["n_refine"] for t in timed],
@@ -440,7 +507,10 @@ def run_ours(args):
         # repeated last so that a view of the line's tail still shows the headline
         "summary": {"value": round(value, 3), "vs_plain_fp64_speedup": vs_plain["speedup"] if vs_plain else None,
                     "max_rel_diff_c": vs_plain["max_rel_diff_c"] if vs_plain else None,
-                    "roofline_frac": roof.get("frac"), "cpu_baseline": cpu["value"] if cpu else None},
+                    "roofline_frac": roof.get("frac"), "cpu_baseline": cpu["value"] if cpu else None,
+                    "mbb_2d_mixed": {k: v["mixed_gmg"]["value"] for k, v in other["mbb_2d"]["grids"].items()}
+                    if other else None,
+                    "batched_256_it_s": other["batched_2d"]["design_iterations_per_s"] if other else None},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
