@@ -81,6 +81,9 @@ def parse_args():
                          "of the same kernels (lets profilers see every launch)")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the 2D MBB (300x100 .. 1200x400) and 256-instance batched measurements")
+    ap.add_argument("--warm-rule", default="residual", choices=["energy", "residual"],
+                    help="how the learned warm start combines U_prev and the network output: energy "
+                         "minimiser or residual-norm minimiser over their span")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the PCG iteration's kernels without programmatic dependent launch")
     return ap.parse_args()
@@ -222,7 +225,9 @@ def _train_warm_start(args):
                         f"16x8x8 / 24x12x12 / 32x16x16 cantilever-family problems, energy objective, "
                         f"{args.learn_epochs} epochs",
             "energy_loss_first_last": [round(hist[0], 4), round(hist[-1], 4)],
-            "train_seconds": round(time.perf_counter() - t0, 1)}
+            "train_seconds": round(time.perf_counter() - t0, 1),
+            "combination": ("minimiser of ||F - K U0||_2" if args.warm_rule == "residual" else
+                            "minimiser of the potential energy") + " over span{U_prev, U_net}"}
     return net, info
 
 
@@ -334,7 +339,7 @@ def run_ours(args):
         net, learned_info = _train_warm_start(args)
     g, d = _make_design(args, w, precision, precond, ku_impl, stream)
     if net is not None:
-        Lr.attach(g, net)
+        Lr.attach(g, net, rule=0 if args.warm_rule == "energy" else 1)
     for _ in range(args.warmup):
         d.step()
     torch.cuda.synchronize()
@@ -500,7 +505,10 @@ def run_ours(args):
                                  for k in ("t_setup_ms", "t_krylov_ms", "t_resid_ms", "t_warm_ms",
                                            "t_filter_ms", "t_sens_ms", "t_oc_ms")},
                      "warm_err_mean": round(statistics.mean(t["warm_err"] for t in timed), 5),
-                     "warm_err_prev_mean": round(statistics.mean(t["warm_err_prev"] for t in timed), 5)},
+                     "warm_err_prev_mean": round(statistics.mean(t["warm_err_prev"] for t in timed), 5),
+                     "warm_res_mean": round(statistics.mean(t["warm_res"] for t in timed), 6),
+                     "warm_res_prev_mean": round(statistics.mean(t["warm_res_prev"] for t in timed), 6),
+                     "warm_b": [round(t["warm_b"], 4) for t in timed]},
         "final": {"c": last["c"], "V": last["V"], "eta": last["eta"]},
         "paper_context": "top3D125 + MGCG, 96x48x48 rmin 2sqrt(3): 14.20 s/it (0.0704 it/s), "
                          "serial Matlab FP64 on an i7-5500U (Table 4); different rmin, context only",

@@ -203,9 +203,14 @@ typedef struct to_iter_info {
     double t_warm_ms;       /* learned warm start (inside t_solve_ms), 0 without a network */
     double warm_a, warm_b;  /* its starting point: warm_a U_prev + warm_b U_net */
     double warm_err_prev;   /* energy-norm error of U_prev relative to that of U = 0: ||U_prev - U||_K^2 / ||U||_K^2 */
-    double warm_err;        /* the same for the warm start actually used (<= warm_err_prev) */
+    double warm_err;        /* the same for the warm start actually used (<= warm_err_prev under
+                               TO_WARM_ENERGY) */
     int32_t pae;            /* Anderson extrapolation of this step: 0 off, 1 damped step, 2 extrapolated */
     int32_t _pad2;
+    double warm_res_prev;   /* ||F - K U_prev|| / ||F|| over the free DOFs (operator products in the
+                               warm start's precision), 0 without a network */
+    double warm_res;        /* the same for the warm start actually used (<= warm_res_prev under
+                               TO_WARM_RESIDUAL) */
 } to_iter_info;
 
 /* Thread-local message of the last failing call ("" if none). */
@@ -530,6 +535,15 @@ void to_net_destroy(to_net* net);
  * (coarse node I on fine node stride*I; loads restricted by full weighting,
  * the output prolongated trilinearly); fixed at the first use of the grid. */
 to_status to_set_warm_start(to_grid* g, to_net* net, int32_t stride);
+
+/* How the warm start combines U (the previous solution) and U_net:
+ * TO_WARM_ENERGY (default): the minimiser of the potential energy over
+ * span{U, U_net}, as above. TO_WARM_RESIDUAL: the minimiser of the residual
+ * norm ||F - K (a U + b U_net)||_2 over the free DOFs, the norm of the solve's
+ * stopping test, so the start's residual never exceeds that of U (five more
+ * dot products). TO_EINVAL for other values. */
+enum { TO_WARM_ENERGY = 0, TO_WARM_RESIDUAL = 1 };
+to_status to_set_warm_start_rule(to_grid* g, int32_t rule);
 /* Network input of the grid at xPhys: x[D][H][W][4] on the (coarsened) node
  * grid padded to multiples of 4 (D, H, W along x, z, y): the mean density of
  * the elements around each node (-1 at nodes with a Dirichlet DOF) and the

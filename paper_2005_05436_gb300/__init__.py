@@ -6,7 +6,7 @@ bindings of it. Importing this package does not load the library; the first
 ``Grid`` does, and raises if it has not been built.
 """
 from ._lib import (TO_OC_BISECTION, TO_OC_PRIMAL_DUAL, TO_OC_PHYSICAL_VOLUME, TO_CNT_ADD, TO_CNT_MUL, TO_FP64, TO_MIXED, TO_PC_GMG, TO_PC_JACOBI,  # noqa: F401
-                   TO_REFINE_RELIABLE, TO_REFINE_FLEXIBLE, TO_OK, TO_EINVAL, TO_ENOMEM, TO_ECUDA, TO_ENOTCONV, TO_ENAN, TO_ETIMEOUT,
+                   TO_REFINE_RELIABLE, TO_REFINE_FLEXIBLE, TO_WARM_ENERGY, TO_WARM_RESIDUAL, TO_OK, TO_EINVAL, TO_ENOMEM, TO_ECUDA, TO_ENOTCONV, TO_ENAN, TO_ETIMEOUT,
                    TopoptError, default_params, load)
 
 

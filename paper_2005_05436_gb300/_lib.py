@@ -20,6 +20,7 @@ TO_PC_JACOBI, TO_PC_GMG = 0, 1
 TO_CNT_ADD, TO_CNT_MUL = 0, 1
 TO_OC_BISECTION, TO_OC_PRIMAL_DUAL, TO_OC_PHYSICAL_VOLUME = 0, 1, 2
 TO_REFINE_RELIABLE, TO_REFINE_FLEXIBLE = 0, 1
+TO_WARM_ENERGY, TO_WARM_RESIDUAL = 0, 1
 
 
 class Continuation(C.Structure):
@@ -65,7 +66,8 @@ class IterInfo(C.Structure):
                 ("rel_res", C.c_double), ("t_filter_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_warm_ms", C.c_double), ("warm_a", C.c_double), ("warm_b", C.c_double),
-                ("warm_err_prev", C.c_double), ("warm_err", C.c_double), ("pae", C.c_int32), ("_pad2", C.c_int32)]
+                ("warm_err_prev", C.c_double), ("warm_err", C.c_double), ("pae", C.c_int32), ("_pad2", C.c_int32),
+                ("warm_res_prev", C.c_double), ("warm_res", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -144,6 +146,7 @@ _SIGS = {
     "to_net_adam": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
     "to_net_destroy": (None, [P]),
     "to_set_warm_start": (C.c_int, [P, P, C.c_int32]),
+    "to_set_warm_start_rule": (C.c_int, [P, C.c_int32]),
     "to_learned_features": (C.c_int, [P, P, P, P]),
     "to_learned_target": (C.c_int, [P, P, P, P]),
     "to_learned_energy_grad": (C.c_int, [P, P, P, C.c_double, P, C.POINTER(C.c_double)]),

@@ -629,10 +629,13 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     double wen[2] = {0.0, 0.0};
     if (g->net) {
         double coef[2] = {1.0, 0.0}, wms = 0.0;
-        learned_warm_start(g, s->xPhys, s->U, coef, &wms, wen);
+        double wres[2] = {0.0, 0.0};
+        learned_warm_start(g, s->xPhys, s->U, coef, &wms, wen, wres);
         it.warm_a = coef[0];
         it.warm_b = coef[1];
         it.t_warm_ms = wms;
+        it.warm_res_prev = wres[0];
+        it.warm_res = wres[1];
     }
     to_solve_info si{};
     const to_status sst = solve_state(g, g->F, s->U, &si);

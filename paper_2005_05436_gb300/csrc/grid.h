@@ -91,6 +91,7 @@ struct to_grid {
     to_net* net = nullptr;     // learned warm start (to_set_warm_start), not owned
     void* warm = nullptr;      // its workspace (warm.cu)
     int warm_stride = 1;       // the network's node-grid coarsening (1 or 2)
+    int warm_rule = TO_WARM_ENERGY;  // how the warm start combines U_prev and U_net
     void* pae = nullptr;       // Anderson extrapolation history (pae.cu)
 };
 
@@ -124,7 +125,8 @@ void warm_free(to_grid* g);
 void pae_before_oc(to_grid* g, const double* x, cudaStream_t st);
 int pae_after_oc(to_grid* g, double* x, int it, cudaStream_t st);
 void pae_free(to_grid* g);
-void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy);
+void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy,
+                        double* resid);
 void grid_sync_out(to_grid* g);
 void solver_init(to_grid* g);
 void solver_free(to_grid* g);

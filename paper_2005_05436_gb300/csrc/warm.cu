@@ -211,9 +211,9 @@ WarmWS* warm_ws(to_grid* g) {
     w->x = walloc<float>(g, V * 4);
     w->y = walloc<float>(g, V * 3);
     for (double** a : {&w->Uh, &w->KUh, &w->Up, &w->KUp}) *a = walloc<double>(g, g->d.ndof);
-    w->dots = walloc<double>(g, 8);
+    w->dots = walloc<double>(g, 16);
     w->fmax = walloc<unsigned>(g, 1);
-    TOPO_CUDA(cudaMallocHost(&w->hdots, 8 * sizeof(double)));
+    TOPO_CUDA(cudaMallocHost(&w->hdots, 16 * sizeof(double)));
     TOPO_CUDA(cudaEventCreate(&w->e0));
     TOPO_CUDA(cudaEventCreate(&w->e1));
     TOPO_CUDA(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
@@ -284,7 +284,8 @@ struct AuxJoin {
 };
 
 // U <- argmin of the energy over span{U, U_h}; E(xPhys) in g->E (FP64).
-void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy) {
+void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef, double* ms, double* energy,
+                        double* resid) {
     WarmWS* w = warm_ws(g);
     const Dims& d = g->d;
     cudaStream_t st = g->st, ax = w->aux;
@@ -300,6 +301,9 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     kw_crop<<<div_up(d.nnodes, 256), 256, 0, ax>>>(d, w->cg, w->y, g->fixed, w->Uh);
     TOPO_CHECK_LAUNCH();
     launch_mask_copy(d.ndof, U, w->Up, g->fixed, ax);
+    // ||F||^2 over the free DOFs (KUh serves as scratch before its product)
+    launch_mask_copy(d.ndof, g->F, w->KUh, g->fixed, ax);
+    launch_dot(d.ndof, w->KUh, nullptr, w->dots + 13, w->partials, w->counter, ax);
     if (g->p.precision == TO_MIXED) {
         // the products only choose a starting point: the FP32 operator is enough
         launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, w->E32, ax);
@@ -316,14 +320,38 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, w->partials, w->counter, ax);
     launch_dot(d.ndof, w->Up, w->KUh, w->dots + 3, w->partials, w->counter, ax);
     launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 4, w->partials, w->counter, ax);
-    TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 5 * sizeof(double), cudaMemcpyDeviceToHost, ax));
+    const bool by_residual = g->warm_rule == TO_WARM_RESIDUAL;
+    // the Gram matrix of the two residual directions and their products with F
+    // (K U is 0 at fixed DOFs, so these sums run over the free DOFs)
+    launch_dot(d.ndof, w->KUp, w->KUp, w->dots + 8, w->partials, w->counter, ax);
+    launch_dot(d.ndof, w->KUp, w->KUh, w->dots + 9, w->partials, w->counter, ax);
+    launch_dot(d.ndof, w->KUh, w->KUh, w->dots + 10, w->partials, w->counter, ax);
+    launch_dot(d.ndof, g->F, w->KUp, w->dots + 11, w->partials, w->counter, ax);
+    launch_dot(d.ndof, g->F, w->KUh, w->dots + 12, w->partials, w->counter, ax);
+    TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 14 * sizeof(double), cudaMemcpyDeviceToHost, ax));
     TOPO_CUDA(cudaEventRecord(w->ready, ax));
     solver_setup(g);
     TOPO_CUDA(cudaEventSynchronize(w->ready));
     const double fp = w->hdots[0], fh = w->hdots[1], pp = w->hdots[2], ph = w->hdots[3], hh = w->hdots[4];
     double a = 1.0, b = 0.0;  // keep U when the network direction adds nothing
     const bool hok = hh > 0.0 && std::isfinite(hh) && std::isfinite(fh);
-    if (hok && !(pp > 0.0)) {  // no previous solution: the energy-optimal multiple of U_h
+    if (by_residual) {
+        // minimiser of ||F - K (a U_prev + b U_h)||_2 over the free DOFs: the
+        // stopping test's norm, so the start is never worse than U_prev in it
+        const double rpp = w->hdots[8], rph = w->hdots[9], rhh = w->hdots[10], rfp = w->hdots[11],
+                     rfh = w->hdots[12];
+        const bool rok = rhh > 0.0 && std::isfinite(rhh) && std::isfinite(rfh) && std::isfinite(rph);
+        if (rok && !(rpp > 0.0)) {
+            a = 0.0;
+            b = rfh / rhh;
+        } else if (rok && std::isfinite(rpp) && std::isfinite(rfp)) {
+            const double det = rpp * rhh - rph * rph;
+            if (det > 1e-12 * rpp * rhh) {
+                a = (rfp * rhh - rfh * rph) / det;
+                b = (rpp * rfh - rph * rfp) / det;
+            }
+        }
+    } else if (hok && !(pp > 0.0)) {  // no previous solution: the energy-optimal multiple of U_h
         a = 0.0;
         b = fh / hh;
     } else if (hok && std::isfinite(pp) && std::isfinite(ph) && std::isfinite(fp)) {
@@ -353,6 +381,15 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
         energy[0] = 0.5 * pp - fp;
         energy[1] = 0.5 * (a * a * pp + 2.0 * a * b * ph + b * b * hh) - (a * fp + b * fh);
     }
+    if (resid) {  // ||F - K U|| / ||F|| of U_prev and of the new start
+        const double ff = w->hdots[13], rpp = w->hdots[8], rph = w->hdots[9], rhh = w->hdots[10],
+                     rfp = w->hdots[11], rfh = w->hdots[12];
+        auto r2 = [&](double ca, double cb) {
+            return std::fmax(0.0, ff - 2.0 * (ca * rfp + cb * rfh) + ca * ca * rpp + 2.0 * ca * cb * rph + cb * cb * rhh);
+        };
+        resid[0] = ff > 0.0 ? std::sqrt(r2(1.0, 0.0) / ff) : 0.0;
+        resid[1] = ff > 0.0 ? std::sqrt(r2(a, b) / ff) : 0.0;
+    }
 }
 
 }  // namespace topo
@@ -369,6 +406,13 @@ to_status to_set_warm_start(to_grid* g, to_net* net, int32_t stride) {
         return api_fail(TO_EINVAL, "the warm-start coarsening cannot change after first use");
     g->net = net;
     g->warm_stride = stride;
+    return TO_OK;
+}
+
+to_status to_set_warm_start_rule(to_grid* g, int32_t rule) {
+    if (!g) return api_fail(TO_EINVAL, "NULL handle");
+    if (rule != TO_WARM_ENERGY && rule != TO_WARM_RESIDUAL) return api_fail(TO_EINVAL, "rule must be TO_WARM_ENERGY or TO_WARM_RESIDUAL");
+    g->warm_rule = rule;
     return TO_OK;
 }
 

@@ -125,10 +125,14 @@ def target(grid, U):
     return t, m
 
 
-def attach(grid, net, stride=2):
+def attach(grid, net, stride=2, rule=None):
     """Use net as the warm start of every to_step of grid (None detaches); the
-    network works on the node grid coarsened by stride."""
+    network works on the node grid coarsened by stride; rule: TO_WARM_ENERGY or
+    TO_WARM_RESIDUAL (how U_prev and the network's output are combined; None
+    keeps the grid's rule)."""
     L.check(grid.lib.to_set_warm_start(grid.h, net.h if net is not None else None, int(stride)))
+    if rule is not None:
+        L.check(grid.lib.to_set_warm_start_rule(grid.h, int(rule)))
 
 
 def generate(shapes, runs, iters, seed=0, every=1, warmup=2, stride=2, **params):

@@ -76,7 +76,7 @@ def _restore(d, s):
     d.st.eta, d.st.penal, d.st.beta, d.st.loop = s[1]
 
 
-def _steps(g, d, modes, nets):
+def _steps(g, d, modes, nets, rule=None):
     from paper_2005_05436_gb300 import learned as Lr
     trained, raw, _ = nets
     s = _snap(d)
@@ -85,7 +85,7 @@ def _steps(g, d, modes, nets):
         _restore(d, s)
         if mode.startswith("cold"):
             d.U.zero_()
-        Lr.attach(g, trained if mode.endswith("+net") else raw if mode.endswith("+raw") else None)
+        Lr.attach(g, trained if mode.endswith("+net") else raw if mode.endswith("+raw") else None, rule=rule)
         info = d.step()
         out[mode] = (info, d.xPhys.clone(), d.x.clone())
     Lr.attach(g, None)
@@ -112,6 +112,30 @@ def test_warm_start_keeps_the_answer_and_never_raises_the_start_energy(nets, pre
         assert info["warm_err"] <= info["warm_err_prev"] + 1e-9
         assert info["t_warm_ms"] > 0
     assert out["cold+net"][0]["warm_err_prev"] == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_residual_rule_keeps_the_answer_and_never_raises_the_start_residual(nets, precision):
+    """TO_WARM_RESIDUAL: the start minimises ||F - K U0|| over span{U_prev, U_net},
+    so its residual (reported as warm_res) is at most that of U_prev; the
+    solution is the one without the network, and both rules report both
+    measures of both starts."""
+    from paper_2005_05436_gb300 import TO_FP64, TO_MIXED, TO_WARM_ENERGY, TO_WARM_RESIDUAL
+    g, d = _problem(1, TO_FP64 if precision == "fp64" else TO_MIXED)
+    out = _steps(g, d, ["warm", "warm+net", "cold+net"], nets, rule=TO_WARM_RESIDUAL)
+    ref = out["warm"][0]
+    for mode in ("warm+net", "cold+net"):
+        info, xp, _ = out[mode]
+        assert info["rel_res"] <= 1e-8
+        assert abs(info["c"] - ref["c"]) <= 1e-7 * abs(ref["c"])
+        assert float(torch.linalg.norm(xp - out["warm"][1]) / torch.linalg.norm(out["warm"][1])) <= 1e-7
+        assert 0.0 < info["warm_res"] <= info["warm_res_prev"] * (1 + 1e-9) + 1e-12
+    assert out["cold+net"][0]["warm_res_prev"] == pytest.approx(1.0, abs=1e-9)  # U = 0: ||F|| / ||F||
+    en = _steps(g, d, ["warm+net"], nets, rule=TO_WARM_ENERGY)["warm+net"][0]
+    assert en["warm_err"] <= en["warm_err_prev"] + 1e-9 and en["warm_res"] > 0.0
+    # the energy rule's start is the energy minimiser: the residual rule's start is not better in energy
+    assert en["warm_err"] <= out["warm+net"][0]["warm_err"] + 1e-9
+    g.close()
 
 
 def test_what_the_trained_warm_start_gains(nets):
