@@ -154,6 +154,9 @@ typedef struct to_params {
                                programmatic dependent launch, so that each grid is scheduled while
                                its predecessor runs and waits for it before reading memory (same
                                arithmetic and order); 1: plain stream-ordered launches */
+    int32_t mg_nu_fine;     /* GMG: pre- and post-smoothing sweeps on the finest level; 0 (default):
+                               mg_nu, like the coarser levels; 1..16 otherwise, else TO_EINVAL */
+    int32_t _pad5;
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

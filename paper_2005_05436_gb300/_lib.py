@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("loop_mode", C.c_int32), ("mg_coarse_every", C.c_int32), ("oc_method", C.c_int32),
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
                 ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32),
-                ("mg_unfused", C.c_int32), ("pdl_off", C.c_int32)]
+                ("mg_unfused", C.c_int32), ("pdl_off", C.c_int32),
+                ("mg_nu_fine", C.c_int32), ("_pad5", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

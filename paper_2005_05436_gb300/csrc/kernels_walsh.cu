@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TY * TZ, (WalshMinBlocks<T, TY * TZ>::v))
     __shared__ __align__(16) T sp[3][PN];     // node planes in flight (three-deep pipeline)
     __shared__ T sr[2][3][TZ][TY];
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested after the first planes are staged, so its load overlaps theirs
 
     const int tid = threadIdx.x, ty = tid % TY, tz = tid / TY;
     int bid = blockIdx.x;
@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(TY * TZ, (WalshMinBlocks<T, TY * TZ>::v))
     T Ea = loadE(X0 - 1), Eb;
     cp_async_wait_one();
     __syncthreads();
+    if (sk) {  // the same value in every thread; nothing written yet
+        cp_async_wait_all();
+        return;
+    }
     T A[3][4], B[3][4], C0[3][4], C1[3][4];
     read_corners(0, A);
 #pragma unroll

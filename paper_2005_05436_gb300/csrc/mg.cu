@@ -24,21 +24,34 @@ __global__ void __launch_bounds__(256) k_fine_op3(Dims d, const KeP<T, 24> ke, c
                                                   const int* skip, PcgScalars* pcg, double* partials,
                                                   unsigned* counter) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = n < d.nnodes;
     DotAcc<T> dot;
-    if (n < d.nnodes) {
-        T a[3];
-        ku3_node_clamped<T>(ke, E, u, (int)n, d, a[0], a[1], a[2]);  // register-cached, branch-free
+    // the epilogue's operands depend on nothing computed here: fetched first
+    T r_i[3], d_i[3], u_i[3];
+    unsigned f_i[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long i = 3 * n + c;
+        r_i[c] = (MODE != 0 && in) ? r[i] : T(0);
+        d_i[c] = (MODE == 1 && in) ? dinv[i] : T(0);
+        u_i[c] = ((MODE == 1 || PCG) && in) ? u[i] : T(0);
+        f_i[c] = in ? (unsigned)fixed[i] : 0u;
+    }
+    T a[3] = {};
+    if (in) ku3_node_clamped<T>(ke, E, u, (int)n, d, a[0], a[1], a[2]);  // register-cached, branch-free
+    if (sk) return;
+    if (in) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long i = 3 * n + c;
             T o = a[c];
-            if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a[c]);
-            if (MODE == 2) o = r[i] - a[c];
-            if (fixed[i]) o = T(0);
+            if (MODE == 1) o = u_i[c] + omega * d_i[c] * (r_i[c] - a[c]);
+            if (MODE == 2) o = r_i[c] - a[c];
+            if (f_i[c]) o = T(0);
             out[i] = o;
-            if (PCG) dot.add(MODE == 1 ? r[i] : u[i], o);
+            if (PCG) dot.add(MODE == 1 ? r_i[c] : u_i[c], o);
         }
     }
     if (PCG) {
@@ -63,21 +76,34 @@ __global__ void __launch_bounds__(256) k_fine_op2(Dims d, const KeP<T, 8> ke, co
                                                   const int* skip, PcgScalars* pcg, double* partials,
                                                   unsigned* counter) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = n < d.nnodes;
     DotAcc<T> dot;
-    if (n < d.nnodes) {
-        T a[2];
-        ku2_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1]);
+    // the epilogue's operands depend on nothing computed here: fetched first
+    T r_i[2], d_i[2], u_i[2];
+    unsigned f_i[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const long long i = 2 * n + c;
+        r_i[c] = (MODE != 0 && in) ? r[i] : T(0);
+        d_i[c] = (MODE == 1 && in) ? dinv[i] : T(0);
+        u_i[c] = ((MODE == 1 || PCG) && in) ? u[i] : T(0);
+        f_i[c] = in ? (unsigned)fixed[i] : 0u;
+    }
+    T a[2] = {};
+    if (in) ku2_node<T, rel_form<T>()>(ke, E, u, n, d, a[0], a[1]);
+    if (sk) return;
+    if (in) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const long long i = 2 * n + c;
             T o = a[c];
-            if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a[c]);
-            if (MODE == 2) o = r[i] - a[c];
-            if (fixed[i]) o = T(0);
+            if (MODE == 1) o = u_i[c] + omega * d_i[c] * (r_i[c] - a[c]);
+            if (MODE == 2) o = r_i[c] - a[c];
+            if (f_i[c]) o = T(0);
             out[i] = o;
-            if (PCG) dot.add(MODE == 1 ? r[i] : u[i], o);
+            if (PCG) dot.add(MODE == 1 ? r_i[c] : u_i[c], o);
         }
     }
     if (PCG) {
@@ -450,13 +476,21 @@ __global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict_
     constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
     constexpr bool REL = rel_form<T>();
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.nnodes) return;
     const int iy = (int)(n % d.nny);
     const long long t = n / d.nny;
     const int iz = (int)(t % d.nnz);
     const int ix = (int)(t / d.nnz);
+    T r_i[DIM], d_i[DIM];
+    unsigned f_i[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        r_i[c] = MODE != 0 ? r[DIM * n + c] : T(0);
+        d_i[c] = MODE == 1 ? dinv[DIM * n + c] : T(0);
+        f_i[c] = fixed[DIM * n + c];
+    }
     T uc[DIM], acc[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) uc[c] = u[DIM * n + c];
@@ -485,13 +519,14 @@ __global__ void __launch_bounds__(256) k_stencil_op(Dims d, const T* __restrict_
 #pragma unroll
             for (int k = 0; k < DIM; ++k) acc[c] += S[((long long)s * Q + c * DIM + k) * d.nnodes + n] * um[k];
     }
+    if (sk) return;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
         const long long i = DIM * n + c;
         T o = acc[c];
-        if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - acc[c]);
-        if (MODE == 2) o = r[i] - acc[c];
-        if (fixed[i]) o = T(0);
+        if (MODE == 1) o = uc[c] + omega * d_i[c] * (r_i[c] - acc[c]);
+        if (MODE == 2) o = r_i[c] - acc[c];
+        if (f_i[c]) o = T(0);
         out[i] = o;
     }
 }
@@ -507,13 +542,19 @@ template <typename T, int MODE>
 __device__ __forceinline__ void stencil_op3s_body(int vb, const Dims& d, const T* __restrict__ S,
                                                   const T* __restrict__ R, const T* __restrict__ u,
                                                   const T* __restrict__ r, const T* __restrict__ dinv,
-                                                  T* __restrict__ out, const uint8_t* __restrict__ fixed, T omega) {
+                                                  T* __restrict__ out, const uint8_t* __restrict__ fixed, T omega,
+                                                  int skip_now = 0) {
     constexpr int Q = 9;
     constexpr bool REL = rel_form<T>();
     __shared__ T part[9][32];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = ty / 3, pl = ty % 3;
     const long long n = (long long)vb * 32 + tx;
+    // the epilogue's operands depend on nothing computed here: fetched first
+    const bool outp = pl == 0 && n < d.nnodes;
+    const long long i = 3 * n + c;
+    const T r_i = (MODE != 0 && outp) ? r[i] : T(0), d_i = (MODE == 1 && outp) ? dinv[i] : T(0);
+    const unsigned f_i = outp ? (unsigned)fixed[i] : 0u;
     T acc = T(0);
     if (n < d.nnodes) {
         const int iy = (int)(n % d.nny);
@@ -547,13 +588,12 @@ __device__ __forceinline__ void stencil_op3s_body(int vb, const Dims& d, const T
     }
     part[ty][tx] = acc;
     __syncthreads();
-    if (pl != 0 || n >= d.nnodes) return;
+    if (skip_now || !outp) return;
     const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
-    const long long i = 3 * n + c;
     T o = a;
-    if (MODE == 1) o = u[i] + omega * dinv[i] * (r[i] - a);
-    if (MODE == 2) o = r[i] - a;
-    if (fixed[i]) o = T(0);
+    if (MODE == 1) o = u[i] + omega * d_i * (r_i - a);
+    if (MODE == 2) o = r_i - a;
+    if (f_i) o = T(0);
     out[i] = o;
 }
 
@@ -564,8 +604,8 @@ __global__ void __launch_bounds__(288) k_stencil_op3s(Dims d, const T* __restric
                                                       const uint8_t* __restrict__ fixed, T omega,
                                                       const int* skip) {
     pdl_begin();
-    if (skip && *skip) return;
-    stencil_op3s_body<T, MODE>(blockIdx.x, d, S, R, u, r, dinv, out, fixed, omega);
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
+    stencil_op3s_body<T, MODE>(blockIdx.x, d, S, R, u, r, dinv, out, fixed, omega, sk);
 }
 
 // ------------------------------------------------------- transfer operators
@@ -577,9 +617,16 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
                            const uint8_t* __restrict__ fixed_c, const int* skip, const T* __restrict__ dinv_c,
                            T* __restrict__ z_c, T omega) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
     const long long N = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (N >= dc.nnodes) return;
+    unsigned f_N[DIM];
+    T d_N[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        f_N[c] = fixed_c[DIM * N + c];
+        d_N[c] = dinv_c ? dinv_c[DIM * N + c] : T(0);
+    }
     const int NY = (int)(N % dc.nny);
     const long long t = N / dc.nny;
     const int NZ = (int)(t % dc.nnz);
@@ -597,11 +644,12 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
 #pragma unroll
                 for (int c = 0; c < DIM; ++c) acc[c] += w * rf[DIM * f + c];
             }
+    if (sk) return;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-        const T v = fixed_c[DIM * N + c] ? T(0) : acc[c];
+        const T v = f_N[c] ? T(0) : acc[c];
         rc[DIM * N + c] = v;
-        if (dinv_c) z_c[DIM * N + c] = omega * dinv_c[DIM * N + c] * v;
+        if (dinv_c) z_c[DIM * N + c] = omega * d_N[c] * v;
     }
 }
 
@@ -612,11 +660,15 @@ __global__ void k_restrict(Dims dc, Dims df, const T* __restrict__ rf, T* __rest
 template <typename T>
 __device__ __forceinline__ void restrict3s_body(int vb, const Dims& dc, const Dims& df, const T* __restrict__ rf,
                                                 T* __restrict__ rc, const uint8_t* __restrict__ fixed_c,
-                                                const T* __restrict__ dinv_c, T* __restrict__ z_c, T omega) {
+                                                const T* __restrict__ dinv_c, T* __restrict__ z_c, T omega,
+                                                int skip_now = 0) {
     __shared__ T part[9][32];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = ty / 3, ox = ty % 3 - 1;
     const long long N = (long long)vb * 32 + tx;
+    const bool outp = ty % 3 == 0 && N < dc.nnodes;
+    const unsigned f_N = outp ? (unsigned)fixed_c[3 * N + c] : 0u;
+    const T d_N = (outp && dinv_c) ? dinv_c[3 * N + c] : T(0);
     T acc = T(0);
     if (N < dc.nnodes) {
         const int NY = (int)(N % dc.nny);
@@ -640,11 +692,11 @@ __device__ __forceinline__ void restrict3s_body(int vb, const Dims& dc, const Di
     }
     part[ty][tx] = acc;
     __syncthreads();
-    if (ty % 3 != 0 || N >= dc.nnodes) return;
+    if (skip_now || !outp) return;
     const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
-    const T v = fixed_c[3 * N + c] ? T(0) : a;
+    const T v = f_N ? T(0) : a;
     rc[3 * N + c] = v;
-    if (dinv_c) z_c[3 * N + c] = omega * dinv_c[3 * N + c] * v;
+    if (dinv_c) z_c[3 * N + c] = omega * d_N * v;
 }
 
 template <typename T>
@@ -653,17 +705,24 @@ __global__ void __launch_bounds__(288) k_restrict3s(Dims dc, Dims df, const T* _
                                                     const int* skip, const T* __restrict__ dinv_c,
                                                     T* __restrict__ z_c, T omega) {
     pdl_begin();
-    if (skip && *skip) return;
-    restrict3s_body<T>(blockIdx.x, dc, df, rf, rc, fixed_c, dinv_c, z_c, omega);
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
+    restrict3s_body<T>(blockIdx.x, dc, df, rf, rc, fixed_c, dinv_c, z_c, omega, sk);
 }
 
 template <typename T, int DIM>
 __global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __restrict__ zf,
                               const uint8_t* __restrict__ fixed_f, const int* skip) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
     const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= df.nnodes) return;
+    unsigned fl[DIM];
+    T zv[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        fl[c] = fixed_f[DIM * f + c];
+        zv[c] = zf[DIM * f + c];
+    }
     const int fy = (int)(f % df.nny);
     const long long t = f / df.nny;
     const int fz = (int)(t % df.nnz);
@@ -681,9 +740,10 @@ __global__ void k_prolong_add(Dims df, Dims dc, const T* __restrict__ zc, T* __r
 #pragma unroll
                 for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * N + c];
             }
+    if (sk) return;
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
-        if (!fixed_f[DIM * f + c]) zf[DIM * f + c] += acc[c];
+        if (!fl[c]) zf[DIM * f + c] = zv[c] + acc[c];
 }
 
 // Prolongation fused into the first post-smoothing sweep of a 3D coarse level:
@@ -698,7 +758,8 @@ __device__ __forceinline__ void prolong_smooth3s_body(int vb, const Dims& d, con
                                                       const T* __restrict__ cur, const T* __restrict__ S,
                                                       const T* __restrict__ R, const T* __restrict__ r,
                                                       const T* __restrict__ dinv, T* __restrict__ out,
-                                                      const uint8_t* __restrict__ fixed, T omega) {
+                                                      const uint8_t* __restrict__ fixed, T omega,
+                                                      int skip_now = 0) {
     constexpr int TZ = 32 / TY, HY = TY + 2, HZ = TZ + 2, NH = 3 * HZ * HY, Q = 9;
     constexpr bool REL = rel_form<T>();
     __shared__ T us[3 * NH];
@@ -715,7 +776,11 @@ __device__ __forceinline__ void prolong_smooth3s_body(int vb, const Dims& d, con
     const long long n = iy + (long long)d.nny * (iz + (long long)d.nnz * ix);
     const int mx = ix + pl - 1;
     const bool plane = valid && mx >= 0 && mx < d.nnx;
-    // this thread's stencil blocks do not depend on u: their loads go out first
+    // the epilogue's operands and this thread's stencil blocks do not depend on u: their loads go out first
+    const bool outp = pl == 0 && valid;
+    const long long i = 3 * n + c;
+    const T r_i = outp ? r[i] : T(0), d_i = outp ? dinv[i] : T(0);
+    const unsigned f_i = outp ? (unsigned)fixed[i] : 0u;
     T sv[27], rv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) rv[k] = (REL && pl == 1 && valid) ? R[(long long)(c * 3 + k) * d.nnodes + n] : T(0);
@@ -734,21 +799,21 @@ __device__ __forceinline__ void prolong_smooth3s_body(int vb, const Dims& d, con
         T val = T(0);
         if (fx >= 0 && fx < d.nnx && fy >= 0 && fy < d.nny && fz >= 0 && fz < d.nnz) {
             const long long f = fy + (long long)d.nny * (fz + (long long)d.nnz * fx);
-            val = cur[3 * f + k];
-            if (!fixed[3 * f + k]) {
-                T acc = T(0);
-                const int nx = (fx & 1) ? 2 : 1, ny = (fy & 1) ? 2 : 1, nz = (fz & 1) ? 2 : 1;
-                for (int a = 0; a < nx; ++a)
-                    for (int b = 0; b < nz; ++b)
-                        for (int e = 0; e < ny; ++e) {
-                            const int NX = (fx >> 1) + a, NZ = (fz >> 1) + b, NY = (fy >> 1) + e;
-                            const T w = (nx == 2 ? T(0.5) : T(1)) * (ny == 2 ? T(0.5) : T(1)) *
-                                        (nz == 2 ? T(0.5) : T(1));
-                            const long long N = NY + (long long)dc.nny * (NZ + (long long)dc.nnz * NX);
-                            acc += w * zc[3 * N + k];
-                        }
-                val += acc;
-            }
+            const T cv = cur[3 * f + k];
+            const unsigned fv = fixed[3 * f + k];
+            // P zc is formed before the free-DOF test so that its loads go out with cur's
+            T acc = T(0);
+            const int nx = (fx & 1) ? 2 : 1, ny = (fy & 1) ? 2 : 1, nz = (fz & 1) ? 2 : 1;
+            for (int a = 0; a < nx; ++a)
+                for (int b = 0; b < nz; ++b)
+                    for (int e = 0; e < ny; ++e) {
+                        const int NX = (fx >> 1) + a, NZ = (fz >> 1) + b, NY = (fy >> 1) + e;
+                        const T w = (nx == 2 ? T(0.5) : T(1)) * (ny == 2 ? T(0.5) : T(1)) *
+                                    (nz == 2 ? T(0.5) : T(1));
+                        const long long N = NY + (long long)dc.nny * (NZ + (long long)dc.nnz * NX);
+                        acc += w * zc[3 * N + k];
+                    }
+            val = fv ? cv : cv + acc;
         }
         us[v] = val;
     }
@@ -782,11 +847,10 @@ __device__ __forceinline__ void prolong_smooth3s_body(int vb, const Dims& d, con
     }
     part[ty][tx] = acc;
     __syncthreads();
-    if (pl != 0 || !valid) return;
+    if (skip_now || !outp) return;
     const T a = (part[ty][tx] + part[ty + 1][tx]) + part[ty + 2][tx];
-    const long long i = 3 * n + c;
-    T o = us[3 * hc + c] + omega * dinv[i] * (r[i] - a);
-    if (fixed[i]) o = T(0);
+    T o = us[3 * hc + c] + omega * d_i * (r_i - a);
+    if (f_i) o = T(0);
     out[i] = o;
 }
 
@@ -798,8 +862,8 @@ __global__ void __launch_bounds__(288, 2) k_prolong_smooth3s(Dims d, Dims dc, co
                                                           const uint8_t* __restrict__ fixed, T omega,
                                                           const int* skip) {
     pdl_begin();
-    if (skip && *skip) return;
-    prolong_smooth3s_body<T, TY>(blockIdx.x, d, dc, zc, cur, S, R, r, dinv, out, fixed, omega);
+    const int sk = skip ? *skip : 0;  // tested before the stores, so its load overlaps the others
+    prolong_smooth3s_body<T, TY>(blockIdx.x, d, dc, zc, cur, S, R, r, dinv, out, fixed, omega, sk);
 }
 
 // Tile height (nodes along y) of k_prolong_smooth3s with the fewest idle lanes.
@@ -821,9 +885,11 @@ template <typename T>
 __global__ void k_jacobi_first(long long n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z,
                                T omega, const int* skip) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the store, so its load overlaps the others
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) z[i] = omega * dinv[i] * r[i];
+    if (i >= n) return;
+    const T v = omega * dinv[i] * r[i];
+    if (!sk) z[i] = v;
 }
 
 // ------------------------------------------------------- coarsest level
@@ -1058,14 +1124,14 @@ template <typename T>
 __global__ void k_dense_apply(int n, const T* __restrict__ Ainv, const T* __restrict__ r, T* __restrict__ z,
                               const int* skip) {
     pdl_begin();
-    if (skip && *skip) return;
+    const int sk = skip ? *skip : 0;  // tested before the store, so its load overlaps the others
     const int lane = threadIdx.x & 31;
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     double s = 0.0;
     for (int k = lane; k < n; k += 32) s += (double)Ainv[i * n + k] * (double)r[k];
     s = warp_sum(s);
-    if (lane == 0) z[i] = (T)s;
+    if (lane == 0 && !sk) z[i] = (T)s;
 }
 
 // ------------------------------------------------------------ host side
@@ -1302,7 +1368,7 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
                  mg->omega, skip);
     T* cur = L.z;
     T* oth = L.t;
-    const int nu = coarsest ? 4 * mg->nu : mg->nu;
+    const int nu = coarsest ? 4 * mg->nu : (l == 0 && mg->nu_fine > 0 ? mg->nu_fine : mg->nu);
     int s0 = 0;  // post-smoothing sweeps already done (1 when fused with the prolongation)
     for (int s = 1; s < nu; ++s) {
         level_op<T>(g, mg, l, 1, E, cur, rhs, oth, skip, st);

@@ -35,6 +35,7 @@ template <typename T>
 struct MG {
     int nlev = 0;
     int nu = 2;
+    int nu_fine = 0;        // sweeps on level 0 when > 0 (else nu)
     T omega = T(0.6);
     int nc = 0;             // coarsest DOFs (dense inverse) or 0 (smoothing only)
     std::vector<MGLevel<T>> lev;

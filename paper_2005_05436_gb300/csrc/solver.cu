@@ -70,20 +70,18 @@ __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restric
                                                  const T* __restrict__ dinv, T* __restrict__ p, PcgScalars* s,
                                                  double* partials, unsigned* counter) {
     pdl_begin();
-    if (s->done) return;
+    const int dn = s->done;  // tested before the stores, so its load overlaps the others
     DotAcc<T> acc;
     double tot[1];
     for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
-        T zi;
-        if (JAC) {
-            zi = dinv[i] * r[i];
-            z[i] = zi;
-        } else {
-            zi = z[i];
-        }
+        const T ri = r[i];
+        const T zi = JAC ? dinv[i] * ri : z[i];
+        if (dn) return;
+        if (JAC) z[i] = zi;
         if (FIRST) p[i] = zi;
-        acc.add(r[i], zi);
+        acc.add(ri, zi);
     }
+    if (dn) return;
     double v[1] = {acc.value()};
     if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0) {
         if (FIRST) {
@@ -104,11 +102,38 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
                                                  double* partials, unsigned* counter, const T* __restrict__ dinv0,
                                                  T* __restrict__ z0, T omega) {
     pdl_begin();
-    if (s->done) return;
+    const int dn = s->done;  // tested before the stores, so its load overlaps the others
     const T alpha = (T)s->alpha;
     DotAcc<T> acc;
     double tot[1];
-    for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT) {
+    const long long stride = (long long)gridDim.x * KNT;
+    long long i = (long long)blockIdx.x * KNT + threadIdx.x;
+    // four strided elements per trip with every load issued before the first
+    // use, so that a thread waits for memory once rather than four times
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        T xv[4], pv[4], rv[4], av[4], dv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long j = i + k * stride;
+            xv[k] = x[j];
+            pv[k] = p[j];
+            rv[k] = r[j];
+            av[k] = Ap[j];
+            dv[k] = dinv0 ? dinv0[j] : T(0);
+        }
+        if (dn) return;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long j = i + k * stride;
+            x[j] = xv[k] + alpha * pv[k];
+            const T ri = rv[k] - alpha * av[k];
+            r[j] = ri;
+            if (dinv0) z0[j] = omega * dv[k] * ri;
+            acc.add(ri, ri);
+        }
+    }
+    if (dn) return;
+    for (; i < n; i += stride) {
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * Ap[i];
         r[i] = ri;
@@ -133,12 +158,11 @@ template <typename T>
 __global__ void k_gpcg_p(long long n, const T* __restrict__ z, T* __restrict__ p, const PcgScalars* s,
                          cudaGraphConditionalHandle cond, int set_cond) {
     pdl_begin();
-    const int done = s->done;
-    if (!done) {
-        const T beta = (T)s->beta;
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x)
-            p[i] = z[i] + beta * p[i];
+    const int done = s->done;  // tested before the stores, so its load overlaps the others
+    const T beta = (T)s->beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T zi = z[i], pi = p[i];
+        if (!done) p[i] = zi + beta * pi;
     }
     if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
 }
@@ -304,6 +328,7 @@ static void pcg_alloc(to_grid* g, Solver* sv, Pcg<T>& P, bool gmg) {
     if (gmg) {
         P.mg = mg_create<T>(g, g->p.mg_levels, g->p.mg_nu, g->p.mg_omega);
         P.mg->coarse_every = g->p.mg_coarse_every;
+        P.mg->nu_fine = g->p.mg_nu_fine;
     }
 }
 
