@@ -216,25 +216,22 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV*NT/3
     __syncthreads();
 }
 
-// This thread's share of sum_i p[i] (i = threadIdx.x + k NT), in eight
-// independent chains so that eight loads are in flight; the order is fixed by
-// n and NT, so the result is deterministic.
+// This thread's share of sum_i p[i] (i = threadIdx.x + k NT): sixteen loads
+// per trip, all issued before the first is added (so a thread waits for memory
+// once per sixteen values, not once per value), into eight chains; the order is
+// fixed by n and NT, so the result is deterministic.
 template <int NT>
 __device__ __forceinline__ double partial_sum(const double* p, int n) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0, a7 = 0.0, t = 0.0;
-    int i = threadIdx.x;
-    for (; i + 7 * NT < n; i += 8 * NT) {
-        a0 += __ldcg(&p[i]);
-        a1 += __ldcg(&p[i + NT]);
-        a2 += __ldcg(&p[i + 2 * NT]);
-        a3 += __ldcg(&p[i + 3 * NT]);
-        a4 += __ldcg(&p[i + 4 * NT]);
-        a5 += __ldcg(&p[i + 5 * NT]);
-        a6 += __ldcg(&p[i + 6 * NT]);
-        a7 += __ldcg(&p[i + 7 * NT]);
+    constexpr int M = 16;
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += M * NT) {
+        double v[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) v[k] = i + k * NT < n ? __ldcg(&p[i + k * NT]) : 0.0;
+#pragma unroll
+        for (int k = 0; k < M; ++k) a[k & 7] += v[k];
     }
-    for (; i < n; i += NT) t += __ldcg(&p[i]);
-    return (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) + t;
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // Two-level deterministic reduction inside one launch: every block stores its
