@@ -66,6 +66,7 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--mg-nu", type=int, default=1, help="GMG smoothing sweeps per level")
     ap.add_argument("--mg-nu-fine", type=int, default=0, help="GMG smoothing sweeps on the finest level (0: --mg-nu)")
+    ap.add_argument("--mg-omega", type=float, default=1.8, help="GMG l1-Jacobi smoother weight")
     ap.add_argument("--inner-rtol", type=float, default=3e-3,
                     help="mixed path: residual drop of each FP32 PCG segment (reliable updates) or inner solve")
     ap.add_argument("--refine", default="reliable", choices=["reliable", "flexible"],
@@ -196,6 +197,7 @@ def _make_design(args, w, precision, precond, ku_impl, stream):
                        cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
                        ku_impl=ku_impl, loop_mode=args.loop_mode, mg_nu=args.mg_nu,
                        inner_rtol=args.inner_rtol, mg_coarse_every=args.mg_coarse_every, mg_nu_fine=args.mg_nu_fine,
+                       mg_omega=args.mg_omega,
                        refine=0 if args.refine == "reliable" else 1,
                        oc_method=0 if args.oc_method == "bisection" else 1, pdl_off=1 if args.no_pdl else 0,
                        penal_cnt=(1, 3.0, 25, 0.25),
@@ -490,7 +492,7 @@ def run_ours(args):
         "data": "synthetic (paper's cantilever load and supports; no dataset)",
         "config": {"workload": workload_name(w), "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
                    "precision": args.precision, "precond": args.precond, "ku_impl": args.ku_impl,
-                   "mg_nu": args.mg_nu, "mg_nu_fine": args.mg_nu_fine or args.mg_nu, "inner_rtol": args.inner_rtol, "mg_coarse_every": args.mg_coarse_every,
+                   "mg_nu": args.mg_nu, "mg_nu_fine": args.mg_nu_fine or args.mg_nu, "mg_omega": args.mg_omega, "inner_rtol": args.inner_rtol, "mg_coarse_every": args.mg_coarse_every,
                    "refine": args.refine, "pdl": not args.no_pdl,
                    "oc_method": args.oc_method,
                    "learned_warm_start": learned_info,

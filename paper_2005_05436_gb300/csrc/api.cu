@@ -205,7 +205,7 @@ to_status to_params_init(to_params* p, int32_t dim, int32_t nelx, int32_t nely, 
     p->mg_levels = 0;
     p->deadline_cycles = 2000000000LL;
     p->inner_rtol = 1e-3;
-    p->mg_omega = 1.0;
+    p->mg_omega = 1.8;
     p->mg_nu = 2;
     p->mg_coarse_every = 1;
     p->oc_method = TO_OC_BISECTION;
