@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--mg-nu", type=int, default=1, help="GMG smoothing sweeps per level")
     ap.add_argument("--mg-nu-fine", type=int, default=0, help="GMG smoothing sweeps on the finest level (0: --mg-nu)")
     ap.add_argument("--mg-omega", type=float, default=1.8, help="GMG l1-Jacobi smoother weight")
+    ap.add_argument("--mg-omega-coarse", type=float, default=0.0,
+                    help="GMG l1-Jacobi weight below the finest level (0: --mg-omega)")
     ap.add_argument("--inner-rtol", type=float, default=3e-3,
                     help="mixed path: residual drop of each FP32 PCG segment (reliable updates) or inner solve")
     ap.add_argument("--refine", default="reliable", choices=["reliable", "flexible"],
@@ -197,7 +199,7 @@ def _make_design(args, w, precision, precond, ku_impl, stream):
                        cg_rtol=w["cg_rtol"], cg_maxit=50000, precision=precision, precond=precond,
                        ku_impl=ku_impl, loop_mode=args.loop_mode, mg_nu=args.mg_nu,
                        inner_rtol=args.inner_rtol, mg_coarse_every=args.mg_coarse_every, mg_nu_fine=args.mg_nu_fine,
-                       mg_omega=args.mg_omega,
+                       mg_omega=args.mg_omega, mg_omega_coarse=args.mg_omega_coarse,
                        refine=0 if args.refine == "reliable" else 1,
                        oc_method=0 if args.oc_method == "bisection" else 1, pdl_off=1 if args.no_pdl else 0,
                        penal_cnt=(1, 3.0, 25, 0.25),

@@ -160,6 +160,8 @@ typedef struct to_params {
     int32_t mg_nu_fine;     /* GMG: pre- and post-smoothing sweeps on the finest level; 0 (default):
                                mg_nu, like the coarser levels; 1..16 otherwise, else TO_EINVAL */
     int32_t _pad5;
+    double mg_omega_coarse; /* GMG: l1-Jacobi weight on the levels below the finest; 0 (default):
+                               mg_omega; else in (0, 2), else TO_EINVAL */
 } to_params;
 
 typedef struct to_grid to_grid;  /* opaque handle: workspaces, filter weights, graphs */

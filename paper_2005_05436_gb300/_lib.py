@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("pae_q0", C.c_int32), ("pae_q", C.c_int32), ("pae_m", C.c_int32), ("pae_alpha", C.c_double),
                 ("pae_zeta", C.c_double), ("inner_maxit", C.c_int32), ("refine", C.c_int32),
                 ("mg_unfused", C.c_int32), ("pdl_off", C.c_int32),
-                ("mg_nu_fine", C.c_int32), ("_pad5", C.c_int32)]
+                ("mg_nu_fine", C.c_int32), ("_pad5", C.c_int32), ("mg_omega_coarse", C.c_double)]
 
 
 class SolveInfo(C.Structure):

@@ -149,6 +149,8 @@ static void validate(const to_params* p) {
     TOPO_REQUIRE(p->mg_omega > 0.0 && p->mg_omega < 2.0 && p->mg_nu >= 1 && p->mg_nu <= 16,
                  "mg_omega in (0, 2), mg_nu in [1, 16]");
     TOPO_REQUIRE(p->mg_nu_fine >= 0 && p->mg_nu_fine <= 16, "mg_nu_fine must be in [0, 16]");
+    TOPO_REQUIRE(p->mg_omega_coarse == 0.0 || (p->mg_omega_coarse > 0.0 && p->mg_omega_coarse < 2.0),
+                 "mg_omega_coarse must be 0 or in (0, 2)");
     TOPO_REQUIRE(p->ku_impl >= 0 && p->ku_impl <= 4, "ku_impl must be 0, 1, 2, 3 or 4");
     TOPO_REQUIRE(p->pae_q0 >= 0 && p->pae_q >= 1 && p->pae_m >= 1 && p->pae_m <= 4 && p->pae_alpha > 0.0 &&
                      p->pae_alpha <= 1.0 && p->pae_zeta >= 0.0 && p->pae_zeta <= 1.0,

@@ -1155,6 +1155,7 @@ MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
         mg->fuse_up = g->p.mg_unfused == 0;
         mg->nu = nu;
         mg->omega = (T)omega;
+        mg->omega_c = (T)(g->p.mg_omega_coarse > 0.0 ? g->p.mg_omega_coarse : omega);
         Dims d = g->d;
         const int dim = d.dim;
         mg->lev.push_back(MGLevel<T>());
@@ -1338,7 +1339,7 @@ static void level_op(to_grid* g, MG<T>* mg, int l, int mode, const T* E, const T
         return;
     }
     const int nb = div_up(L.d.nnodes, 256);
-    const T w = mg->omega;
+    const T w = mg->omega_c;
 #define TOPO_SOP(DIMV, MODEV) \
     launch_k(k_stencil_op<T, DIMV, MODEV>, nb, 256, 0, st, L.d, L.S, L.R, u, r, L.dinv, out, L.fixed, w, skip)
 #define TOPO_SOP3(MODEV)                                                                                  \
@@ -1365,7 +1366,7 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
     }
     if (!first_done)
         launch_k(k_jacobi_first<T>, div_up(L.d.ndof, 256), 256, 0, st, L.d.ndof, (const T*)L.dinv, rhs, L.z,
-                 mg->omega, skip);
+                 l == 0 ? mg->omega : mg->omega_c, skip);
     T* cur = L.z;
     T* oth = L.t;
     const int nu = coarsest ? 4 * mg->nu : (l == 0 && mg->nu_fine > 0 ? mg->nu_fine : mg->nu);
@@ -1384,10 +1385,10 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
         const T* dc_inv = jf ? C.dinv : nullptr;
         if (L.d.dim == 3)
             launch_k(k_restrict3s<T>, div_up(C.d.nnodes, 32), dim3(32, 9), 0, st, C.d, L.d, (const T*)L.w, C.r,
-                     (const uint8_t*)C.fixed, skip, dc_inv, C.z, mg->omega);
+                     (const uint8_t*)C.fixed, skip, dc_inv, C.z, mg->omega_c);
         else
             launch_k(k_restrict<T, 2>, nbc, 256, 0, st, C.d, L.d, (const T*)L.w, C.r, (const uint8_t*)C.fixed,
-                     skip, dc_inv, C.z, mg->omega);
+                     skip, dc_inv, C.z, mg->omega_c);
         T* zc = vcycle_level<T>(g, mg, l + 1, E, C.r, skip, st, nullptr, nullptr, jf);
         // small levels only: on a large one the halo's repeated prolongation costs
         // more loads than the separate kernel (tiles are one node thick in x)
@@ -1398,7 +1399,7 @@ static T* vcycle_level(to_grid* g, MG<T>* mg, int l, const T* E, const T* rhs, c
             const dim3 blk(32, 9);
 #define TOPO_PS(TYV)                                                                                   \
     launch_k(k_prolong_smooth3s<T, TYV>, (unsigned)nb, blk, 0, st, L.d, C.d, (const T*)zc, (const T*)cur, \
-             (const T*)L.S, (const T*)L.R, rhs, (const T*)L.dinv, oth, (const uint8_t*)L.fixed, mg->omega, skip)
+             (const T*)L.S, (const T*)L.R, rhs, (const T*)L.dinv, oth, (const uint8_t*)L.fixed, mg->omega_c, skip)
             if (ty == 8)
                 TOPO_PS(8);
             else if (ty == 16)

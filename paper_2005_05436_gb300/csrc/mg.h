@@ -36,7 +36,8 @@ struct MG {
     int nlev = 0;
     int nu = 2;
     int nu_fine = 0;        // sweeps on level 0 when > 0 (else nu)
-    T omega = T(0.6);
+    T omega = T(0.6);       // l1-Jacobi weight on the finest level
+    T omega_c = T(0.6);     // and on the coarser ones
     int nc = 0;             // coarsest DOFs (dense inverse) or 0 (smoothing only)
     std::vector<MGLevel<T>> lev;
     T* A = nullptr;         // coarsest dense matrix and its Cholesky factor [nc * nc]
