@@ -55,11 +55,16 @@ def test_params_defaults_follow_the_paper(lib):
     assert (p.penal_cnt.istart, p.penal_cnt.maxpar, p.penal_cnt.isteps, p.penal_cnt.delta) == (1, 3.0, 25, 0.25)
     assert (p.newton_tol, p.oc_tol) == (1e-6, 1e-4)
     assert (p.inner_rtol, p.inner_maxit) == (1e-3, 2000)
+    # solver options (no counterpart in the paper): l1-Jacobi weight 1.8 on every level, the finest
+    # level's sweeps as mg_nu, programmatic dependent launch on, the fusions on
+    assert (p.mg_omega, p.mg_omega_coarse, p.mg_nu_fine, p.pdl_off, p.mg_unfused) == (1.8, 0.0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("field,value", [("dim", 4), ("nelx", 0), ("volfrac", 1.5), ("ft", 7),
                                          ("ftBC", ord("X")), ("rmin", -1.0), ("nelz", 3), ("inner_maxit", 0),
-                                         ("oc_method", 7), ("pae_m", 5), ("inner_rtol", 1.0)])
+                                         ("oc_method", 7), ("pae_m", 5), ("inner_rtol", 1.0),
+                                         ("mg_omega", 2.0), ("mg_omega_coarse", 2.5), ("mg_omega_coarse", -0.5),
+                                         ("mg_nu_fine", 17), ("mg_nu_fine", -1)])
 def test_invalid_params_rejected_on_host(lib, field, value):
     from paper_2005_05436_gb300 import _lib as L
     p = L.default_params(2, 8, 4)
