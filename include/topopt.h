@@ -141,15 +141,22 @@ typedef struct to_params {
                                iterate to the FP64 flexible-CG step, whose exact line search still
                                lowers the energy. >= 1, else TO_EINVAL */
     int32_t refine;         /* TO_MIXED, single grid: how the FP64 residual corrects the FP32 solve.
+                               In both schemes the FP32 PCG (vectors, operator, preconditioner in
+                               FP32) accumulates its iterate in FP64.
                                TO_REFINE_RELIABLE (default): one FP32 PCG whose residual is
                                replaced by the true FP64 residual b - K U (FP64 U += FP32
                                correction) each time it has fallen by inner_rtol; the search
-                               direction is kept across the replacement, so the Krylov space is
-                               not restarted; if a segment reaches min(inner_maxit, 400)
-                               iterations or a replacement does not halve the FP64 residual, the
-                               solve continues as TO_REFINE_FLEXIBLE. TO_REFINE_FLEXIBLE:
-                               FP32 inner solves to inner_rtol from scratch, each followed by one
-                               FP64 flexible-CG step (exact line search). */
+                               direction is kept across the replacement (the Krylov space is not
+                               restarted) while the true residual fell at least a quarter as far
+                               as the recursive one, else the next segment restarts from the true
+                               residual; if a segment reaches min(inner_maxit, 400) iterations,
+                               or 16 + 4 times the first segment's iterations per decade of drop,
+                               or a replacement does not halve the FP64 residual, the solve
+                               continues as TO_REFINE_FLEXIBLE. TO_REFINE_FLEXIBLE: FP32 inner
+                               solves to inner_rtol from scratch, each followed by one FP64
+                               flexible-CG step (exact line search). If either ends in a
+                               non-finite value, or at 60 refinements with cg_maxit not reached,
+                               the FP64 PCG finishes the solve (to_solve_info.fallback). */
     int32_t mg_unfused;     /* GMG, 3D coarse levels of at most 16,384 nodes: 0 prolongation fused
                                into the first post-smoothing sweep (default); 1 separate kernels
                                (same arithmetic and order, for comparison) */
@@ -172,7 +179,9 @@ typedef struct to_solve_info {
     int32_t refinements;    /* outer FP64 refinement steps (TO_MIXED), else 0 */
     double rel_res;         /* ||F - K U||_2 / ||F||_2 in FP64 at exit */
     int32_t status;         /* to_status of the solve */
-    int32_t _pad;
+    int32_t fallback;       /* TO_MIXED: 1 if the FP32 iteration failed (a non-finite value, or
+                               the refinement cap with cg_maxit not reached) and the FP64 PCG
+                               finished the solve (iters counts both), else 0 */
     double t_setup_ms;      /* preconditioner set-up (CUDA events) */
     double t_krylov_ms;     /* PCG iterations (the inner FP32 solves in TO_MIXED) */
     double t_resid_ms;      /* FP64 true residuals and refinement updates */
@@ -214,7 +223,7 @@ typedef struct to_iter_info {
     double warm_err;        /* the same for the warm start actually used (<= warm_err_prev under
                                TO_WARM_ENERGY) */
     int32_t pae;            /* Anderson extrapolation of this step: 0 off, 1 damped step, 2 extrapolated */
-    int32_t _pad2;
+    int32_t fallback;       /* to_solve_info.fallback of the state solve */
     double warm_res_prev;   /* ||F - K U_prev|| / ||F|| over the free DOFs (operator products in the
                                warm start's precision), 0 without a network */
     double warm_res;        /* the same for the warm start actually used (<= warm_res_prev under

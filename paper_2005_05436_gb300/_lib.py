@@ -49,7 +49,7 @@ class Params(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("rel_res", C.c_double),
-                ("status", C.c_int32), ("_pad", C.c_int32), ("t_setup_ms", C.c_double),
+                ("status", C.c_int32), ("fallback", C.c_int32), ("t_setup_ms", C.c_double),
                 ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double)]
 
 
@@ -67,7 +67,7 @@ class IterInfo(C.Structure):
                 ("rel_res", C.c_double), ("t_filter_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("t_sens_ms", C.c_double), ("t_oc_ms", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_krylov_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_warm_ms", C.c_double), ("warm_a", C.c_double), ("warm_b", C.c_double),
-                ("warm_err_prev", C.c_double), ("warm_err", C.c_double), ("pae", C.c_int32), ("_pad2", C.c_int32),
+                ("warm_err_prev", C.c_double), ("warm_err", C.c_double), ("pae", C.c_int32), ("fallback", C.c_int32),
                 ("warm_res_prev", C.c_double), ("warm_res", C.c_double)]
 
     def as_dict(self):

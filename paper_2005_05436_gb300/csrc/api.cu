@@ -676,6 +676,7 @@ to_status to_step(to_grid* g, to_state* s, to_iter_info* info) {
     it.loop = s->loop;
     it.n_cg = si.iters;
     it.n_refine = si.refinements;
+    it.fallback = si.fallback;
     it.rel_res = si.rel_res;
     it.c = h.c;
     if (g->net && h.c > 0.0) {  // energy errors relative to the zero start: (E(U) - E*) / (-E*), E* = -c / 2

@@ -254,11 +254,11 @@ __global__ void kb_begin_solve(BG* G, BS* S, int count, cudaGraphConditionalHand
 
 // FP64 refinement test: r = F - K(E64) U on free DOFs; ||r|| / ||F||. Instances
 // at or below rtol (or at max_ref refinements) stop; the others keep r (FP64)
-// and get r32 = (float) r and x32 = 0 for the next inner solve.
+// and get r32 = (float) r and xin = 0 for the next inner solve.
 __global__ void kb_resid(BK k, const KeP<double, 8> ke, const double* __restrict__ E64,
                          const double* __restrict__ U, const double* __restrict__ F,
                          const uint8_t* __restrict__ fixed, double* __restrict__ r64, float* __restrict__ r32,
-                         float* __restrict__ x32, double rtol, int max_ref) {
+                         double* __restrict__ xin, double rtol, int max_ref) {
     B_TILE(k)
     if (S.ref_done) return;
     double v[2] = {0.0, 0.0}, tot[2];
@@ -273,7 +273,7 @@ __global__ void kb_resid(BK k, const KeP<double, 8> ke, const double* __restrict
             const double r = f ? 0.0 : b - a[c];
             r64[i + c] = r;
             r32[i + c] = (float)r;
-            x32[i + c] = 0.f;
+            xin[i + c] = 0.0;
             v[0] += r * r;
             v[1] += b * b;
         }
@@ -348,7 +348,7 @@ __global__ void kb_ku32(BK k, const KeP<float, 8> ke, const float* __restrict__ 
 }
 
 // x += alpha p, r -= alpha Ap, z = D^-1 r; stopping test ||r|| <= inner_rtol ||r0||.
-__global__ void kb_inner_update(BK k, const float* __restrict__ dinv, float* __restrict__ x32,
+__global__ void kb_inner_update(BK k, const float* __restrict__ dinv, double* __restrict__ xin,
                                 float* __restrict__ r32, float* __restrict__ z32, const float* __restrict__ p32,
                                 const float* __restrict__ Ap32, double inner_rtol, int maxit) {
     B_TILE(k)
@@ -359,7 +359,7 @@ __global__ void kb_inner_update(BK k, const float* __restrict__ dinv, float* __r
         const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            x32[i + c] += alpha * p32[i + c];
+            xin[i + c] += (double)alpha * (double)p32[i + c];
             const float r = r32[i + c] - alpha * Ap32[i + c];
             r32[i + c] = r;
             const float z = dinv[i + c] * r;
@@ -426,7 +426,7 @@ __global__ void kb_mg_init(BK k, const float* __restrict__ r32, const float* __r
 }
 
 // x += alpha p, r -= alpha Ap; stopping test ||r|| <= inner_rtol ||r0||.
-__global__ void kb_mg_xr(BK k, float* __restrict__ x32, float* __restrict__ r32, const float* __restrict__ p32,
+__global__ void kb_mg_xr(BK k, double* __restrict__ xin, float* __restrict__ r32, const float* __restrict__ p32,
                          const float* __restrict__ Ap32, double inner_rtol, int maxit) {
     B_TILE(k)
     if (S.ref_done || S.inner_done) return;
@@ -436,7 +436,7 @@ __global__ void kb_mg_xr(BK k, float* __restrict__ x32, float* __restrict__ r32,
         const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            x32[i + c] += alpha * p32[i + c];
+            xin[i + c] += (double)alpha * (double)p32[i + c];
             const float r = r32[i + c] - alpha * Ap32[i + c];
             r32[i + c] = r;
             rr.add(r, r);
@@ -471,32 +471,32 @@ __global__ void kb_mg_rz(BK k, const float* __restrict__ r32, const float* __res
 }
 
 // FP64 outer iteration as a flexible CG with one previous direction: the FP32
-// inner solution d (x32) is K-orthogonalised against the previous direction,
+// inner solution d (xin) is K-orthogonalised against the previous direction,
 // p = d + beta p_prev with beta = -(d . K p_prev) / (p_prev . K p_prev), and
 // taken with the exact FP64 line search alpha = (p . r) / (p . K p). Every step
 // minimises the energy norm of the error along p, so the error cannot grow even
 // when an FP32 inner solve is poor (high-contrast designs push the condition
 // number of K far beyond the reach of FP32 refinement).
-__global__ void kb_fcg_beta(BK k, const float* __restrict__ x32, const double* __restrict__ Kp64) {
+__global__ void kb_fcg_beta(BK k, const double* __restrict__ xin, const double* __restrict__ Kp64) {
     B_TILE(k)
     if (S.ref_done || !S.f_has_prev) return;
     double v[1] = {0.0}, tot[1];
     if (tx_ < I.nnx && ty_ < I.nny) {
         const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
-        v[0] = (double)x32[i] * Kp64[i] + (double)x32[i + 1] * Kp64[i + 1];
+        v[0] = xin[i] * Kp64[i] + xin[i + 1] * Kp64[i + 1];
     }
     if (!seg_reduce<1>(k, I.tn0, I.tnn, &k.counters[inst], v, tot) || threadIdx.x) return;
     S.f_beta = S.f_pkp > 0.0 ? -tot[0] / S.f_pkp : 0.0;
 }
 
-__global__ void kb_fcg_dir(BK k, const float* __restrict__ x32, double* __restrict__ p64) {
+__global__ void kb_fcg_dir(BK k, const double* __restrict__ xin, double* __restrict__ p64) {
     B_TILE(k)
     if (S.ref_done) return;
     if (tx_ >= I.nnx || ty_ >= I.nny) return;
     const double beta = S.f_has_prev ? S.f_beta : 0.0;
     const long long i = 2 * (I.node0 + ty_ + (long long)I.nny * tx_);
-    p64[i] = (double)x32[i] + beta * p64[i];
-    p64[i + 1] = (double)x32[i + 1] + beta * p64[i + 1];
+    p64[i] = xin[i] + beta * p64[i];
+    p64[i + 1] = xin[i + 1] + beta * p64[i + 1];
 }
 
 // Kp = K(E64) p (Dirichlet rows 0); alpha = (p . r) / (p . Kp).
@@ -848,7 +848,7 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
         KB_LAUNCH(kb_begin_solve, 1, 256, st, b->dG, b->dS, b->count, h_ref);
         b->k_static += captured_launches_reset();
         add_while(st, b->sb[0], h_ref, [&](cudaStream_t s) {
-            KB_LAUNCH(kb_resid, nb_n, tn, s, kn, b->ke64, b->E64, U, b->F, b->fixed, b->r64, b->r32, b->x32,
+            KB_LAUNCH(kb_resid, nb_n, tn, s, kn, b->ke64, b->E64, U, b->F, b->fixed, b->r64, b->r32, b->xin,
                       p.cg_rtol, max_ref);
             float* zmg = nullptr;
             if (b->mg) {
@@ -863,20 +863,20 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
             add_while(s, b->sb[1], h_in, [&](cudaStream_t s2) {
                 KB_LAUNCH(kb_ku32, nb_n, tn, s2, kn, b->ke32, b->E32, b->p32, b->Ap32, b->fixed);
                 if (b->mg) {
-                    KB_LAUNCH(kb_mg_xr, nb_n, tn, s2, kn, b->x32, b->r32, b->p32, b->Ap32, p.inner_rtol, inner_cap);
+                    KB_LAUNCH(kb_mg_xr, nb_n, tn, s2, kn, b->xin, b->r32, b->p32, b->Ap32, p.inner_rtol, inner_cap);
                     float* z = bmg_vcycle(b, s2, b->r32, 1);
                     TOPO_REQUIRE(z == zmg, "V-cycle output buffer");
                     KB_LAUNCH(kb_mg_rz, nb_n, tn, s2, kn, b->r32, z);
                     KB_LAUNCH(kb_inner_p, nb_n, tn, s2, kn, z, b->p32, h_in);
                 } else {
-                    KB_LAUNCH(kb_inner_update, nb_n, tn, s2, kn, b->dinv, b->x32, b->r32, b->z32, b->p32, b->Ap32,
+                    KB_LAUNCH(kb_inner_update, nb_n, tn, s2, kn, b->dinv, b->xin, b->r32, b->z32, b->p32, b->Ap32,
                               p.inner_rtol, inner_cap);
                     KB_LAUNCH(kb_inner_p, nb_n, tn, s2, kn, b->z32, b->p32, h_in);
                 }
             });
             b->k_body[LOOP_INNER] = captured_launches_reset();
-            KB_LAUNCH(kb_fcg_beta, nb_n, tn, s, kn, b->x32, b->Kp64);
-            KB_LAUNCH(kb_fcg_dir, nb_n, tn, s, kn, b->x32, b->p64);
+            KB_LAUNCH(kb_fcg_beta, nb_n, tn, s, kn, b->xin, b->Kp64);
+            KB_LAUNCH(kb_fcg_dir, nb_n, tn, s, kn, b->xin, b->p64);
             KB_LAUNCH(kb_fcg_kp, nb_n, tn, s, kn, b->ke64, b->E64, b->p64, b->r64, b->Kp64, b->fixed);
             KB_LAUNCH(kb_refine, nb_n, tn, s, kn, b->p64, U, h_ref);
             b->k_body[LOOP_REF] += captured_launches_reset();
@@ -1037,8 +1037,8 @@ to_status to_batch_init(const to_params* base, int32_t count, const to_instance*
         b->counters = balloc<unsigned>(b, count);
         for (double** a : {&b->xt, &b->dprj, &b->dc, &b->dcf, &b->dV0, &b->ocP, &b->E64}) *a = balloc<double>(b, el);
         b->E32 = balloc<float>(b, el);
-        for (float** a : {&b->dinv, &b->r32, &b->z32, &b->p32, &b->Ap32, &b->x32}) *a = balloc<float>(b, 2 * nd);
-        for (double** a : {&b->r64, &b->p64, &b->Kp64}) *a = balloc<double>(b, 2 * nd);
+        for (float** a : {&b->dinv, &b->r32, &b->z32, &b->p32, &b->Ap32}) *a = balloc<float>(b, 2 * nd);
+        for (double** a : {&b->r64, &b->p64, &b->Kp64, &b->xin}) *a = balloc<double>(b, 2 * nd);
         TOPO_CUDA(cudaMemcpyAsync(b->toff, toff.data(), toff.size() * sizeof(int2), cudaMemcpyHostToDevice, b->st));
         TOPO_CUDA(cudaMemcpyAsync(b->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, b->st));
         TOPO_CUDA(cudaMemsetAsync(b->counters, 0, count * sizeof(unsigned), b->st));

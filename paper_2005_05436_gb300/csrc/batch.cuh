@@ -268,6 +268,7 @@ struct CInst {
     int level, nc, nnx, nny;
     long long node0, a0;   // node offset within the level; offset of the inverse in the pool
     const float* S;        // the level's stencils (SoA, stride nnode)
+    const float* R;        // and their row sums (SoA, stride nnode)
     const uint8_t* fixed;  // the level's Dirichlet mask
     const float* rhs;      // the level's right-hand side
     float* z;              // the level's V-cycle output buffer
@@ -286,6 +287,7 @@ struct BMGLevel {
     float *Kel = nullptr, *S = nullptr, *R = nullptr, *dinv = nullptr;
     float *z = nullptr, *t = nullptr, *w = nullptr, *r = nullptr;
     uint8_t* fixed = nullptr;
+    uint8_t* touched = nullptr;  // [nel] coarse levels: a fine Dirichlet DOF lies under the element
 };
 
 struct BMG {
@@ -354,8 +356,11 @@ struct to_batch {
     const uint8_t* fixed = nullptr;
     double *xt = nullptr, *dprj = nullptr, *dc = nullptr, *dcf = nullptr, *dV0 = nullptr, *ocP = nullptr,
            *E64 = nullptr;
-    float *E32 = nullptr, *dinv = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *Ap32 = nullptr,
-          *x32 = nullptr;
+    float *E32 = nullptr, *dinv = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
+    // inner solution of the FP32 PCG, accumulated in FP64: rounded to FP32 at
+    // every step it would limit the inner solve's true residual to about
+    // eps_32 || |K| |x| || (the recursion for r32 never sees that rounding)
+    double* xin = nullptr;
     double *r64 = nullptr, *p64 = nullptr, *Kp64 = nullptr;  // outer flexible CG
     topo::KeP<double, 8> ke64{};
     topo::KeP<float, 8> ke32{};

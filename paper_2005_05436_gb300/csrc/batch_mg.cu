@@ -74,13 +74,19 @@ __global__ void kbm_l1_fine(BKL k, const RowAbs8 ra, const float* __restrict__ E
 }
 
 // One warp per coarse element: Kc = sum_j P_j^T K_j P_j (8 x 8, row-major, local
-// node order of local_node()).
+// node order of local_node()). touched_c[ec] = 1 if a fine Dirichlet DOF lies
+// under the element (level 1: among its 3 x 3 fine nodes; deeper: under one of
+// its children); an untouched element matrix annihilates the rigid
+// translations exactly (K_j does, and P_j maps a coarse translation to the same
+// fine one).
 template <bool FROM_FINE>
 __global__ void __launch_bounds__(256) kbm_galerkin(const LInst* __restrict__ Lc, const long long* __restrict__ cstart,
                                                     int count, long long nelc, const LInst* __restrict__ Lf,
                                                     const float* __restrict__ Ef, const uint8_t* __restrict__ fixed_f,
                                                     const KeP<float, 8> ke, const float* __restrict__ Cj,
-                                                    const float* __restrict__ Kf, float* __restrict__ Kc) {
+                                                    const float* __restrict__ Kf, float* __restrict__ Kc,
+                                                    const uint8_t* __restrict__ touched_f,
+                                                    uint8_t* __restrict__ touched_c) {
     __shared__ float pw[64];  // [j][b][B]
     __shared__ float Ks[8][256];
     __shared__ float Ts[8][256];
@@ -106,12 +112,12 @@ __global__ void __launch_bounds__(256) kbm_galerkin(const LInst* __restrict__ Lc
     if (FROM_FINE) {
         const bool inside = 2 * ex + 1 < F.nelx && 2 * ey + 1 < F.nely;
         bool fx = false;
-        if (inside && lane < 18) {
-            const int q = lane >> 1, c = lane & 1;
-            const long long nf = F.node0 + (2 * ey + q % 3) + (long long)F.nny * (2 * ex + q / 3);
-            fx = fixed_f[2 * nf + c] != 0;
+        if (lane < 18) {
+            const int q = lane >> 1, c = lane & 1, fy = 2 * ey + q % 3, fxn = 2 * ex + q / 3;
+            if (fy < F.nny && fxn < F.nnx) fx = fixed_f[2 * (F.node0 + fy + (long long)F.nny * fxn) + c] != 0;
         }
         const bool any_fixed = __any_sync(0xffffffffu, fx);
+        if (lane == 0) touched_c[ec] = any_fixed ? 1 : 0;
         if (inside && !any_fixed) {
             float Ej[4];
 #pragma unroll
@@ -127,6 +133,13 @@ __global__ void __launch_bounds__(256) kbm_galerkin(const LInst* __restrict__ Lc
             }
             return;
         }
+    } else if (lane == 0) {
+        int tch = 0;
+        for (int j = 0; j < 4; ++j) {
+            const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j));
+            if (exf < F.nelx && eyf < F.nely) tch |= touched_f[F.el0 + eyf + (long long)F.nely * exf];
+        }
+        touched_c[ec] = (uint8_t)tch;
     }
     for (int idx = lane; idx < 256; idx += 32) {
         const int j = idx >> 6, rem = idx & 63, row = rem >> 3, col = rem & 7;
@@ -170,9 +183,14 @@ __global__ void __launch_bounds__(256) kbm_galerkin(const LInst* __restrict__ Lc
 
 // Node stencils of a coarse level from its element matrices: S[s][c][k] is the
 // (n, n + s) block summed over the elements containing both nodes, R the row
-// sums; l1-Jacobi weights; DOFs with a zero diagonal become Dirichlet.
-__global__ void kbm_stencil(BKL k, const float* __restrict__ Kel, float* __restrict__ Sst, float* __restrict__ R,
-                            float* __restrict__ dinv, uint8_t* __restrict__ fixed, long long nn) {
+// sums (the operator applied to the unit translations), stored as exactly 0 at
+// a node none of whose elements is touched by a Dirichlet DOF (summed in FP32
+// they would hold the rounding of cancelling blocks, which the relative form
+// R_n u_n applies to absolute displacements); l1-Jacobi weights; DOFs with a
+// zero diagonal become Dirichlet.
+__global__ void kbm_stencil(BKL k, const float* __restrict__ Kel, const uint8_t* __restrict__ touched,
+                            float* __restrict__ Sst, float* __restrict__ R, float* __restrict__ dinv,
+                            uint8_t* __restrict__ fixed, long long nn) {
     BL_TILE(k)
     (void)S;
     if (ix >= L.nnx || iy >= L.nny) return;
@@ -209,8 +227,14 @@ __global__ void kbm_stencil(BKL k, const float* __restrict__ Kel, float* __restr
             dg[1] = blk[3];
         }
     }
+    bool tch = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) R[(long long)q * nn + n] = rs[q];
+    for (int o = 0; o < 4; ++o) {
+        const int ex = ix - 1 + (o >> 1), ey = iy - 1 + (o & 1);
+        if (ex >= 0 && ex < L.nelx && ey >= 0 && ey < L.nely) tch |= touched[L.el0 + ey + (long long)L.nely * ex] != 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) R[(long long)q * nn + n] = tch ? rs[q] : 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const bool f = !(dg[c] > 0.f);
@@ -219,9 +243,11 @@ __global__ void kbm_stencil(BKL k, const float* __restrict__ Kel, float* __restr
     }
 }
 
-// One CTA per instance: assemble the coarsest operator (FP64), Cholesky
-// A = L L^T, X = L^-1, and the inverse A^-1 = X^T X stored in FP32. Dirichlet
-// DOFs get identity rows and columns.
+// One CTA per instance: assemble the coarsest operator (FP64; the diagonal block
+// of node n as R_n - sum_{m != n} S_nm, the operator the relative-form stencil
+// applies, exact for the rigid translations), Cholesky A = L L^T with pivots
+// floored at 1e-6 of the original diagonal, X = L^-1, and the inverse
+// A^-1 = X^T X stored in FP32. Dirichlet DOFs get identity rows and columns.
 __global__ void __launch_bounds__(256) kbm_dense_factor(const CInst* __restrict__ Cs, double* __restrict__ Aw,
                                                         float* __restrict__ Ainv) {
     const CInst& c = Cs[blockIdx.x];
@@ -243,23 +269,32 @@ __global__ void __launch_bounds__(256) kbm_dense_factor(const CInst* __restrict_
                 A[(long long)row * n + row] = 1.0;
                 continue;
             }
+            double dg[2] = {(double)c.R[(long long)(cc * 2) * c.nnode + gn],
+                            (double)c.R[(long long)(cc * 2 + 1) * c.nnode + gn]};
             for (int s = 0; s < 9; ++s) {
+                if (s == 4) continue;
                 const int mx = ix + s / 3 - 1, my = iy + s % 3 - 1;
                 if (mx < 0 || mx >= c.nnx || my < 0 || my >= c.nny) continue;
                 const int m = my + c.nny * mx;
                 for (int kk = 0; kk < 2; ++kk) {
-                    if (c.fixed[2 * (c.node0 + m) + kk]) continue;
-                    A[(long long)row * n + 2 * m + kk] = (double)c.S[((long long)s * 4 + cc * 2 + kk) * c.nnode + gn];
+                    const double v = (double)c.S[((long long)s * 4 + cc * 2 + kk) * c.nnode + gn];
+                    dg[kk] -= v;
+                    if (!c.fixed[2 * (c.node0 + m) + kk]) A[(long long)row * n + 2 * m + kk] = v;
                 }
             }
+            for (int kk = 0; kk < 2; ++kk)
+                if (!c.fixed[2 * gn + kk]) A[(long long)row * n + 2 * q + kk] = dg[kk];
         }
     }
+    __syncthreads();
+    // X's diagonal keeps the original diagonal until X = L^-1 is formed
+    for (int k = tid; k < n; k += nt) X[(long long)k * n + k] = A[(long long)k * n + k];
     __syncthreads();
     __shared__ double piv;
     for (int k = 0; k < n; ++k) {
         if (tid == 0) {
-            const double d = A[(long long)k * n + k];
-            piv = d > 0.0 ? sqrt(d) : 1.0;
+            const double d = A[(long long)k * n + k], d0 = X[(long long)k * n + k];
+            piv = d > 1e-6 * d0 ? sqrt(d) : (d0 > 0.0 ? sqrt(1e-6 * d0) : 1.0);
             A[(long long)k * n + k] = piv;
         }
         __syncthreads();
@@ -513,6 +548,7 @@ void bmg_create(to_batch* b) {
             V.w = b->w0 = mg_alloc<float>(b, 2 * nd);
         } else {
             V.Kel = mg_alloc<float>(b, V.nel * 64);
+            V.touched = mg_alloc<uint8_t>(b, V.nel);
             V.S = mg_alloc<float>(b, 36 * nd);
             V.R = mg_alloc<float>(b, 4 * nd);
             V.dinv = mg_alloc<float>(b, 2 * nd);
@@ -538,6 +574,7 @@ void bmg_create(to_batch* b) {
         C.node0 = Li.node0;
         C.a0 = pool;
         C.S = mg->lev[c].S;
+        C.R = mg->lev[c].R;
         C.fixed = mg->lev[c].fixed;
         C.rhs = mg->lev[c].r;
         C.z = mg->lev[c].t;  // the buffer that holds every level's result after the up-sweep
@@ -614,12 +651,12 @@ void bmg_setup(to_batch* b, cudaStream_t st) {
         const int blocks = div_up(V.nel, 8);
         if (l == 1)
             kbm_galerkin<true><<<blocks, 256, 0, st>>>(V.dL, V.dstart, b->count, V.nel, Fv.dL, b->E32, b->fixed,
-                                                       b->ke32, mg->Cj, nullptr, V.Kel);
+                                                       b->ke32, mg->Cj, nullptr, V.Kel, nullptr, V.touched);
         else
             kbm_galerkin<false><<<blocks, 256, 0, st>>>(V.dL, V.dstart, b->count, V.nel, Fv.dL, nullptr, nullptr,
-                                                        b->ke32, nullptr, Fv.Kel, V.Kel);
+                                                        b->ke32, nullptr, Fv.Kel, V.Kel, Fv.touched, V.touched);
         TOPO_CHECK_LAUNCH();
-        kbm_stencil<<<V.ntiles, th, 0, st>>>(level_k(b, l), V.Kel, V.S, V.R, V.dinv, V.fixed, V.nnode);
+        kbm_stencil<<<V.ntiles, th, 0, st>>>(level_k(b, l), V.Kel, V.touched, V.S, V.R, V.dinv, V.fixed, V.nnode);
         TOPO_CHECK_LAUNCH();
     }
     kbm_dense_factor<<<b->count, 256, 0, st>>>(mg->dC, mg->Aw, mg->Ainv);

@@ -188,18 +188,24 @@ __device__ __forceinline__ float pn_weight(int j, int b, int B) {
 // FROM_FINE: K_j = M_j (E_j Ke) M_j with M_j zeroing fine Dirichlet DOFs. When
 // no fine DOF of the coarse element is fixed this is sum_j E_j C_j with the
 // constant C_j = P_j^T Ke P_j (Cj, precomputed), 16x fewer multiply-adds.
+// touched_c[ec] = 1 if a fine Dirichlet DOF lies under the coarse element
+// (FROM_FINE: among its 3^dim fine nodes; else: under one of its children,
+// touched_f). An untouched element matrix annihilates the rigid translations
+// exactly: K_j does, and the interpolation P_j maps a coarse translation to the
+// same fine translation.
 template <typename T, int DIM, bool FROM_FINE>
 __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __restrict__ Ef,
                                                   const double* __restrict__ Ke, const T* __restrict__ Cj,
                                                   const T* __restrict__ Kf, const uint8_t* __restrict__ fixed_f,
-                                                  T* __restrict__ Kc) {
+                                                  const uint8_t* __restrict__ touched_f, T* __restrict__ Kc,
+                                                  uint8_t* __restrict__ touched_c) {
     constexpr int NN = DIM == 3 ? 8 : 4, D = DIM * NN, DD = D * D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Ks = (T*)smem_raw;  // [NN children][D*D]
     T* Ts = Ks + NN * DD;  // [NN children][NN a][NN B][DIM][DIM]
     __shared__ T pw[NN * NN * NN];  // pn weights [j][b][B]
     __shared__ T Ej[NN];
-    __shared__ int any_fixed;
+    __shared__ int any_fixed, has_fixed;
     const long long ec = blockIdx.x;
     const int ey = (int)(ec % dc.nely);
     const long long t0 = ec / dc.nely;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __r
     // children beyond an odd fine grid (ceil coarsening) contribute nothing
     const bool all_inside = 2 * ex + 1 < df.nelx && 2 * ey + 1 < df.nely && (DIM == 2 || 2 * ez + 1 < df.nelz);
     if (FROM_FINE) {
-        if (threadIdx.x == 0) any_fixed = all_inside ? 0 : 1;  // partial coarse elements take the general path
+        if (threadIdx.x == 0) has_fixed = 0;
         if (threadIdx.x < NN) {
             const int j = threadIdx.x;
             const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j)), ezf = DIM == 3 ? 2 * ez + lnz(j) : 0;
@@ -225,7 +231,12 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __r
             const int fy = 2 * ey + oy, fz = DIM == 3 ? 2 * ez + oz : 0, fx = 2 * ex + ox;
             if (fy >= df.nny || fz >= df.nnz || fx >= df.nnx) continue;
             const long long nf = fy + (long long)df.nny * (fz + (long long)df.nnz * fx);
-            if (fixed_f[DIM * nf + c]) any_fixed = 1;
+            if (fixed_f[DIM * nf + c]) has_fixed = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            touched_c[ec] = (uint8_t)has_fixed;
+            any_fixed = has_fixed || !all_inside;  // partial coarse elements take the general path
         }
         __syncthreads();
         if (!any_fixed) {
@@ -237,6 +248,14 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims dc, Dims df, const T* __r
             }
             return;
         }
+    } else if (threadIdx.x == 0) {
+        int tch = 0;
+        for (int j = 0; j < NN; ++j) {
+            const int exf = 2 * ex + lnx(j), eyf = 2 * ey + (1 - lny(j)), ezf = DIM == 3 ? 2 * ez + lnz(j) : 0;
+            if (exf < df.nelx && eyf < df.nely && ezf < df.nelz)
+                tch |= touched_f[eyf + (long long)df.nely * (ezf + (long long)df.nelz * exf)];
+        }
+        touched_c[ec] = (uint8_t)tch;
     }
     for (int idx = threadIdx.x; idx < NN * DD; idx += blockDim.x) {
         const int j = idx / DD, rem = idx % DD, row = rem / D, col = rem % D;
@@ -304,10 +323,33 @@ __global__ void k_elem_from_E(Dims d, const T* __restrict__ E, const double* __r
 template <int DIM>
 __host__ __device__ constexpr int n_stencil() { return DIM == 3 ? 27 : 9; }
 
+// Whether a coarse node's row sums can be nonzero: one of its (up to 2^dim)
+// elements is touched by a fine Dirichlet DOF (touched == nullptr: all are).
+template <int DIM>
+__device__ __forceinline__ bool node_touched(const Dims& d, const uint8_t* __restrict__ touched, int ix, int iy,
+                                             int iz) {
+    if (!touched) return true;
+    bool t = false;
+#pragma unroll
+    for (int o = 0; o < (DIM == 3 ? 8 : 4); ++o) {
+        const int ex = ix - 1 + (DIM == 3 ? (o >> 2) & 1 : (o >> 1) & 1), ey = iy - 1 + (o & 1);
+        const int ez = DIM == 3 ? iz - 1 + ((o >> 1) & 1) : 0;
+        if (ex < 0 || ex >= d.nelx || ey < 0 || ey >= d.nely || ez < 0 || ez >= d.nelz) continue;
+        t |= touched[ey + (long long)d.nely * (ez + (long long)d.nelz * ex)] != 0;
+    }
+    return t;
+}
+
 // Node stencil S[n][s] = sum over the elements containing n and n + s of the
-// element-matrix block (n, n + s); R[n] = sum_s S[n][s]. SoA layout.
+// element-matrix block (n, n + s); R[n] = sum_s S[n][s], the operator applied
+// to the unit translations. SoA layout. At a node none of whose elements is
+// touched R is exactly 0 and is stored so: summed in the level's precision it
+// would instead hold the rounding of the cancelling blocks, which in the
+// relative form of the operator (R_n u_n) acts on absolute displacements and
+// perturbs the smooth modes the coarse correction exists for.
 template <typename T, int DIM>
-__global__ void k_stencil_build(Dims d, const T* __restrict__ Kel, T* __restrict__ S, T* __restrict__ R) {
+__global__ void k_stencil_build(Dims d, const T* __restrict__ Kel, const uint8_t* __restrict__ touched,
+                                T* __restrict__ S, T* __restrict__ R) {
     constexpr int NS = n_stencil<DIM>(), D = DIM == 3 ? 24 : 8, DD = D * D, Q = DIM * DIM;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.nnodes) return;
@@ -349,8 +391,9 @@ __global__ void k_stencil_build(Dims d, const T* __restrict__ Kel, T* __restrict
             rs[q] += blk[q];
         }
     }
+    const bool tch = node_touched<DIM>(d, touched, ix, iy, iz);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) R[(long long)q * d.nnodes + n] = rs[q];
+    for (int q = 0; q < Q; ++q) R[(long long)q * d.nnodes + n] = tch ? rs[q] : T(0);
 }
 
 // 3D stencils with one thread per (node, stencil block): block (SB_NODES, 27),
@@ -364,6 +407,7 @@ struct StencilNodes {
 
 template <typename T>
 __global__ void __launch_bounds__(27 * StencilNodes<T>::v) k_stencil_build3s(Dims d, const T* __restrict__ Kel,
+                                                                          const uint8_t* __restrict__ touched,
                                                                           T* __restrict__ S, T* __restrict__ R) {
     constexpr int NB = StencilNodes<T>::v, D = 24, DD = D * D, Q = 9;
     __shared__ T part[27][NB][Q];
@@ -405,7 +449,10 @@ __global__ void __launch_bounds__(27 * StencilNodes<T>::v) k_stencil_build3s(Dim
     if (s < Q && valid) {
         T rs = T(0);
         for (int k = 0; k < 27; ++k) rs += part[k][tx][s];
-        R[(long long)s * d.nnodes + n] = rs;
+        const int iy = (int)(n % d.nny);
+        const long long t = n / d.nny;
+        R[(long long)s * d.nnodes + n] =
+            node_touched<3>(d, touched, (int)(t / d.nnz), iy, (int)(t % d.nnz)) ? rs : T(0);
     }
 }
 
@@ -894,8 +941,16 @@ __global__ void k_jacobi_first(long long n, const T* __restrict__ dinv, const T*
 
 // ------------------------------------------------------- coarsest level
 
+// The coarsest operator as a dense FP64 matrix: the off-diagonal blocks are the
+// stencil's, the diagonal block of node n is R_n - sum_{m != n} S_nm, i.e. the
+// operator of the relative form k_stencil_op applies (exact for the rigid
+// translations however S was rounded), summed in FP64. Fixed DOFs get
+// identity rows and columns. A (and A32) arrive zeroed: only the nonzeros are
+// written.
 template <typename T, int DIM>
-__global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const uint8_t* __restrict__ fixed, T* __restrict__ A) {
+__global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const T* __restrict__ R,
+                                 const uint8_t* __restrict__ fixed, double* __restrict__ A,
+                                 float* __restrict__ A32) {
     constexpr int NS = n_stencil<DIM>(), Q = DIM * DIM;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.nnodes) return;
@@ -906,26 +961,52 @@ __global__ void k_dense_assemble(Dims d, const T* __restrict__ S, const uint8_t*
     const int ix = (int)(t / d.nnz);
     for (int c = 0; c < DIM; ++c) {
         const long long i = DIM * n + c;
-        T* row = A + i * nc;
-        for (long long j = 0; j < nc; ++j) row[j] = T(0);
+        double* row = A + i * nc;
+        float* row32 = A32 ? A32 + i * nc : nullptr;
         if (fixed[i]) {
-            row[i] = T(1);
+            row[i] = 1.0;
+            if (row32) row32[i] = 1.f;
             continue;
         }
+        double dg[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) dg[k] = (double)R[(long long)(c * DIM + k) * d.nnodes + n];
         for (int s = 0; s < NS; ++s) {
+            if (s == NS / 2) continue;
             const int dx = DIM == 3 ? s / 9 - 1 : s / 3 - 1;
             const int dz = DIM == 3 ? (s / 3) % 3 - 1 : 0;
             const int dy = s % 3 - 1;
             const int mx = ix + dx, my = iy + dy, mz = iz + dz;
             if (mx < 0 || mx >= d.nnx || my < 0 || my >= d.nny || mz < 0 || mz >= d.nnz) continue;
             const long long m = my + (long long)d.nny * (mz + (long long)d.nnz * mx);
-            for (int k = 0; k < DIM; ++k)
-                if (!fixed[DIM * m + k]) row[DIM * m + k] = S[((long long)s * Q + c * DIM + k) * d.nnodes + n];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const double v = (double)S[((long long)s * Q + c * DIM + k) * d.nnodes + n];
+                dg[k] -= v;
+                if (!fixed[DIM * m + k]) {
+                    row[DIM * m + k] = v;
+                    if (row32) row32[DIM * m + k] = (float)v;
+                }
+            }
         }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            if (!fixed[DIM * n + k]) {
+                row[DIM * n + k] = dg[k];
+                if (row32) row32[DIM * n + k] = (float)dg[k];
+            }
     }
 }
 
-// Coarsest-level dense inverse, in the solve's precision T, in four kernels:
+// Coarsest-level dense inverse in four kernels (below). The FP64 solve factors in
+// FP64. The FP32 solve factors in FP32, and again in FP64 only where the FP32
+// factorization met a pivot below 1e-4 of its original diagonal (four of FP32's
+// seven digits cancelled): the coarsest operator of a weakly supported or
+// high-contrast design can be far too ill-conditioned for FP32, while FP64 runs
+// at a small fraction of the FP32 rate on this part. The choice is made on the
+// device: every kernel takes a gate (the FP32 factorization's flag) and the
+// branch it belongs to, and returns at once on the other branch. The inverse is
+// stored in the solve's precision T.
 //  1. blocked right-looking Cholesky A = L L^T by one CTA: the NB x NB diagonal
 //     block is factored in shared memory by the whole CTA (one thread per
 //     element, three barriers per column), the column panel below it is solved
@@ -941,13 +1022,19 @@ struct CholNB {
     static constexpr int v = sizeof(T) == 8 ? 16 : 32;
 };
 
+// True when the kernel belongs to the branch the gate selects (no gate: always).
+__device__ __forceinline__ bool gate_open(const int* gate, int want) { return !gate || ((*gate != 0) == (want != 0)); }
+
+// status: set to 1 if a pivot fell to flag_ratio of its original diagonal or below.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, int* status) {
+__global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, int* status, T flag_ratio,
+                                                       const int* gate, int want) {
     constexpr int NB = CholNB<T>::v, LD = NB + 1;
     extern __shared__ __align__(16) unsigned char chol_smem[];
     T* Dg = (T*)chol_smem;  // NB x LD diagonal block
     T* Pn = Dg + NB * LD;   // up to n x LD panel
     __shared__ T rdiag[NB];  // reciprocals of the factored diagonal
+    if (!gate_open(gate, want)) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) *status = 0;
     for (int k = tid; k < n; k += nt) diag0[k] = A[(long long)k * n + k];
@@ -964,10 +1051,8 @@ __global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, in
             if (tid == 0) {
                 T p = Dg[j * LD + j];
                 const T fl = T(1e-6) * diag0[k0 + j];
-                if (!(p > fl)) {
-                    *status = 1;
-                    p = fl > T(0) ? fl : T(1);
-                }
+                if (!(p > flag_ratio * diag0[k0 + j])) *status = 1;
+                if (!(p > fl)) p = fl > T(0) ? fl : T(1);
                 Dg[j * LD + j] = sqrt(p);
             }
             __syncthreads();
@@ -1049,8 +1134,9 @@ __global__ void __launch_bounds__(1024) k_chol_blocked(int n, T* A, T* diag0, in
 // Inverse of diagonal block b of the lower-triangular L: one CTA per block,
 // thread c solves column c.
 template <typename T>
-__global__ void k_chol_diag_inv(int n, const T* __restrict__ L, T* __restrict__ Dinv) {
+__global__ void k_chol_diag_inv(int n, const T* __restrict__ L, T* __restrict__ Dinv, const int* gate, int want) {
     constexpr int NB = CholNB<T>::v;
+    if (!gate_open(gate, want)) return;
     const int b = blockIdx.x, k0 = b * NB, kw = min(NB, n - k0), c = threadIdx.x;
     if (c >= NB) return;
     T* out = Dinv + (long long)b * NB * NB;
@@ -1071,8 +1157,9 @@ __global__ void k_chol_diag_inv(int n, const T* __restrict__ L, T* __restrict__ 
 // Block column jb of W = L^{-1}: W_jj = inv(L_jj); W_ij = -inv(L_ii) sum_{k=j}^{i-1} L_ik W_kj.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_chol_trinv(int n, const T* __restrict__ L, const T* __restrict__ Dinv,
-                                                     T* __restrict__ W) {
+                                                     T* __restrict__ W, const int* gate, int want) {
     constexpr int NB = CholNB<T>::v, LD = NB + 1;
+    if (!gate_open(gate, want)) return;
     extern __shared__ __align__(16) unsigned char trinv_smem[];
     const int nblk = (n + NB - 1) / NB, jb = blockIdx.x;
     T* Wc = (T*)trinv_smem;        // [nblk][NB][LD] blocks of this column
@@ -1109,15 +1196,39 @@ __global__ void __launch_bounds__(1024) k_chol_trinv(int n, const T* __restrict_
     }
 }
 
-// A^{-1} = W^T W (W = L^{-1} lower triangular); fixed rows and columns zero.
-template <typename T>
-__global__ void k_chol_wtw(int n, const T* __restrict__ W, const uint8_t* __restrict__ fixed, T* __restrict__ Ainv) {
+// A^{-1} = W^T W (W = L^{-1} lower triangular, type TW), stored in T; fixed
+// rows and columns zero.
+template <typename TW, typename T>
+__global__ void k_chol_wtw(int n, const TW* __restrict__ W, const uint8_t* __restrict__ fixed,
+                           T* __restrict__ Ainv, const int* gate, int want) {
+    if (!gate_open(gate, want)) return;
     const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    T s = T(0);
+    TW s = TW(0);
     if (!fixed[i] && !fixed[j])
         for (int k = max(i, j); k < n; ++k) s += W[(long long)k * n + i] * W[(long long)k * n + j];
-    Ainv[(long long)i * n + j] = s;
+    Ainv[(long long)i * n + j] = (T)s;
+}
+
+// One factorization branch: Cholesky of A (type TF), diagonal-block inverses,
+// W = L^{-1} and Ainv = W^T W. flag: the Cholesky's status word.
+template <typename TF, typename T>
+static void chol_inverse(int nc, TF* A, TF* work, TF* dblk, int* flag, TF flag_ratio, const uint8_t* fixed,
+                         T* Ainv, const int* gate, int want, cudaStream_t st) {
+    constexpr int NB = CholNB<TF>::v;
+    const int nblk = (nc + NB - 1) / NB;
+    const int smem_chol = (NB * (NB + 1) + nc * (NB + 1)) * (int)sizeof(TF);
+    const int smem_trinv = (nblk * NB * (NB + 1) + NB * (NB + 1)) * (int)sizeof(TF);
+    TOPO_CUDA(cudaFuncSetAttribute(k_chol_blocked<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
+    TOPO_CUDA(cudaFuncSetAttribute(k_chol_trinv<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trinv));
+    k_chol_blocked<TF><<<1, 1024, smem_chol, st>>>(nc, A, work, flag, flag_ratio, gate, want);
+    TOPO_CHECK_LAUNCH();
+    k_chol_diag_inv<TF><<<nblk, 32, 0, st>>>(nc, A, dblk, gate, want);
+    TOPO_CHECK_LAUNCH();
+    k_chol_trinv<TF><<<nblk, NB * NB, smem_trinv, st>>>(nc, A, dblk, work, gate, want);
+    TOPO_CHECK_LAUNCH();
+    k_chol_wtw<TF, T><<<dim3(div_up(nc, 128), nc), 128, 0, st>>>(nc, work, fixed, Ainv, gate, want);
+    TOPO_CHECK_LAUNCH();
 }
 
 template <typename T>
@@ -1186,15 +1297,23 @@ MG<T>* mg_create(to_grid* g, int max_levels, int nu, double omega) {
                 L.Kel = mg_alloc<T>(mg, L.d.nel * D * D * sizeof(T));
                 L.S = mg_alloc<T>(mg, (size_t)NS * dim * dim * L.d.nnodes * sizeof(T));
                 L.R = mg_alloc<T>(mg, (size_t)dim * dim * L.d.nnodes * sizeof(T));
+                if (l > 0) L.touched = mg_alloc<uint8_t>(mg, L.d.nel);
             }
         }
         const Dims& dc = mg->lev.back().d;
         if (dc.ndof <= DENSE_MAX) {
             mg->nc = (int)dc.ndof;
-            mg->A = mg_alloc<T>(mg, (size_t)mg->nc * mg->nc * sizeof(T));
-            mg->A_work = mg_alloc<T>(mg, (size_t)mg->nc * mg->nc * sizeof(T));
+            mg->A = mg_alloc<double>(mg, (size_t)mg->nc * mg->nc * sizeof(double));
+            mg->A_work = mg_alloc<double>(mg, (size_t)mg->nc * mg->nc * sizeof(double));
+            mg->Dblk = mg_alloc<double>(mg, (size_t)(mg->nc + CholNB<double>::v) * CholNB<double>::v * sizeof(double));
+            if (sizeof(T) == 4) {
+                mg->A32 = mg_alloc<float>(mg, (size_t)mg->nc * mg->nc * sizeof(float));
+                mg->A32_work = mg_alloc<float>(mg, (size_t)mg->nc * mg->nc * sizeof(float));
+                mg->Dblk32 = mg_alloc<float>(mg, (size_t)(mg->nc + CholNB<float>::v) * CholNB<float>::v * sizeof(float));
+            }
             mg->Ainv = mg_alloc<T>(mg, (size_t)mg->nc * mg->nc * sizeof(T));
-            mg->status = mg_alloc<int>(mg, sizeof(int));
+            mg->status = mg_alloc<int>(mg, 2 * sizeof(int));
+            TOPO_CUDA(cudaMemset(mg->status, 0, 2 * sizeof(int)));
         }
         if (mg->nlev > 1) {
             // C_j = P_j^T Ke P_j for the children j of a coarse element (level-1 fast path)
@@ -1266,17 +1385,19 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
             k_elem_from_E<T, DIM><<<div_up(L.d.nel * D * D, 256), 256, 0, st>>>(L.d, E, g->Ke_dev, L.Kel);
         } else if (l == 1) {
             k_galerkin<T, DIM, true><<<(unsigned)L.d.nel, 256, smem, st>>>(L.d, mg->lev[0].d, E, g->Ke_dev, mg->Cj,
-                                                                       nullptr, g->fixed, L.Kel);
+                                                                       nullptr, g->fixed, nullptr, L.Kel,
+                                                                       L.touched);
         } else {
-            k_galerkin<T, DIM, false><<<(unsigned)L.d.nel, 256, smem, st>>>(L.d, mg->lev[l - 1].d, nullptr, nullptr,
-                                                                        nullptr, mg->lev[l - 1].Kel, nullptr, L.Kel);
+            k_galerkin<T, DIM, false><<<(unsigned)L.d.nel, 256, smem, st>>>(
+                L.d, mg->lev[l - 1].d, nullptr, nullptr, nullptr, mg->lev[l - 1].Kel, nullptr,
+                mg->lev[l - 1].touched, L.Kel, L.touched);
         }
         TOPO_CHECK_LAUNCH();
         if (DIM == 3) {
             constexpr int NB = StencilNodes<T>::v;
-            k_stencil_build3s<T><<<div_up(L.d.nnodes, NB), dim3(NB, 27), 0, st>>>(L.d, L.Kel, L.S, L.R);
+            k_stencil_build3s<T><<<div_up(L.d.nnodes, NB), dim3(NB, 27), 0, st>>>(L.d, L.Kel, L.touched, L.S, L.R);
         } else {
-            k_stencil_build<T, DIM><<<div_up(L.d.nnodes, 128), 128, 0, st>>>(L.d, L.Kel, L.S, L.R);
+            k_stencil_build<T, DIM><<<div_up(L.d.nnodes, 128), 128, 0, st>>>(L.d, L.Kel, L.touched, L.S, L.R);
         }
         TOPO_CHECK_LAUNCH();
         if (l > 0) {
@@ -1296,24 +1417,22 @@ static void setup_dim(to_grid* g, MG<T>* mg, const T* E, cudaStream_t st) {
         TOPO_CUDA(cudaEventRecord(mg->fork, st));
         TOPO_CUDA(cudaStreamWaitEvent(mg->side, mg->fork, 0));
         st = mg->side;
-        k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.fixed, mg->A);
+        const size_t nn2 = (size_t)mg->nc * mg->nc;
+        TOPO_CUDA(cudaMemsetAsync(mg->A, 0, nn2 * sizeof(double), st));
+        if (mg->A32) TOPO_CUDA(cudaMemsetAsync(mg->A32, 0, nn2 * sizeof(float), st));
+        k_dense_assemble<T, DIM><<<div_up(L.d.nnodes, 64), 64, 0, st>>>(L.d, L.S, L.R, L.fixed, mg->A, mg->A32);
         TOPO_CHECK_LAUNCH();
-        // A_work holds the original diagonal during the factorization, then W = L^{-1};
-        // Ainv holds the diagonal-block inverses until the final product overwrites it
-        constexpr int NB = CholNB<T>::v;
-        const int nc = mg->nc, nblk = (nc + NB - 1) / NB;
-        const int smem_chol = (NB * (NB + 1) + nc * (NB + 1)) * (int)sizeof(T);
-        const int smem_trinv = (nblk * NB * (NB + 1) + NB * (NB + 1)) * (int)sizeof(T);
-        TOPO_CUDA(cudaFuncSetAttribute(k_chol_blocked<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
-        TOPO_CUDA(cudaFuncSetAttribute(k_chol_trinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trinv));
-        k_chol_blocked<T><<<1, 1024, smem_chol, st>>>(nc, mg->A, mg->A_work, mg->status);
-        TOPO_CHECK_LAUNCH();
-        k_chol_diag_inv<T><<<nblk, 32, 0, st>>>(nc, mg->A, mg->Ainv);
-        TOPO_CHECK_LAUNCH();
-        k_chol_trinv<T><<<nblk, NB * NB, smem_trinv, st>>>(nc, mg->A, mg->Ainv, mg->A_work);
-        TOPO_CHECK_LAUNCH();
-        k_chol_wtw<T><<<dim3(div_up(nc, 128), nc), 128, 0, st>>>(nc, mg->A_work, L.fixed, mg->Ainv);
-        TOPO_CHECK_LAUNCH();
+        // work holds the original diagonal during a factorization, then W = L^{-1};
+        // dblk the inverses of L's diagonal blocks
+        if (mg->A32) {
+            chol_inverse<float, T>(mg->nc, mg->A32, mg->A32_work, mg->Dblk32, mg->status, 1e-4f, L.fixed,
+                                   mg->Ainv, nullptr, 1, st);
+            chol_inverse<double, T>(mg->nc, mg->A, mg->A_work, mg->Dblk, mg->status + 1, 1e-6, L.fixed, mg->Ainv,
+                                    mg->status, 1, st);
+        } else {
+            chol_inverse<double, T>(mg->nc, mg->A, mg->A_work, mg->Dblk, mg->status + 1, 1e-6, L.fixed, mg->Ainv,
+                                    nullptr, 1, st);
+        }
         TOPO_CUDA(cudaEventRecord(mg->ready, st));
         mg->pending = true;
     }

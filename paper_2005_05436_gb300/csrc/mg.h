@@ -7,8 +7,8 @@
 // trilinear (bilinear) prolongation P masked at the fine Dirichlet DOFs, formed
 // element by element (Kc = sum over the 8 (4) children of P_j^T K_j P_j, which
 // equals P^T K P exactly) and stored as a node stencil for application. The
-// coarsest level is solved with a dense inverse (computed in the solve's precision) when small
-// enough, else smoothed. Smoother: damped Jacobi, nu pre and nu post sweeps, so
+// coarsest level is solved with a dense inverse (factored in FP64, stored in the solve's
+// precision) when small enough, else smoothed. Smoother: damped Jacobi, nu pre and nu post sweeps, so
 // the V-cycle is a symmetric positive definite operator usable inside CG.
 #pragma once
 
@@ -26,6 +26,7 @@ struct MGLevel {
     T* S = nullptr;         // stencil, SoA [NS * dim * dim][nnodes] (coarse levels)
     T* R = nullptr;         // row sums of the stencil blocks [dim * dim][nnodes] (coarse levels)
     T* Kel = nullptr;       // element matrices [nel][D * D] (coarse levels)
+    uint8_t* touched = nullptr;  // [nel] (coarse levels): a fine Dirichlet DOF lies under the element
     T* dinv = nullptr;      // Jacobi inverse diagonal [ndof]
     uint8_t* fixed = nullptr;  // [ndof]; level 0: the problem's; coarse: zero-diagonal DOFs
     T *r = nullptr, *z = nullptr, *t = nullptr, *w = nullptr;  // [ndof] work vectors
@@ -40,11 +41,16 @@ struct MG {
     T omega_c = T(0.6);     // and on the coarser ones
     int nc = 0;             // coarsest DOFs (dense inverse) or 0 (smoothing only)
     std::vector<MGLevel<T>> lev;
-    T* A = nullptr;         // coarsest dense matrix and its Cholesky factor [nc * nc]
-    T* Ainv = nullptr;      // its inverse [nc * nc]
-    T* A_work = nullptr;    // column workspace of the inverse [nc * nc]
+    double* A = nullptr;    // coarsest dense matrix and its Cholesky factor [nc * nc], FP64
+    T* Ainv = nullptr;      // its inverse [nc * nc], in the solve's precision
+    double* A_work = nullptr;  // column workspace of the inverse [nc * nc]
+    double* Dblk = nullptr;    // inverses of the factor's diagonal blocks
+    // FP32 hierarchy: the same matrix factored in FP32 first (the FP64 branch runs
+    // only where that factorization lost four digits at a pivot)
+    float *A32 = nullptr, *A32_work = nullptr, *Dblk32 = nullptr;
     T* Cj = nullptr;        // P_j^T Ke P_j of the 2^dim children of a coarse element
-    int* status = nullptr;  // device: nonzero if the coarse Cholesky met a non-positive pivot
+    int* status = nullptr;  // device [2]: the FP32 factorization lost four digits at a pivot (FP64
+                            // branch taken); the FP64 factorization floored a pivot
     const T* E = nullptr;   // fine modulus of the current set-up
     int coarse_every = 1;   // rebuild the coarsest inverse at every k-th set-up
     long long setups = 0;

@@ -96,8 +96,15 @@ __global__ void __launch_bounds__(KNT) k_gpcg_rz(long long n, const T* __restric
 // x += alpha p; r -= alpha Ap; rr; iteration count and the stopping tests.
 // With dinv0 (multigrid): also the V-cycle's first fine-level iterate
 // z0 = omega dinv0 r (the k_jacobi_first of level 0, fused).
+// The iterate x is FP64 in either precision. Rounding x to FP32 at every
+// update would add an error of about eps_32 |x| per DOF that the recursion
+// for r never sees; its image under K, about eps_32 || |K| |x| ||, is then
+// a floor for the true residual far above the FP32 residual recursion's own
+// (it grows with the size of the displacements, i.e. with the grid and the
+// softness of the design). Kept in FP64, x carries exactly the steps
+// alpha p whose K-images the recursion subtracted.
 template <typename T>
-__global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x, T* __restrict__ r,
+__global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, double* __restrict__ x, T* __restrict__ r,
                                                  const T* __restrict__ p, const T* __restrict__ Ap, PcgScalars* s,
                                                  double* partials, unsigned* counter, const T* __restrict__ dinv0,
                                                  T* __restrict__ z0, T omega) {
@@ -111,7 +118,8 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
     // four strided elements per trip with every load issued before the first
     // use, so that a thread waits for memory once rather than four times
     for (; i + 3 * stride < n; i += 4 * stride) {
-        T xv[4], pv[4], rv[4], av[4], dv[4];
+        double xv[4];
+        T pv[4], rv[4], av[4], dv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const long long j = i + k * stride;
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const long long j = i + k * stride;
-            x[j] = xv[k] + alpha * pv[k];
+            x[j] = xv[k] + (double)alpha * (double)pv[k];
             const T ri = rv[k] - alpha * av[k];
             r[j] = ri;
             if (dinv0) z0[j] = omega * dv[k] * ri;
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(KNT) k_gpcg_xr(long long n, T* __restrict__ x,
     }
     if (dn) return;
     for (; i < n; i += stride) {
-        x[i] += alpha * p[i];
+        x[i] += (double)alpha * (double)p[i];
         const T ri = r[i] - alpha * Ap[i];
         r[i] = ri;
         if (dinv0) z0[i] = omega * dinv0[i] * ri;
@@ -195,9 +203,9 @@ __global__ void k_pcg_resume(PcgScalars* s, double rtol2, int maxit) {
     s->done = 0;
 }
 
-__global__ void k_refine_update(long long n, double* __restrict__ x64, const float* __restrict__ d32) {
+__global__ void k_refine_update(long long n, double* __restrict__ x64, const double* __restrict__ d) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x64[i] += (double)d32[i];
+    if (i < n) x64[i] += d[i];
 }
 
 template <typename T>
@@ -218,22 +226,22 @@ struct FcgS {
     int has_prev, pad;
 };
 
-__global__ void __launch_bounds__(KNT) k_fcg_beta(long long n, const float* __restrict__ d,
+__global__ void __launch_bounds__(KNT) k_fcg_beta(long long n, const double* __restrict__ d,
                                                   const double* __restrict__ Kp, FcgS* s, double* partials,
                                                   unsigned* counter) {
     if (!s->has_prev) return;  // uniform
     double v[1] = {0.0}, tot[1];
     for (long long i = (long long)blockIdx.x * KNT + threadIdx.x; i < n; i += (long long)gridDim.x * KNT)
-        v[0] += (double)d[i] * Kp[i];
+        v[0] += d[i] * Kp[i];
     if (last_block_totals<KNT, 1>(v, partials, counter, tot) && threadIdx.x == 0)
         s->beta = s->pkp > 0.0 ? -tot[0] / s->pkp : 0.0;
 }
 
-__global__ void k_fcg_dir(long long n, const float* __restrict__ d, double* __restrict__ p, const FcgS* s) {
+__global__ void k_fcg_dir(long long n, const double* __restrict__ d, double* __restrict__ p, const FcgS* s) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double beta = s->has_prev ? s->beta : 0.0;
-    p[i] = (double)d[i] + beta * p[i];
+    p[i] = d[i] + beta * p[i];
 }
 
 __global__ void __launch_bounds__(KNT) k_fcg_alpha(long long n, const double* __restrict__ p,
@@ -273,7 +281,8 @@ __global__ void __launch_bounds__(KNT) k_fcg_update(long long n, double* __restr
 
 template <typename T>
 struct Pcg {
-    T *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *zj = nullptr, *dinv_j = nullptr, *b = nullptr;
+    double* x = nullptr;         // iterate, FP64 in either precision (k_gpcg_xr)
+    T *r = nullptr, *p = nullptr, *Ap = nullptr, *zj = nullptr, *dinv_j = nullptr, *b = nullptr;
     T* E = nullptr;              // modulus in T
     MG<T>* mg = nullptr;         // nullptr: Jacobi
     PcgScalars* s = nullptr;     // device
@@ -316,7 +325,7 @@ static T* salloc(Solver* s, size_t count) {
 template <typename T>
 static void pcg_alloc(to_grid* g, Solver* sv, Pcg<T>& P, bool gmg) {
     const long long n = g->d.ndof;
-    P.x = salloc<T>(sv, n);
+    P.x = salloc<double>(sv, n);
     P.r = salloc<T>(sv, n);
     P.p = salloc<T>(sv, n);
     P.Ap = salloc<T>(sv, n);
@@ -437,11 +446,16 @@ static PcgScalars run_pcg(to_grid* g, Solver* sv, Pcg<T>& P, double rtol, int ma
         TOPO_CUDA(cudaMemcpyAsync(P.s, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
     }
     if (x0_zero) {
-        k_zero<T><<<div_up(n, 256), 256, 0, st>>>(n, P.x);
+        k_zero<double><<<div_up(n, 256), 256, 0, st>>>(n, P.x);
         TOPO_CUDA(cudaMemcpyAsync(P.r, P.b, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
         count_launches(1);
     } else {
-        launch_fine_op<T>(g, 2, P.E, P.x, P.b, nullptr, P.r, T(0), nullptr, nullptr, st);
+        // only the FP64 solve starts from a nonzero x; the FP32 one solves for a correction
+        if constexpr (sizeof(T) == 8) {
+            launch_fine_op<T>(g, 2, P.E, P.x, P.b, nullptr, P.r, T(0), nullptr, nullptr, st);
+        } else {
+            TOPO_REQUIRE(false, "the FP32 PCG starts from x = 0");
+        }
     }
     k_gpcg_init<T><<<kblocks(n), KNT, 0, st>>>(n, P.b, P.r, g->fixed, P.s, g->partials, g->counter);
     TOPO_CHECK_LAUNCH();
@@ -573,6 +587,44 @@ void solver_discard_setup(to_grid* g) {
     if (g->solver) g->solver->setup_done = false;
 }
 
+// The FP64 PCG of a TO_MIXED handle, allocated the first time the mixed solve
+// hands over to it (its iterate and residual are the refinement's x64, r64).
+static void ensure_fp64_pcg(to_grid* g, Solver* sv) {
+    Pcg<double>& P = sv->p64;
+    if (P.b) return;
+    const long long n = g->d.ndof;
+    P.p = salloc<double>(sv, n);
+    P.Ap = salloc<double>(sv, n);
+    P.zj = salloc<double>(sv, n);
+    P.b = salloc<double>(sv, n);
+    P.dinv_j = salloc<double>(sv, n);
+    P.E = g->E;
+    P.s = salloc<PcgScalars>(sv, 1);
+    if (g->p.precond == TO_PC_GMG) {
+        P.mg = mg_create<double>(g, g->p.mg_levels, g->p.mg_nu, g->p.mg_omega);
+        P.mg->coarse_every = g->p.mg_coarse_every;
+        P.mg->nu_fine = g->p.mg_nu_fine;
+    }
+}
+
+// FP64 PCG from x = P.x on P.b: the recursive CG residual can drift below the
+// true one, so the true FP64 residual decides, and the PCG restarts from the
+// current x if needed (restarts counted in *restarts).
+static to_status fp64_pcg(to_grid* g, Solver* sv, bool setup, int& iters, int& restarts, double& rel) {
+    Pcg<double>& P = sv->p64;
+    for (int restart = 0;; ++restart) {
+        const PcgScalars h =
+            run_pcg<double>(g, sv, P, g->p.cg_rtol, g->p.cg_maxit - iters, false, restart == 0 && setup);
+        iters += h.iters;
+        true_residual(g, sv, P.b, P.x, P.r, nullptr);
+        rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
+        if (h.done == 3 || !std::isfinite(rel)) return TO_ENAN;
+        if (rel <= g->p.cg_rtol) return TO_OK;
+        if (h.done == 2 || restart >= 8 || iters >= g->p.cg_maxit) return TO_ENOTCONV;
+        restarts = restart + 1;
+    }
+}
+
 to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* info) {
     Solver* sv = g->solver;
     const Dims& d = g->d;
@@ -584,30 +636,13 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
     sv->t_setup = sv->t_krylov = sv->t_resid = 0.0;
     const bool pre = sv->setup_done;  // the preconditioner is already set up for this modulus
     sv->setup_done = false;
+    bool fallback = false;
     if (g->p.precision == TO_FP64) {
         Pcg<double>& P = sv->p64;
         TOPO_CUDA(cudaMemcpyAsync(P.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, P.x, g->fixed);
         TOPO_CHECK_LAUNCH();
-        // The recursive CG residual can drift below the true one; the true FP64
-        // residual decides, and the PCG restarts from the current x if needed.
-        for (int restart = 0;; ++restart) {
-            const PcgScalars h =
-                run_pcg<double>(g, sv, P, g->p.cg_rtol, g->p.cg_maxit - iters, false, restart == 0 && !pre);
-            iters += h.iters;
-            true_residual(g, sv, P.b, P.x, P.r, nullptr);
-            rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
-            if (h.done == 3 || !std::isfinite(rel)) {
-                status = TO_ENAN;
-                break;
-            }
-            if (rel <= g->p.cg_rtol) break;
-            if (h.done == 2 || restart >= 8 || iters >= g->p.cg_maxit) {
-                status = TO_ENOTCONV;
-                break;
-            }
-            refinements = restart + 1;  // reported as restarts of the FP64 PCG
-        }
+        status = fp64_pcg(g, sv, !pre, iters, refinements, rel);  // restarts reported as refinements
         TOPO_CUDA(cudaMemcpyAsync(U, P.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
         Pcg<float>& P = sv->p32;
@@ -627,6 +662,7 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         TOPO_CUDA(cudaMemsetAsync(sv->fs, 0, sizeof(FcgS), st));
         bool reliable = g->p.refine == TO_REFINE_RELIABLE;
         bool have_dir = false;  // a previous segment left its search direction
+        double per_decade = 0.0;  // PCG iterations per decade of residual drop in the first segment
         for (;;) {
             if (!std::isfinite(rel)) {
                 status = TO_ENAN;
@@ -651,10 +687,12 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
                 // recursion), then U += the FP32 correction in FP64 and the true FP64 residual
                 // replaces the recursive one; the next segment keeps the search direction
                 const double drop = std::max(g->p.inner_rtol, std::min(0.5, 0.3 * g->p.cg_rtol / rel));
-                // a segment that needs more than RELIABLE_SEG_MAX iterations has stalled in FP32
-                const PcgScalars h = run_pcg<float>(
-                    g, sv, P, drop, std::min({g->p.inner_maxit, RELIABLE_SEG_MAX, g->p.cg_maxit - iters}), true,
-                    !prepared, have_dir);
+                const double decades = std::max(std::log10(1.0 / drop), 0.3);
+                // a segment that needs more than RELIABLE_SEG_MAX iterations, or four times the
+                // first segment's rate, has stalled in FP32
+                int cap = std::min({g->p.inner_maxit, RELIABLE_SEG_MAX, g->p.cg_maxit - iters});
+                if (per_decade > 0.0) cap = std::min(cap, 16 + (int)std::ceil(4.0 * per_decade * decades));
+                const PcgScalars h = run_pcg<float>(g, sv, P, drop, cap, true, !prepared, have_dir);
                 prepared = true;
                 iters += h.iters;
                 if (h.done == 3) {
@@ -664,12 +702,19 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
                 k_refine_update<<<div_up(n, 256), 256, 0, st>>>(n, x64, P.x);
                 TOPO_CHECK_LAUNCH();
                 count_launches(1);
+                if (per_decade == 0.0 && h.done == 1 && h.iters > 0) per_decade = h.iters / decades;
                 const double rel_prev = rel;
                 true_residual(g, sv, b, x64, r64, P.b);
                 rel = sv->hres[1] > 0 ? std::sqrt(sv->hres[0] / sv->hres[1]) : 0.0;
                 confirmed = true;
                 ++refinements;
-                have_dir = true;
+                // the next segment keeps the search direction only while the FP32 recursion
+                // tracks the true residual: where the true residual fell far less than the
+                // recursive one (the FP32 operator's accuracy limit), beta = r.z / r.z_old
+                // would scale the old direction up by the mismatch and the resumed iteration
+                // stalls; it then restarts from the true residual instead
+                const double rec = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
+                have_dir = std::isfinite(rel) && rel <= 4.0 * rec * rel_prev;
                 // the FP32 recursion stalled (segment cap) or no longer tracks the FP64
                 // residual: continue with the flexible-CG steps, whose exact FP64 line search
                 // cannot raise the energy
@@ -705,6 +750,23 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
             confirmed = false;
             ++refinements;
         }
+        // The FP32 iteration failed (a non-finite value, or the refinement cap with
+        // iterations left): the design is beyond FP32's reach (a condition number far
+        // above 1 / eps_32, e.g. a load path through near-void elements or a few
+        // clamped nodes). The FP64 PCG finishes the solve, from the refined iterate,
+        // or from the caller's start after a non-finite value.
+        if ((status == TO_ENAN || status == TO_ENOTCONV) && iters < g->p.cg_maxit) {
+            ensure_fp64_pcg(g, sv);
+            Pcg<double>& Q = sv->p64;  // Q.x is x64, Q.r is r64
+            TOPO_CUDA(cudaMemcpyAsync(Q.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            if (status == TO_ENAN) {
+                k_cast_mask<double, double><<<div_up(n, 256), 256, 0, st>>>(n, U, x64, g->fixed);
+                TOPO_CHECK_LAUNCH();
+            }
+            int restarts = 0;
+            status = fp64_pcg(g, sv, true, iters, restarts, rel);
+            fallback = true;
+        }
         TOPO_CUDA(cudaMemcpyAsync(U, x64, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (g->tc_err) {
             int herr = 0;
@@ -720,6 +782,7 @@ to_status solve_state(to_grid* g, const double* b, double* U, to_solve_info* inf
         info->refinements = refinements;
         info->rel_res = rel;
         info->status = (int)status;
+        info->fallback = fallback ? 1 : 0;
         info->t_setup_ms = sv->t_setup;
         info->t_krylov_ms = sv->t_krylov;
         info->t_resid_ms = sv->t_resid;
