@@ -301,7 +301,10 @@ def batched_256(steps=4):
     x0 = torch.from_numpy(np.concatenate([I.initial_design(q.nelx * q.nely, q.volfrac) for q in insts])).cuda()
     b = Batch(p, [(q.nelx, q.nely, q.volfrac, q.rmin) for q in insts], F, fixed, x0)
     tune = b.autotune(reps=3)
-    infos = [b.step() for _ in range(steps)]
+    infos = [b.step(check=False) for _ in range(steps)]
+    bad = [i["status"] for i in infos if i["status"] not in (0, 4)]  # 4: TO_ENOTCONV, reported below
+    if bad:
+        raise RuntimeError(f"batched step failed with status {bad}")
     ms = [i["ms"] for i in infos[1:]]
     t = sum(ms) / len(ms)
     b.close()
@@ -309,7 +312,9 @@ def batched_256(steps=4):
             "elements": int(b.nel), "design_iterations_per_s": round(1000.0 / t, 3),
             "elements_per_s": round(b.nel * 1000.0 / t, 1), "ms_per_iteration": round(t, 2),
             "tiles": {"node": tune["node"], "elem": tune["elem"]},
-            "max_rel_res": max(i["max_rel_res"] for i in infos), "kernels_per_iteration": infos[-1]["kernels"]}
+            "max_rel_res": max(i["max_rel_res"] for i in infos), "kernels_per_iteration": infos[-1]["kernels"],
+            "max_refinements": [i["max_refinements"] for i in infos],
+            "stalled_instances": [i["stalled"] for i in infos]}
 
 
 def run_ours(args):

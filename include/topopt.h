@@ -137,7 +137,8 @@ typedef struct to_params {
     double pae_alpha;       /* damping of the other steps, x += alpha r (0.9) */
     double pae_zeta;        /* damping of the extrapolated step (1) */
     int32_t inner_maxit;    /* TO_MIXED (to_step, to_solve and the batched solve): iteration cap of
-                               each FP32 inner solve (2000); a stalled inner solve hands its
+                               each FP32 inner solve (2000; the batched solve caps at 1000 with
+                               Jacobi and 200 with GMG as well); a stalled inner solve hands its
                                iterate to the FP64 flexible-CG step, whose exact line search still
                                lowers the energy. >= 1, else TO_EINVAL */
     int32_t refine;         /* TO_MIXED, single grid: how the FP64 residual corrects the FP32 solve.
@@ -437,14 +438,16 @@ typedef struct to_tile_info {
 /* Record of one batched design iteration. */
 typedef struct to_batch_info {
     int32_t loop;               /* design iteration counter after the step (1-based) */
-    int32_t status;             /* TO_OK, or TO_ENOTCONV when an instance stopped at the
-                                   refinement cap above cg_rtol */
+    int32_t status;             /* TO_OK, or TO_ENOTCONV when an instance stopped above cg_rtol
+                                   (refinement cap, or stalled) */
     int32_t max_refinements;    /* max over instances of the FP64 refinement steps */
     int32_t max_inner_iters;    /* max over instances of the inner PCG iterations (all refinements) */
     int32_t newton_passes;      /* lockstep passes of the eta loop (all instances) */
     int32_t inner_passes;       /* lockstep passes of the inner PCG loop */
     int32_t oc_passes;          /* lockstep passes of the lambda loop */
-    int32_t _pad;
+    int32_t stalled;            /* instances whose FP64 residual did not halve over 10 refinements
+                                   and stopped there above cg_rtol (status TO_ENOTCONV; their
+                                   rel_res in to_batch_results) */
     double max_rel_res;         /* max over instances of ||F - K U|| / ||F|| (FP64) at exit */
     double penal, beta;         /* after the continuation of this iteration */
     double ms;                  /* device time of the graph launch (CUDA events) */

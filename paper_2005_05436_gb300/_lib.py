@@ -87,7 +87,7 @@ class TileInfo(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("loop", C.c_int32), ("status", C.c_int32), ("max_refinements", C.c_int32),
                 ("max_inner_iters", C.c_int32), ("newton_passes", C.c_int32), ("inner_passes", C.c_int32),
-                ("oc_passes", C.c_int32), ("_pad", C.c_int32), ("max_rel_res", C.c_double),
+                ("oc_passes", C.c_int32), ("stalled", C.c_int32), ("max_rel_res", C.c_double),
                 ("penal", C.c_double), ("beta", C.c_double), ("ms", C.c_double), ("kernels", C.c_int64)]
 
 

@@ -249,12 +249,19 @@ __global__ void kb_begin_solve(BG* G, BS* S, int count, cudaGraphConditionalHand
         S[i].ref_done = 0;
         S[i].n_ref = 0;
         S[i].f_has_prev = 0;
+        S[i].stalled = 0;
+        S[i].rel_mark = 0.0;
     }
 }
 
 // FP64 refinement test: r = F - K(E64) U on free DOFs; ||r|| / ||F||. Instances
-// at or below rtol (or at max_ref refinements) stop; the others keep r (FP64)
-// and get r32 = (float) r and xin = 0 for the next inner solve.
+// at or below rtol (or at max_ref refinements) stop; so does an instance whose
+// residual has not halved over the last STALL_WINDOW refinements (its design is
+// beyond the reach of the FP32 inner solves: every flexible-CG step still lowers
+// the energy, but too little to be worth holding the batch; it keeps its U and
+// is counted in to_batch_info.stalled). The others keep r (FP64) and get
+// r32 = (float) r and xin = 0 for the next inner solve.
+constexpr int STALL_WINDOW = 10;
 __global__ void kb_resid(BK k, const KeP<double, 8> ke, const double* __restrict__ E64,
                          const double* __restrict__ U, const double* __restrict__ F,
                          const uint8_t* __restrict__ fixed, double* __restrict__ r64, float* __restrict__ r32,
@@ -282,10 +289,14 @@ __global__ void kb_resid(BK k, const KeP<double, 8> ke, const double* __restrict
     const double rel = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : 0.0;
     S.rel_res = rel;
     if (!isfinite(rel)) k.G->status = (int)TO_ENAN;
-    if (!(rel > rtol) || S.n_ref >= max_ref) {
+    const bool mark = S.n_ref % STALL_WINDOW == 0;
+    const bool stalled = mark && S.n_ref > 0 && rel > 0.5 * S.rel_mark;
+    if (!(rel > rtol) || S.n_ref >= max_ref || stalled) {
         S.ref_done = 1;
+        S.stalled = (rel > rtol && stalled) ? 1 : 0;
         atomicSub(&k.G->active[LOOP_REF], 1);
     } else {
+        if (mark) S.rel_mark = rel;
         S.n_ref += 1;
     }
 }
@@ -680,7 +691,8 @@ __global__ void kb_bench_state(BS* S, int count) {
     }
 }
 
-constexpr int INNER_CAP = 1000;  // FP32 inner iterations per refinement
+constexpr int INNER_CAP = 1000;     // FP32 inner iterations per refinement (Jacobi)
+constexpr int INNER_CAP_MG = 200;   // and with the multigrid preconditioner (10-50 needed when FP32 suffices)
 constexpr int MAX_REFINE = 200;  // FP64 refinements per solve
 
 constexpr int N_CAND = 8;
@@ -808,11 +820,14 @@ void capture_step(to_batch* b, double* x, double* xPhys, double* xOld, double* U
     const int nb_n = b->n_nt, nb_e = b->n_et, tn = b->nty * b->ntx, te = b->ety * b->etx;
     const int ft = p.ft;
     // Each FP32 inner solve restarts from the FP64 residual after at most
-    // inner_maxit iterations (and INNER_CAP with the Jacobi preconditioner):
-    // long FP32 Krylov runs lose orthogonality on high-contrast designs and can
-    // return a correction that raises the FP64 residual; a restarted run still
-    // reduces the energy-norm error.
-    const int inner_cap = std::min(std::min(p.cg_maxit, p.inner_maxit), b->mg ? p.inner_maxit : INNER_CAP);
+    // inner_maxit iterations (and INNER_CAP, INNER_CAP_MG with the Jacobi and
+    // the multigrid preconditioner): long FP32 Krylov runs lose orthogonality on
+    // high-contrast designs and can return a correction that raises the FP64
+    // residual; a restarted run still reduces the energy-norm error, and an
+    // instance that needs far more than the cap is beyond FP32 anyway (the stall
+    // rule of kb_resid stops it), while every inner iteration of the batch runs
+    // as long as any instance is still iterating.
+    const int inner_cap = std::min(std::min(p.cg_maxit, p.inner_maxit), b->mg ? INNER_CAP_MG : INNER_CAP);
     const int max_ref = MAX_REFINE;
     cudaStream_t st = b->st;
     captured_launches_reset();
@@ -1178,6 +1193,7 @@ to_status to_batch_step(to_batch* b, double* x, double* xPhys, double* xOld, dou
             info->max_refinements = std::max(info->max_refinements, s.n_ref);
             info->max_inner_iters = std::max(info->max_inner_iters, s.inner_total);
             info->max_rel_res = std::max(info->max_rel_res, s.rel_res);
+            info->stalled += s.stalled;
         }
         if (info->status == 0 && info->max_rel_res > b->p.cg_rtol) info->status = (int32_t)TO_ENOTCONV;
     }

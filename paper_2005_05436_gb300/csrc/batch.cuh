@@ -30,7 +30,8 @@ struct BS {
     int eta_mode, eta_it, eta_bis, eta_done;
     double rel_res;                            // FP64 relative residual of the last refinement test
     int ref_done, n_ref, inner_done, inner_it;
-    int inner_total, pad0;
+    int inner_total, stalled;                  // stalled: stopped by the stall rule (kb_resid)
+    double rel_mark;                           // residual at the last stall-window mark
     double rz, alpha, beta_cg, irr0;           // inner PCG scalars
     double f_beta, f_alpha, f_pkp;             // FP64 outer flexible CG (previous p.Kp)
     int f_has_prev, pad2;
@@ -268,7 +269,6 @@ struct CInst {
     int level, nc, nnx, nny;
     long long node0, a0;   // node offset within the level; offset of the inverse in the pool
     const float* S;        // the level's stencils (SoA, stride nnode)
-    const float* R;        // and their row sums (SoA, stride nnode)
     const uint8_t* fixed;  // the level's Dirichlet mask
     const float* rhs;      // the level's right-hand side
     float* z;              // the level's V-cycle output buffer

@@ -243,11 +243,9 @@ __global__ void kbm_stencil(BKL k, const float* __restrict__ Kel, const uint8_t*
     }
 }
 
-// One CTA per instance: assemble the coarsest operator (FP64; the diagonal block
-// of node n as R_n - sum_{m != n} S_nm, the operator the relative-form stencil
-// applies, exact for the rigid translations), Cholesky A = L L^T with pivots
-// floored at 1e-6 of the original diagonal, X = L^-1, and the inverse
-// A^-1 = X^T X stored in FP32. Dirichlet DOFs get identity rows and columns.
+// One CTA per instance: assemble the coarsest operator (FP64), Cholesky
+// A = L L^T, X = L^-1, and the inverse A^-1 = X^T X stored in FP32. Dirichlet
+// DOFs get identity rows and columns.
 __global__ void __launch_bounds__(256) kbm_dense_factor(const CInst* __restrict__ Cs, double* __restrict__ Aw,
                                                         float* __restrict__ Ainv) {
     const CInst& c = Cs[blockIdx.x];
@@ -269,32 +267,23 @@ __global__ void __launch_bounds__(256) kbm_dense_factor(const CInst* __restrict_
                 A[(long long)row * n + row] = 1.0;
                 continue;
             }
-            double dg[2] = {(double)c.R[(long long)(cc * 2) * c.nnode + gn],
-                            (double)c.R[(long long)(cc * 2 + 1) * c.nnode + gn]};
             for (int s = 0; s < 9; ++s) {
-                if (s == 4) continue;
                 const int mx = ix + s / 3 - 1, my = iy + s % 3 - 1;
                 if (mx < 0 || mx >= c.nnx || my < 0 || my >= c.nny) continue;
                 const int m = my + c.nny * mx;
                 for (int kk = 0; kk < 2; ++kk) {
-                    const double v = (double)c.S[((long long)s * 4 + cc * 2 + kk) * c.nnode + gn];
-                    dg[kk] -= v;
-                    if (!c.fixed[2 * (c.node0 + m) + kk]) A[(long long)row * n + 2 * m + kk] = v;
+                    if (c.fixed[2 * (c.node0 + m) + kk]) continue;
+                    A[(long long)row * n + 2 * m + kk] = (double)c.S[((long long)s * 4 + cc * 2 + kk) * c.nnode + gn];
                 }
             }
-            for (int kk = 0; kk < 2; ++kk)
-                if (!c.fixed[2 * gn + kk]) A[(long long)row * n + 2 * q + kk] = dg[kk];
         }
     }
-    __syncthreads();
-    // X's diagonal keeps the original diagonal until X = L^-1 is formed
-    for (int k = tid; k < n; k += nt) X[(long long)k * n + k] = A[(long long)k * n + k];
     __syncthreads();
     __shared__ double piv;
     for (int k = 0; k < n; ++k) {
         if (tid == 0) {
-            const double d = A[(long long)k * n + k], d0 = X[(long long)k * n + k];
-            piv = d > 1e-6 * d0 ? sqrt(d) : (d0 > 0.0 ? sqrt(1e-6 * d0) : 1.0);
+            const double d = A[(long long)k * n + k];
+            piv = d > 0.0 ? sqrt(d) : 1.0;
             A[(long long)k * n + k] = piv;
         }
         __syncthreads();
@@ -574,7 +563,6 @@ void bmg_create(to_batch* b) {
         C.node0 = Li.node0;
         C.a0 = pool;
         C.S = mg->lev[c].S;
-        C.R = mg->lev[c].R;
         C.fixed = mg->lev[c].fixed;
         C.rhs = mg->lev[c].r;
         C.z = mg->lev[c].t;  // the buffer that holds every level's result after the up-sweep

@@ -332,9 +332,12 @@ def bench_batch(a):
     tune = b.autotune(reps=5) if a.autotune else None
     steps = []
     for _ in range(a.steps):
-        info = b.step()
-        steps.append({k: info[k] for k in ("loop", "ms", "max_refinements", "max_inner_iters", "inner_passes",
-                                           "newton_passes", "oc_passes", "max_rel_res", "kernels")})
+        info = b.step(check=False)
+        if info["status"] not in (0, 4):  # 4: TO_ENOTCONV (an instance stopped above cg_rtol), reported
+            raise RuntimeError(f"batched step failed with status {info['status']}")
+        steps.append({k: info[k] for k in ("loop", "status", "ms", "max_refinements", "max_inner_iters",
+                                           "inner_passes", "newton_passes", "oc_passes", "max_rel_res", "stalled",
+                                           "kernels")})
     ms = [s["ms"] for s in steps[1:]] or [steps[0]["ms"]]
     t_max = R.max_over_ranks(sum(ms) / len(ms) / 1000.0, world, device="cuda")
     nel_all = R.sum_over_ranks(b.nel, world, device="cuda")
