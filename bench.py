@@ -69,7 +69,7 @@ def parse_args():
     ap.add_argument("--mg-omega", type=float, default=1.8, help="GMG l1-Jacobi smoother weight")
     ap.add_argument("--mg-omega-coarse", type=float, default=0.0,
                     help="GMG l1-Jacobi weight below the finest level (0: --mg-omega)")
-    ap.add_argument("--inner-rtol", type=float, default=3e-3,
+    ap.add_argument("--inner-rtol", type=float, default=1e-4,
                     help="mixed path: residual drop of each FP32 PCG segment (reliable updates) or inner solve")
     ap.add_argument("--refine", default="reliable", choices=["reliable", "flexible"],
                     help="mixed path: FP32 PCG with FP64 reliable updates, or FP32 solves with FP64 flexible-CG steps")
@@ -267,7 +267,7 @@ def mbb_config2(flush, stream, warmup=3, steps=5):
         for name, prec in (("fp64_gmg", TO_FP64), ("mixed_gmg", TO_MIXED)):
             p = default_params(2, nelx, nely, 0, volfrac=0.3, penal=1.0, rmin=0.03 * nelx, ft=3, eta=0.5, beta=2.0,
                                move=0.2, cg_rtol=1e-8, cg_maxit=100000, precision=prec, precond=TO_PC_GMG, mg_nu=1,
-                               inner_rtol=3e-3, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+                               inner_rtol=1e-4, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
             g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda(), stream=stream)
             d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.3)).cuda())
             for _ in range(warmup):

@@ -198,7 +198,7 @@ def bench_mbb(a):
         res = {}
         for name, prec in (("fp64_gmg", TO_FP64), ("mixed_gmg", TO_MIXED)):
             p = default_params(2, nelx, nely, 0, ft=3, eta=0.5, beta=2.0, move=0.2, cg_rtol=1e-8, cg_maxit=100000,
-                               precision=prec, precond=TO_PC_GMG, mg_nu=1, inner_rtol=3e-3, **kw)
+                               precision=prec, precond=TO_PC_GMG, mg_nu=1, inner_rtol=1e-4, **kw)
             g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
             d = Design(g, torch.from_numpy(I.initial_design(g.nel, p.volfrac)).cuda())
             for _ in range(a.warmup):
@@ -263,7 +263,7 @@ def bench_learned(a):
     F, fixed = I.cantilever_3d(nelx, nely, nelz)
     p = default_params(3, nelx, nely, nelz, volfrac=0.12, penal=3.0, rmin=math.sqrt(3.0), ft=3, beta=2.0,
                        cg_rtol=1e-8, cg_maxit=50000, precision=TO_MIXED, precond=TO_PC_GMG, mg_nu=1,
-                       inner_rtol=3e-3, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
+                       inner_rtol=1e-4, penal_cnt=(1, 3.0, 25, 0.25), beta_cnt=(1, 16.0, 25, 2.0, TO_CNT_MUL))
     g = Grid(p, torch.from_numpy(F).cuda(), torch.from_numpy(fixed).cuda())
     d = Design(g, torch.from_numpy(I.initial_design(g.nel, 0.12)).cuda())
     # the first state solve from U = 0, without and with the network
