@@ -7,6 +7,7 @@
 // tolerance, so the solution does not depend on the network; only the
 // iteration count can. It runs on a stream of its own while the grid stream
 // sets up the preconditioner.
+#include <algorithm>
 #include <cmath>
 
 #include "grid.h"
@@ -169,6 +170,42 @@ __global__ void kw_energy_grad(Dims d, CGrid c, const double* __restrict__ F, co
     for (int q = 0; q < 3; ++q) gy[v * 3 + q] = (float)a[q];
 }
 
+// The sums both combination rules need, in one pass over F, U_prev (Up, zero at
+// fixed DOFs), U_h and their operator products: dots[0] F.Up, [1] F.Uh,
+// [2] Up.KUp, [3] Up.KUh, [4] Uh.KUh, [8] KUp.KUp, [9] KUp.KUh, [10] KUh.KUh,
+// [11] F.KUp, [12] F.KUh and [13] ||F||^2 over the free DOFs (K U is 0 at fixed
+// DOFs, so the sums with it run over the free DOFs). Block partials are summed
+// in block order by the last block (deterministic).
+constexpr int WNT = 256;
+constexpr int WDOTS = 11;
+__global__ void __launch_bounds__(WNT) kw_dots(long long n, const double* __restrict__ F,
+                                               const uint8_t* __restrict__ fixed, const double* __restrict__ Up,
+                                               const double* __restrict__ Uh, const double* __restrict__ KUp,
+                                               const double* __restrict__ KUh, double* dots, double* partials,
+                                               unsigned* counter) {
+    double v[WDOTS] = {}, tot[WDOTS];
+    for (long long i = (long long)blockIdx.x * WNT + threadIdx.x; i < n; i += (long long)gridDim.x * WNT) {
+        const double f = F[i], up = Up[i], uh = Uh[i], kp = KUp[i], kh = KUh[i];
+        const double ff = fixed[i] ? 0.0 : f;
+        v[0] += f * up;
+        v[1] += f * uh;
+        v[2] += up * kp;
+        v[3] += up * kh;
+        v[4] += uh * kh;
+        v[5] += kp * kp;
+        v[6] += kp * kh;
+        v[7] += kh * kh;
+        v[8] += f * kp;
+        v[9] += f * kh;
+        v[10] += ff * ff;
+    }
+    if (last_block_totals<WNT, WDOTS>(v, partials, counter, tot) && threadIdx.x == 0) {
+        constexpr int slot[WDOTS] = {0, 1, 2, 3, 4, 8, 9, 10, 11, 12, 13};
+#pragma unroll
+        for (int k = 0; k < WDOTS; ++k) dots[slot[k]] = tot[k];
+    }
+}
+
 __global__ void kw_combine(long long n, double a, const double* __restrict__ Up, double b,
                            const double* __restrict__ Uh, double* __restrict__ U) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,9 +338,6 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
     kw_crop<<<div_up(d.nnodes, 256), 256, 0, ax>>>(d, w->cg, w->y, g->fixed, w->Uh);
     TOPO_CHECK_LAUNCH();
     launch_mask_copy(d.ndof, U, w->Up, g->fixed, ax);
-    // ||F||^2 over the free DOFs (KUh serves as scratch before its product)
-    launch_mask_copy(d.ndof, g->F, w->KUh, g->fixed, ax);
-    launch_dot(d.ndof, w->KUh, nullptr, w->dots + 13, w->partials, w->counter, ax);
     if (g->p.precision == TO_MIXED) {
         // the products only choose a starting point: the FP32 operator is enough
         launch_modulus<float>(d.nel, xPhys, g->penal, g->p.E0, g->p.Emin, w->E32, ax);
@@ -315,19 +349,16 @@ void learned_warm_start(to_grid* g, const double* xPhys, double* U, double* coef
         launch_apply_K<double>(d, g->ke3, g->ke2, g->wk, g->node_centric, g->E, w->Up, w->KUp, g->fixed,
                                true, ax);
     }
-    launch_dot(d.ndof, g->F, w->Up, w->dots + 0, w->partials, w->counter, ax);
-    launch_dot(d.ndof, g->F, w->Uh, w->dots + 1, w->partials, w->counter, ax);
-    launch_dot(d.ndof, w->Up, w->KUp, w->dots + 2, w->partials, w->counter, ax);
-    launch_dot(d.ndof, w->Up, w->KUh, w->dots + 3, w->partials, w->counter, ax);
-    launch_dot(d.ndof, w->Uh, w->KUh, w->dots + 4, w->partials, w->counter, ax);
+    // the energy rule's Gram matrix and products with F, the residual rule's
+    // (the two residual directions K U), and ||F||^2, in one pass
+    {
+        const long long nb = std::min<long long>({(d.ndof + 4LL * WNT - 1) / (4LL * WNT), 1024LL,
+                                                  g->npartials / WDOTS});
+        kw_dots<<<(unsigned)std::max<long long>(nb, 1), WNT, 0, ax>>>(d.ndof, g->F, g->fixed, w->Up, w->Uh, w->KUp,
+                                                                      w->KUh, w->dots, w->partials, w->counter);
+        TOPO_CHECK_LAUNCH();
+    }
     const bool by_residual = g->warm_rule == TO_WARM_RESIDUAL;
-    // the Gram matrix of the two residual directions and their products with F
-    // (K U is 0 at fixed DOFs, so these sums run over the free DOFs)
-    launch_dot(d.ndof, w->KUp, w->KUp, w->dots + 8, w->partials, w->counter, ax);
-    launch_dot(d.ndof, w->KUp, w->KUh, w->dots + 9, w->partials, w->counter, ax);
-    launch_dot(d.ndof, w->KUh, w->KUh, w->dots + 10, w->partials, w->counter, ax);
-    launch_dot(d.ndof, g->F, w->KUp, w->dots + 11, w->partials, w->counter, ax);
-    launch_dot(d.ndof, g->F, w->KUh, w->dots + 12, w->partials, w->counter, ax);
     TOPO_CUDA(cudaMemcpyAsync(w->hdots, w->dots, 14 * sizeof(double), cudaMemcpyDeviceToHost, ax));
     TOPO_CUDA(cudaEventRecord(w->ready, ax));
     solver_setup(g);
